@@ -1,0 +1,155 @@
+"""ADMM with Barzilai-Borwein dual step, float64 (oracle; test use only).
+
+Sec. 2.2.  Consensus form (Eq. 5): minimise sum_s f_s(x_s) s.t. x_s = z,
+z in the box.  Each iteration k:
+  1. x_s^{k+1} = argmin f_s(x) + (rho/2)||x - z^k + y_s^k/rho||^2      (Eq. 6)
+     = solution of B_s x = c_s^k,  B_s = A~_s^T A~_s + (rho/2) I,
+       c_s^k = A~_s^T p~ + (rho/2)(z^k - y_s^k/rho)                  (App. A)
+  2. z^{k+1} = P_box(mean_s(x_s^{k+1} + y_s^k/rho))   [zmode "std"]
+     or       P_box(mean_s x_s^{k+1})                 [zmode "lit", as printed]
+  3. y_s^{k+1} = y_s^k + step_k (x_s^{k+1} - z^{k+1})                   (Eq. 7)
+     step_k = BB value beta^k = -dd'dy/||dd||^2 if it is > 0, else rho   (Eq. 8)
+     dd = d^{k+1} - d^k with d = x - 1(x)z, dy = y^k - y^{k-1}
+  4. stop when ||r_prim|| <= eps_prim and ||r_dual|| <= eps_dual          (Eq. 9)
+     r_prim = x^{k+1} - 1(x)z^{k+1},  r_dual = 1(x) rho (z^{k+1} - z^k),
+     eps_prim = eps_abs sqrt(Nn) + eps_rel max(||x||, sqrt(N)||z||),
+     eps_dual = eps_abs sqrt(Nn) + eps_rel ||y||.
+Optionally combined (AND) with a relative objective-change test (Sec. 2.3).
+
+Readings (the paper is silent): z^0 = P(z0) (default 0), y^0 = y0 (default 0),
+x_s^0 = z^0; the BB step needs y^{k-1}, so the first iteration uses rho; the
+step must be finite and > 0, else rho; bb="guarded" clamps it to
+[rho/kappa, kappa*rho]; bb="off" always uses rho.
+
+The subproblem is solved either with a Cholesky factor of B_s computed once
+(App. A, the paper's method) or by conjugate gradients warm-started from
+x_s^k (a reading: the paper only uses the factor).  CG stops when
+    ||c_s - B_s x|| <= max(theta (rho/2) max(r_prim^k, eps_prim^k) / sqrt(N),
+                           floor_rel ||c_s||)
+(k >= 1; ||x_err|| <= 2||residual||/rho, so the subproblem error stays a
+fraction theta of the primal residual), and when ||c_s - B_s x|| <= eta0 ||c_s||
+in the first iteration.
+"""
+from __future__ import annotations
+
+import math
+import time
+
+import numpy as np
+import scipy.linalg as sla
+
+from .problem import Weighted
+
+
+def _cg(W, s, rho, c, x, tol, kmax):
+    """Conjugate gradients (Hestenes-Stiefel) on B_s x = c from the warm start x,
+    stopped when the residual norm ||c - B_s x|| <= tol."""
+    r = c - W.normal_apply(s, x, rho)
+    gam = float(r @ r)
+    if math.sqrt(gam) <= tol:
+        return x, 0
+    p = r.copy()
+    it = 0
+    for it in range(1, kmax + 1):
+        u = W.normal_apply(s, p, rho)
+        alpha = gam / float(p @ u)
+        x = x + alpha * p
+        r = r - alpha * u
+        gnew = float(r @ r)
+        if math.sqrt(gnew) <= tol:
+            break
+        p = r + (gnew / gam) * p
+        gam = gnew
+    return x, it
+
+
+def admm_bb(prob_or_w, rho=None, eps_abs=1e-4, eps_rel=1e-4, max_iter=1000,
+            subproblem="chol", bb="paper", zmode="std", bb_kappa=10.0,
+            z0=None, y0=None, tol_obj=math.inf, cg_theta=0.1, cg_eta0=1e-2,
+            cg_floor_rel=0.0, cg_max=200, record=False):
+    W = prob_or_w if isinstance(prob_or_w, Weighted) else Weighted(prob_or_w)
+    N, n = W.N, W.n
+    if rho is None:
+        from .problem import default_rho
+        rho = default_rho(W)
+    t0 = time.perf_counter()
+    b = [W.b(s) for s in range(N)]
+    if subproblem == "chol":
+        fac = [sla.cho_factor(W.B_dense(s, rho), lower=False) for s in range(N)]
+    z = W.proj(np.zeros(n) if z0 is None else np.asarray(z0, float).copy())
+    y = np.zeros((N, n)) if y0 is None else np.asarray(y0, float).reshape(N, n).copy()
+    x = np.tile(z, (N, 1))
+    d_prev = x - z[None, :]
+    y_prev = None
+    rp_prev, ep_prev = None, None
+    f_prev = W.f(z) if math.isfinite(tol_obj) else None
+    hist = []
+    status = "not_converged"
+    cg_total = 0
+    it = 0
+    step = rho
+    for k in range(max_iter):
+        # 1. scenario subproblems
+        xn = np.empty_like(x)
+        for s in range(N):
+            c = b[s] + 0.5 * rho * (z - y[s] / rho)
+            if subproblem == "chol":
+                xn[s] = sla.cho_solve(fac[s], c)
+            else:
+                cn = float(np.linalg.norm(c))
+                if rp_prev is None:
+                    tol = cg_eta0 * cn
+                else:
+                    tol = max(cg_theta * 0.5 * rho * max(rp_prev, ep_prev) / math.sqrt(N),
+                              cg_floor_rel * cn)
+                xn[s], kk = _cg(W, s, rho, c, x[s].copy(), tol, cg_max)
+                cg_total += kk
+        # 2. consensus projection
+        if zmode == "std":
+            zn = W.proj(np.mean(xn + y / rho, axis=0))
+        elif zmode == "lit":
+            zn = W.proj(np.mean(xn, axis=0))
+        else:
+            raise ValueError(zmode)
+        # 3. BB step and dual update
+        d = xn - zn[None, :]
+        step = rho
+        if bb != "off" and y_prev is not None:
+            dd = (d - d_prev).ravel()
+            dy = (y - y_prev).ravel()
+            den = float(dd @ dd)
+            if den > 0.0:
+                beta = -float(dd @ dy) / den
+                if math.isfinite(beta) and beta > 0.0:
+                    step = beta
+                    if bb == "guarded":
+                        step = min(max(step, rho / bb_kappa), bb_kappa * rho)
+        yn = y + step * d
+        # 4. residuals and stopping rule
+        r_prim = float(np.linalg.norm(d))
+        r_dual = math.sqrt(N) * rho * float(np.linalg.norm(zn - z))
+        xnorm = float(np.linalg.norm(xn))
+        eps_prim = eps_abs * math.sqrt(N * n) + eps_rel * max(xnorm, math.sqrt(N) * float(np.linalg.norm(zn)))
+        eps_dual = eps_abs * math.sqrt(N * n) + eps_rel * float(np.linalg.norm(yn))
+        ok = r_prim <= eps_prim and r_dual <= eps_dual
+        if math.isfinite(tol_obj):
+            fz = W.f(zn)
+            ok = ok and abs(f_prev - fz) <= tol_obj * max(abs(fz), 1e-300)
+            f_prev = fz
+        if record:
+            hist.append(dict(k=k + 1, t=time.perf_counter() - t0, r_prim=r_prim, r_dual=r_dual,
+                             eps_prim=eps_prim, eps_dual=eps_dual, step=step, f=W.f(zn)))
+        y_prev, y = y, yn
+        x, z, d_prev = xn, zn, d
+        rp_prev, ep_prev = r_prim, eps_prim
+        it = k + 1
+        if not (math.isfinite(r_prim) and math.isfinite(r_dual)):
+            status = "diverged"
+            break
+        if ok:
+            status = "converged"
+            break
+    return dict(z=z, x=x, y=y, iterations=it, status=status, rho=rho, step=step,
+                r_prim=r_prim, r_dual=r_dual, eps_prim=eps_prim, eps_dual=eps_dual,
+                cg_iterations=cg_total, f=W.f(z), history=hist,
+                seconds=time.perf_counter() - t0)
