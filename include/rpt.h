@@ -1,0 +1,231 @@
+/*
+ * rpt.h -- C ABI of librpt: robust proton treatment planning by ADMM with a
+ * Barzilai-Borwein dual step (ADMM-BB), on one GPU (sm_103a).
+ *
+ * Problem (Sec. 2.1, Eqs. 1-2; scenario probabilities as in Sec. 2.1):
+ *     minimise  f(x) = sum_s c_s sum_i w_i (a_{s,i}^T x - p_i)^2
+ *     subject to lb <= x <= ub
+ * A_s (m x n, one per uncertainty scenario s = 1..N) are dose-influence
+ * matrices with rows = voxels and columns = proton spots; w = voxel weights,
+ * p = prescription, c_s = scenario weights.  The paper's case is lb = 0,
+ * ub = +inf.
+ *
+ * Conventions for every entry point:
+ *  - The return value is a status code (RPT_OK = 0, > 0 warning, < 0 error).
+ *    On an error no output array is written.  No call aborts the process.
+ *    rpt_last_error() gives a thread-local message for the last failure.
+ *  - Array arguments are HOST pointers unless the name ends in "_dev".
+ *    Host input arrays are only read during the call; the library copies what
+ *    it keeps.  Output arrays are caller-allocated and written on success.
+ *  - Dense vectors are float64.  "[N*n]" means scenario-major: element j of
+ *    scenario s is at s*n + j.
+ *  - A plan owns its device memory and one CUDA stream (the caller's stream if
+ *    given in rpt_device_opts).  Calls on one plan must not overlap; different
+ *    plans may be used from different threads.
+ *  - All device-side loops are bounded (max_iter, cg_max, max_trials);
+ *    the library has no unbounded device wait.
+ */
+#ifndef RPT_H
+#define RPT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------- */
+#define RPT_OK              0
+#define RPT_NOT_CONVERGED   1   /* iteration cap reached; the last iterate is returned */
+#define RPT_EINVAL        (-1)  /* bad argument: sizes, CSR structure, NaN/Inf, lb > ub */
+#define RPT_ENOMEM        (-2)  /* device or host allocation failed */
+#define RPT_ECUDA         (-3)  /* a CUDA runtime call failed (message in rpt_last_error) */
+#define RPT_TIMEOUT       (-4)  /* a bounded device-side wait ran out */
+#define RPT_DIVERGED      (-5)  /* a residual or objective became non-finite */
+#define RPT_EUNSUPPORTED  (-6)  /* valid request outside this build's limits (e.g. n too large) */
+
+/* ---- value formats of the stored dose-influence matrix ------------------- */
+#define RPT_F32      0   /* float32 as given */
+#define RPT_BF16     1   /* bfloat16 with one float32 scale per spot column */
+#define RPT_FP8E4M3  2   /* float8 e4m3 with one float32 scale per spot column */
+
+/* ---- ADMM variants (readings of Sec. 2.2, see rpt_admm_params) ----------- */
+#define RPT_BB_PAPER    0   /* Eq. 8: BB value if > 0 (and finite), else rho */
+#define RPT_BB_GUARDED  1   /* Eq. 8 clamped to [rho/bb_kappa, bb_kappa*rho] */
+#define RPT_BB_OFF      2   /* always rho: textbook consensus ADMM */
+#define RPT_Z_STD       0   /* z = P(mean_s(x_s + y_s/rho)): exact z-minimiser */
+#define RPT_Z_LIT       1   /* z = P(mean_s x_s): the update as printed in Sec. 2.2 */
+
+/* Largest spot count this build supports (the spot vector and its accumulator
+ * are staged in shared memory of one CTA). */
+#define RPT_MAX_SPOTS 24576
+
+typedef struct rpt_plan rpt_plan;   /* opaque; created and owned by the library */
+
+/* The problem, as host arrays (Sec. 2.1).  All pointers are read-only and only
+ * read during rpt_plan_create. */
+typedef struct {
+  int32_t m;                        /* voxels (rows), >= 1 */
+  int32_t n;                        /* spots (columns), 1..RPT_MAX_SPOTS */
+  int32_t N;                        /* scenarios, >= 1 */
+  const int32_t* const* row_ptr;    /* N arrays of m+1: row_ptr[s][0] = 0, non-decreasing */
+  const int32_t* const* col_idx;    /* N arrays of nnz_s = row_ptr[s][m]: in [0,n), strictly increasing within a row */
+  const float*   const* val;        /* N arrays of nnz_s: finite and >= 0 (dose influence) */
+  const double* voxel_w;            /* [m] voxel weights w_i, finite and >= 0 (Eq. 1) */
+  const double* presc;              /* [m] prescription p_i, finite and >= 0 (Eq. 1) */
+  const double* scen_weight;        /* [N] scenario weights c_s in [0,1], or NULL for all 1 */
+  const double* lb;                 /* [n] lower bounds, or NULL for 0 (Eq. 2: x >= 0) */
+  const double* ub;                 /* [n] upper bounds, or NULL for +inf; lb <= ub */
+  int32_t value_format;             /* RPT_F32 | RPT_BF16 | RPT_FP8E4M3 */
+  int32_t index_width;              /* 32, or 16 (column indices stored as uint16; needs n <= 65535) */
+} rpt_problem;
+
+typedef struct {
+  int32_t device;                   /* CUDA device ordinal */
+  void*   stream;                   /* cudaStream_t to run on, or NULL for a stream owned by the plan */
+  int32_t ctas_per_sm;              /* row-pass CTAs per SM (0 = library choice) */
+  int32_t row_path;                 /* 0 default (= 1), 1 register-direct loads, 2 bulk-copy (TMA) ring */
+} rpt_device_opts;
+
+/* ADMM-BB parameters (Sec. 2.2).  Fill with rpt_admm_params_default(). */
+typedef struct {
+  double  rho;            /* penalty rho > 0; <= 0 selects rho_scale * 2 mean_s(trace(A~_s^T A~_s))/n */
+  double  rho_scale;      /* multiplier for the default rule (default 1.0) */
+  double  eps_abs;        /* stopping tolerances of Eq. 9 (default 1e-4) */
+  double  eps_rel;
+  double  tol_obj;        /* relative change of f(z) AND-ed with Eq. 9 (Sec. 2.3); +inf = off (default) */
+  int32_t max_iter;       /* ADMM iteration cap (default 5000) */
+  int32_t bb_mode;        /* RPT_BB_PAPER (default) | RPT_BB_GUARDED | RPT_BB_OFF */
+  double  bb_kappa;       /* guard factor for RPT_BB_GUARDED (default 10) */
+  int32_t z_mode;         /* RPT_Z_STD (default) | RPT_Z_LIT */
+  int32_t cg_max;         /* CG iterations per subproblem solve (default 50) */
+  double  cg_theta;       /* CG stops at ||c_s - B_s x|| <= theta (rho/2) max(r_prim, eps_prim)/sqrt(N) (default 0.3) */
+  double  cg_eta0;        /* first ADMM iteration: CG stops at ||r|| <= eta0 ||r_0|| (default 1e-2) */
+  double  cg_floor_rel;   /* never ask CG for ||r|| below floor_rel * ||r_0|| of the first solve (default 1e-6) */
+  int32_t use_graph;      /* 1 (default): one CUDA graph with device-side loops; 0: host-driven loop */
+  int32_t check_every;    /* host-driven loop: read the convergence flag every k iterations (default 1) */
+  int32_t resume;         /* 1: start from the plan's stored state (rpt_state_set / previous solve) */
+  int32_t cg_precond;     /* 0: plain CG; 1: Jacobi-preconditioned CG, M = diag(B_s) (default 1) */
+} rpt_admm_params;
+
+/* PGD parameters (Sec. 2.1, Eq. 3 read as sufficient decrease). */
+typedef struct {
+  double  alpha;          /* initial step; <= 0 selects 4 / L with L = 2 lambda_max(sum_s A~_s^T A~_s) */
+  double  beta;           /* sufficient-decrease constant in (0,1) (default 1e-4) */
+  double  gamma;          /* step shrink factor in (0,1) (default 0.5) */
+  double  tol_rel_df;     /* stop when |f_k - f_{k+1}| / f_k <= tol (default 1e-5) */
+  double  f_target;       /* > 0: also stop once f <= f_target (default 0 = off) */
+  int32_t max_iter;       /* default 20000 */
+  int32_t max_trials;     /* Armijo trials per iteration (default 30) */
+  int32_t use_graph;      /* 1 (default): device-side loops in a CUDA graph */
+  int32_t reserved;
+} rpt_pgd_params;
+
+typedef struct {
+  int32_t status;         /* same code as the return value */
+  int32_t iterations;     /* ADMM or PGD iterations done */
+  int64_t inner;          /* CG iterations (summed over scenarios) or Armijo trials */
+  int64_t row_passes;     /* full passes over the stored matrices */
+  int64_t kernels;        /* kernel launches of the solve (row passes + vector kernels) */
+  double  seconds;        /* device time of the solve (CUDA events) */
+  double  f;              /* f(x_out) (float64 accumulation) */
+  double  r_prim, r_dual, eps_prim, eps_dual;   /* Eq. 9 at the last iteration (ADMM) */
+  double  step;           /* last dual step (ADMM) or accepted step (PGD) */
+  double  rho;            /* penalty used (ADMM) or Lipschitz estimate L (PGD) */
+} rpt_solve_info;
+
+typedef struct {
+  int32_t m, n, N;
+  int32_t m_active;       /* rows kept on the device (rows empty in every scenario are dropped) */
+  int64_t nnz;            /* total stored entries over all scenarios */
+  int64_t matrix_bytes;   /* device bytes of values + indices + row pointers */
+  int32_t value_format, index_width;
+  int32_t row_blocks;     /* CTAs of one row pass */
+  int32_t sm_count;
+  double  default_rho;    /* 2 mean_s(trace(A~_s^T A~_s))/n (without rho_scale) */
+  double  const_term;     /* sum over dropped rows of c_s w_i p_i^2 (part of every f) */
+} rpt_plan_stats;
+
+/* ---- defaults ----------------------------------------------------------- */
+void rpt_admm_params_default(rpt_admm_params* p);
+void rpt_pgd_params_default(rpt_pgd_params* p);
+
+/* ---- plans -------------------------------------------------------------- */
+
+/* Validate and upload a problem; computes the weighted layout of App. A
+ * (w folded per row at run time, not into the values), the row-block
+ * partition and the default penalty.  Fails with RPT_EINVAL on malformed CSR
+ * (row_ptr not starting at 0 or decreasing, column out of range or not
+ * strictly increasing within a row), non-finite or negative val/w/p, lb > ub,
+ * non-finite lb (ub may be +inf); RPT_EUNSUPPORTED for n > RPT_MAX_SPOTS or
+ * an unsupported format; RPT_ENOMEM/RPT_ECUDA on device failures.  *out is
+ * set only on success. */
+int rpt_plan_create(const rpt_problem* prob, const rpt_device_opts* opts, rpt_plan** out);
+
+/* Release a plan and its device memory.  NULL is accepted. */
+void rpt_plan_destroy(rpt_plan* plan);
+
+int rpt_plan_query(const rpt_plan* plan, rpt_plan_stats* out);
+
+/* ---- solvers ------------------------------------------------------------ */
+
+/* ADMM-BB (Sec. 2.2, Eqs. 5-9; App. A).  Each iteration: x_s-updates
+ * (Eq. 6) by warm-started conjugate gradients on B_s x = c_s (App. A) for all
+ * scenarios at once; z-update (box projection of the scenario mean); BB
+ * dual step (Eq. 8) and dual update (Eq. 7); stopping rule (Eq. 9).
+ * z0: [n] initial consensus point (projected onto the box) or NULL for 0.
+ * y0: [N*n] initial duals or NULL for 0.  x_out: [n] the final z.
+ * info may be NULL.  Returns RPT_OK when Eq. 9 (and the optional tol_obj
+ * test) holds, RPT_NOT_CONVERGED at max_iter (x_out written), RPT_DIVERGED
+ * if a residual became non-finite (x_out not written). */
+int rpt_admm_bb_solve(rpt_plan* plan, const rpt_admm_params* params,
+                      const double* z0, const double* y0,
+                      double* x_out, rpt_solve_info* info);
+
+/* Projected gradient descent with Armijo backtracking (Sec. 2.1, Eq. 3 read
+ * as f(x+) <= f(x) + beta grad'(x+ - x)).  x0: [n] or NULL for 0; x_out [n]. */
+int rpt_pgd_solve(rpt_plan* plan, const rpt_pgd_params* params,
+                  const double* x0, double* x_out, rpt_solve_info* info);
+
+/* ---- operators (for checking and for users who verify plans) ------------- */
+
+/* f(x) (Eq. 2) and optionally the physical doses A_s x.  x: [n];
+ * f_out: scalar; dose_out: [N*m] scenario-major or NULL. */
+int rpt_objective(rpt_plan* plan, const double* x, double* f_out, double* dose_out);
+
+/* Gradient of Eq. 2: g = sum_s 2 A~_s^T (A~_s x - p~_s) (Eq. 4 summed), and f(x).
+ * x, g_out: [n]; f_out may be NULL. */
+int rpt_gradient(rpt_plan* plan, const double* x, double* g_out, double* f_out);
+
+/* Subproblem operator of App. A: u_s = (A~_s^T A~_s + (rho/2) I) v_s for every
+ * scenario.  v, u_out: [N*n]; rho >= 0. */
+int rpt_apply_normal(rpt_plan* plan, const double* v, double rho, double* u_out);
+
+/* Time the row pass alone: `reps` back-to-back launches on the plan's stream
+ * bracketed by CUDA events, over every scenario, with the spot vectors last
+ * staged on the plan (e.g. by rpt_apply_normal).  mode 0: the CG operator
+ * pass (A~_s^T A~_s v_s); mode 1: the residual pass (A~_s^T (A~_s v_s - p~),
+ * with the objective).  *ms_per_pass: average milliseconds per launch;
+ * *bytes_per_pass: the algorithmic bytes of one launch (stored values and
+ * indices, row pointers, one voxel weight per row and scenario (+ one
+ * prescription in mode 1), the spot vectors in and out). */
+int rpt_profile_row_pass(rpt_plan* plan, int mode, int reps, double* ms_per_pass,
+                         double* bytes_per_pass);
+
+/* ---- ADMM state (checkpoint / resume) ----------------------------------- */
+
+/* The plan keeps the state (z, x_s, y_s) of its last ADMM solve.  get copies
+ * it out (any pointer may be NULL to skip); set replaces it (all three
+ * required), for rpt_admm_params.resume.  z: [n]; x, y: [N*n]. */
+int rpt_state_get(rpt_plan* plan, double* z, double* x, double* y);
+int rpt_state_set(rpt_plan* plan, const double* z, const double* x, const double* y);
+
+/* ---- diagnostics --------------------------------------------------------- */
+const char* rpt_status_string(int status);   /* static string */
+const char* rpt_last_error(void);            /* thread-local, valid until the next call on this thread */
+const char* rpt_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RPT_H */

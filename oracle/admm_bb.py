@@ -23,12 +23,14 @@ step must be finite and > 0, else rho; bb="guarded" clamps it to
 
 The subproblem is solved either with a Cholesky factor of B_s computed once
 (App. A, the paper's method) or by conjugate gradients warm-started from
-x_s^k (a reading: the paper only uses the factor).  CG stops when
-    ||c_s - B_s x|| <= max(theta (rho/2) max(r_prim^k, eps_prim^k) / sqrt(N),
-                           floor_rel ||c_s||)
-(k >= 1; ||x_err|| <= 2||residual||/rho, so the subproblem error stays a
-fraction theta of the primal residual), and when ||c_s - B_s x|| <= eta0 ||c_s||
-in the first iteration.
+x_s^k (a reading: the paper only uses the factor), optionally with the
+Jacobi preconditioner M = diag(B_s).  CG on scenario s stops
+when ||c_s - B_s x|| <= tol_s with
+    k = 0:  tol_s = eta0 ||r0_s||,  r0_s = c_s - B_s x_s^0 (the first residual)
+    k >= 1: tol_s = max(theta (rho/2) max(r_prim^k, eps_prim^k) / sqrt(N),
+                        floor_rel ||r0_s||)
+Since ||x_err|| <= 2 ||residual|| / rho, the subproblem error stays a
+fraction theta of the primal residual.
 """
 from __future__ import annotations
 
@@ -41,32 +43,36 @@ import scipy.linalg as sla
 from .problem import Weighted
 
 
-def _cg(W, s, rho, c, x, tol, kmax):
-    """Conjugate gradients (Hestenes-Stiefel) on B_s x = c from the warm start x,
-    stopped when the residual norm ||c - B_s x|| <= tol."""
+def _cg(W, s, rho, c, x, tol_fn, kmax, minv=None):
+    """Preconditioned conjugate gradients (Hestenes-Stiefel) on B_s x = c from the
+    warm start x, with M^{-1} = diag(minv) (None: no preconditioner); stopped when
+    the residual norm ||c - B_s x|| <= tol_fn(||initial residual||)."""
     r = c - W.normal_apply(s, x, rho)
-    gam = float(r @ r)
-    if math.sqrt(gam) <= tol:
+    tol = tol_fn(float(np.linalg.norm(r)))
+    if float(np.linalg.norm(r)) <= tol:
         return x, 0
-    p = r.copy()
+    z = r if minv is None else minv * r
+    gam = float(r @ z)
+    p = z.copy()
     it = 0
     for it in range(1, kmax + 1):
         u = W.normal_apply(s, p, rho)
         alpha = gam / float(p @ u)
         x = x + alpha * p
         r = r - alpha * u
-        gnew = float(r @ r)
-        if math.sqrt(gnew) <= tol:
+        if float(np.linalg.norm(r)) <= tol:
             break
-        p = r + (gnew / gam) * p
+        z = r if minv is None else minv * r
+        gnew = float(r @ z)
+        p = z + (gnew / gam) * p
         gam = gnew
     return x, it
 
 
 def admm_bb(prob_or_w, rho=None, eps_abs=1e-4, eps_rel=1e-4, max_iter=1000,
             subproblem="chol", bb="paper", zmode="std", bb_kappa=10.0,
-            z0=None, y0=None, tol_obj=math.inf, cg_theta=0.1, cg_eta0=1e-2,
-            cg_floor_rel=0.0, cg_max=200, record=False):
+            z0=None, y0=None, tol_obj=math.inf, cg_theta=0.3, cg_eta0=1e-2,
+            cg_floor_rel=0.0, cg_max=200, cg_precond="jacobi", record=False, record_f=False):
     W = prob_or_w if isinstance(prob_or_w, Weighted) else Weighted(prob_or_w)
     N, n = W.N, W.n
     if rho is None:
@@ -76,12 +82,18 @@ def admm_bb(prob_or_w, rho=None, eps_abs=1e-4, eps_rel=1e-4, max_iter=1000,
     b = [W.b(s) for s in range(N)]
     if subproblem == "chol":
         fac = [sla.cho_factor(W.B_dense(s, rho), lower=False) for s in range(N)]
+    minv = [None] * N
+    if subproblem == "cg" and cg_precond == "jacobi":
+        # Jacobi preconditioner: diag(B_s) = diag(A~_s^T A~_s) + rho/2
+        minv = [1.0 / (np.asarray(W.At[s].multiply(W.At[s]).sum(axis=0)).ravel() + 0.5 * rho)
+                for s in range(N)]
     z = W.proj(np.zeros(n) if z0 is None else np.asarray(z0, float).copy())
     y = np.zeros((N, n)) if y0 is None else np.asarray(y0, float).reshape(N, n).copy()
     x = np.tile(z, (N, 1))
     d_prev = x - z[None, :]
     y_prev = None
     rp_prev, ep_prev = None, None
+    r0 = np.zeros(N)
     f_prev = W.f(z) if math.isfinite(tol_obj) else None
     hist = []
     status = "not_converged"
@@ -96,13 +108,15 @@ def admm_bb(prob_or_w, rho=None, eps_abs=1e-4, eps_rel=1e-4, max_iter=1000,
             if subproblem == "chol":
                 xn[s] = sla.cho_solve(fac[s], c)
             else:
-                cn = float(np.linalg.norm(c))
                 if rp_prev is None:
-                    tol = cg_eta0 * cn
+                    def tol_fn(r0n, s=s):
+                        r0[s] = r0n
+                        return cg_eta0 * r0n
                 else:
-                    tol = max(cg_theta * 0.5 * rho * max(rp_prev, ep_prev) / math.sqrt(N),
-                              cg_floor_rel * cn)
-                xn[s], kk = _cg(W, s, rho, c, x[s].copy(), tol, cg_max)
+                    def tol_fn(r0n, s=s):
+                        return max(cg_theta * 0.5 * rho * max(rp_prev, ep_prev) / math.sqrt(N),
+                                   cg_floor_rel * r0[s])
+                xn[s], kk = _cg(W, s, rho, c, x[s].copy(), tol_fn, cg_max, minv[s])
                 cg_total += kk
         # 2. consensus projection
         if zmode == "std":
@@ -138,7 +152,8 @@ def admm_bb(prob_or_w, rho=None, eps_abs=1e-4, eps_rel=1e-4, max_iter=1000,
             f_prev = fz
         if record:
             hist.append(dict(k=k + 1, t=time.perf_counter() - t0, r_prim=r_prim, r_dual=r_dual,
-                             eps_prim=eps_prim, eps_dual=eps_dual, step=step, f=W.f(zn)))
+                             eps_prim=eps_prim, eps_dual=eps_dual, step=step, cg=cg_total,
+                             f=W.f(zn) if record_f else None))
         y_prev, y = y, yn
         x, z, d_prev = xn, zn, d
         rp_prev, ep_prev = r_prim, eps_prim

@@ -1,0 +1,916 @@
+// C ABI of librpt: plan creation (validation, row compaction, row blocks,
+// upload, optional quantisation) and the extern "C" wrappers.
+#include <algorithm>
+#include <cstdlib>
+#include <atomic>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "plan.h"
+
+namespace rpt {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+int cuda_fail(cudaError_t e, const char* what) {
+  g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+  if (e == cudaErrorMemoryAllocation) return RPT_ENOMEM;
+  return RPT_ECUDA;
+}
+
+namespace {
+
+// ---- quantisation kernels (plan creation only) ---------------------------------
+
+__global__ void k_colmax(const float* __restrict__ val, const int32_t* __restrict__ col, int64_t nnz,
+                         unsigned int* __restrict__ mx) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nnz;
+       k += (int64_t)gridDim.x * blockDim.x)
+    atomicMax(&mx[col[k]], __float_as_uint(val[k]));   // values are >= 0
+}
+
+__global__ void k_scales(const unsigned int* __restrict__ mx, int n, int n_pad, float fmt_max,
+                         float* __restrict__ scale) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n_pad) return;
+  float s = 1.f;
+  if (j < n) {
+    const float m = __uint_as_float(mx[j]);
+    if (m > 0.f) s = m / fmt_max;
+  }
+  scale[j] = s;
+}
+
+template <typename Q>
+__global__ void k_quantise(const float* __restrict__ val, const int32_t* __restrict__ col, int64_t nnz,
+                           const float* __restrict__ scale, Q* __restrict__ out);
+
+template <>
+__global__ void k_quantise<__nv_bfloat16>(const float* __restrict__ val, const int32_t* __restrict__ col,
+                                          int64_t nnz, const float* __restrict__ scale,
+                                          __nv_bfloat16* __restrict__ out) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nnz;
+       k += (int64_t)gridDim.x * blockDim.x)
+    out[k] = __float2bfloat16_rn(val[k] / scale[col[k]]);
+}
+
+template <>
+__global__ void k_quantise<__nv_fp8_e4m3>(const float* __restrict__ val, const int32_t* __restrict__ col,
+                                          int64_t nnz, const float* __restrict__ scale,
+                                          __nv_fp8_e4m3* __restrict__ out) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nnz;
+       k += (int64_t)gridDim.x * blockDim.x)
+    out[k] = __nv_fp8_e4m3(val[k] / scale[col[k]]);   // round to nearest, saturating
+}
+
+__global__ void k_to_u16(const int32_t* __restrict__ in, int64_t nnz, uint16_t* __restrict__ out) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nnz;
+       k += (int64_t)gridDim.x * blockDim.x)
+    out[k] = (uint16_t)in[k];
+}
+
+struct ScenarioCheck {
+  std::string err;
+  double trace = 0.0;          // sum_i w_i sum_j a_ij^2
+  std::vector<double> diag;    // [n] sum_i w_i a_ij^2 (Jacobi preconditioner)
+};
+
+void check_scenario(const rpt_problem* pr, int s, ScenarioCheck* out) {
+  const int m = pr->m, n = pr->n;
+  const int32_t* rp = pr->row_ptr[s];
+  const int32_t* ci = pr->col_idx[s];
+  const float* va = pr->val[s];
+  if (rp[0] != 0) {
+    out->err = "row_ptr[" + std::to_string(s) + "][0] != 0";
+    return;
+  }
+  double tr = 0.0;
+  out->diag.assign(n, 0.0);
+  for (int i = 0; i < m; ++i) {
+    const int32_t a = rp[i], b = rp[i + 1];
+    if (b < a) {
+      out->err = "row_ptr of scenario " + std::to_string(s) + " decreases at row " + std::to_string(i);
+      return;
+    }
+    double rs = 0.0;
+    int32_t prev = -1;
+    for (int32_t k = a; k < b; ++k) {
+      const int32_t c = ci[k];
+      const float v = va[k];
+      if (c < 0 || c >= n) {
+        out->err = "column index out of range in scenario " + std::to_string(s) + ", row " + std::to_string(i);
+        return;
+      }
+      if (c <= prev) {
+        out->err = "column indices not strictly increasing in scenario " + std::to_string(s) +
+                   ", row " + std::to_string(i);
+        return;
+      }
+      prev = c;
+      if (!std::isfinite(v) || v < 0.f) {
+        out->err = "value not finite or negative in scenario " + std::to_string(s) + ", row " + std::to_string(i);
+        return;
+      }
+      rs += (double)v * (double)v;
+      out->diag[c] += pr->voxel_w[i] * (double)v * (double)v;
+    }
+    tr += pr->voxel_w[i] * rs;
+  }
+  out->trace = tr;
+}
+
+struct Alloc {
+  Plan* P;
+  cudaError_t err = cudaSuccess;
+  template <typename T>
+  T* get(size_t count) {
+    if (err != cudaSuccess) return nullptr;
+    void* p = nullptr;
+    err = cudaMalloc(&p, std::max<size_t>(count, 1) * sizeof(T));
+    if (err != cudaSuccess) return nullptr;
+    P->allocs.push_back(p);
+    return (T*)p;
+  }
+};
+
+void free_plan(Plan* P) {
+  if (!P) return;
+  int cur = -1;
+  cudaGetDevice(&cur);
+  cudaSetDevice(P->device);
+  if (P->stream) cudaStreamSynchronize(P->stream);
+  destroy_graphs(P);
+  for (void* a : P->allocs) cudaFree(a);
+  P->allocs.clear();
+  if (P->ctl_host) cudaFreeHost(P->ctl_host);
+  if (P->ev0) cudaEventDestroy(P->ev0);
+  if (P->ev1) cudaEventDestroy(P->ev1);
+  if (P->own_stream && P->stream) cudaStreamDestroy(P->stream);
+  if (cur >= 0) cudaSetDevice(cur);
+  delete P;
+}
+
+struct TmaLayout {
+  std::vector<ChunkDesc> chunks;
+  std::vector<int4> segs;      // (s, chunk_begin, chunk_end, slot)
+  std::vector<int> cta_seg;    // [G+1]
+  std::vector<int> slot_first; // [N+1]
+};
+
+// Cut the scenario-major sequence of all rows into G equal-cost slices (one
+// persistent CTA each), split slices at scenario boundaries into segments and
+// segments into row-aligned chunks of at most cmax copied entries (16-entry
+// aligned span) and rmax rows.  Returns false if a single row does not fit.
+bool build_tma_layout(const std::vector<int32_t>& rp_h, const std::vector<int64_t>& base, int N,
+                      int m_act, int G, int cmax, int rmax, double row_cost, TmaLayout* L) {
+  const int64_t R = (int64_t)N * m_act;
+  auto rowlen = [&](int64_t idx) {
+    const int s = (int)(idx / m_act), r = (int)(idx % m_act);
+    const int32_t* o = &rp_h[(size_t)s * (m_act + 1)];
+    return (double)(o[r + 1] - o[r]);
+  };
+  double total = 0.0;
+  for (int64_t i = 0; i < R; ++i) total += rowlen(i) + row_cost;
+  std::vector<int64_t> cut(G + 1, R);
+  cut[0] = 0;
+  {
+    double acc = 0.0;
+    int g = 1;
+    for (int64_t i = 0; i < R && g < G; ++i) {
+      while (g < G && acc >= total * g / G) cut[g++] = i;
+      acc += rowlen(i) + row_cost;
+    }
+    while (g < G) cut[g++] = R;
+  }
+  L->cta_seg.assign(G + 1, 0);
+  L->slot_first.assign(N + 1, -1);
+  for (int c = 0; c < G; ++c) {
+    L->cta_seg[c] = (int)L->segs.size();
+    int64_t a = cut[c];
+    const int64_t b = cut[c + 1];
+    while (a < b) {
+      const int s = (int)(a / m_act);
+      const int r0 = (int)(a % m_act);
+      const int r1 = (int)std::min<int64_t>(b - (int64_t)s * m_act, m_act);
+      const int32_t* o = &rp_h[(size_t)s * (m_act + 1)];
+      const int slot = (int)L->segs.size();
+      if (L->slot_first[s] < 0) L->slot_first[s] = slot;
+      const int cb = (int)L->chunks.size();
+      int r = r0;
+      while (r < r1) {
+        const int64_t g_al = (base[s] + o[r]) & ~(int64_t)15;
+        int re = r;
+        while (re < r1 && re - r < rmax) {
+          const int64_t g_end = (base[s] + o[re + 1] + 15) & ~(int64_t)15;
+          if (g_end - g_al > cmax) break;
+          ++re;
+        }
+        if (re == r) return false;
+        ChunkDesc ch{};
+        ch.g_al = g_al;
+        ch.row_begin = r;
+        ch.n_rows = re - r;
+        ch.n_ent = (int)std::max<int64_t>(16, ((base[s] + o[re] + 15) & ~(int64_t)15) - g_al);
+        L->chunks.push_back(ch);
+        r = re;
+      }
+      L->segs.push_back(make_int4(s, cb, (int)L->chunks.size(), slot));
+      a = (int64_t)s * m_act + r1;
+    }
+  }
+  L->cta_seg[G] = (int)L->segs.size();
+  L->slot_first[N] = (int)L->segs.size();
+  for (int s = N - 1; s >= 0; --s)
+    if (L->slot_first[s] < 0) L->slot_first[s] = L->slot_first[s + 1];
+  return true;
+}
+
+int env_int(const char* name, int dflt) {
+  const char* v = std::getenv(name);
+  if (!v || !*v) return dflt;
+  return std::atoi(v);
+}
+
+int create_plan(const rpt_problem* pr, const rpt_device_opts* opts, rpt_plan** out) {
+  if (!pr || !out) {
+    set_error("null argument");
+    return RPT_EINVAL;
+  }
+  const int m = pr->m, n = pr->n, N = pr->N;
+  if (m < 1 || n < 1 || N < 1) {
+    set_error("m, n and N must be >= 1");
+    return RPT_EINVAL;
+  }
+  if (n > RPT_MAX_SPOTS) {
+    set_error("n = " + std::to_string(n) + " exceeds RPT_MAX_SPOTS = " + std::to_string(RPT_MAX_SPOTS));
+    return RPT_EUNSUPPORTED;
+  }
+  if (pr->value_format < RPT_F32 || pr->value_format > RPT_FP8E4M3) {
+    set_error("unknown value_format");
+    return RPT_EUNSUPPORTED;
+  }
+  if (pr->index_width != 32 && pr->index_width != 16) {
+    set_error("index_width must be 32 or 16");
+    return RPT_EUNSUPPORTED;
+  }
+  if (pr->index_width == 16 && n > 65535) {
+    set_error("index_width 16 needs n <= 65535");
+    return RPT_EINVAL;
+  }
+  if (!pr->row_ptr || !pr->col_idx || !pr->val || !pr->voxel_w || !pr->presc) {
+    set_error("null array in rpt_problem");
+    return RPT_EINVAL;
+  }
+  for (int s = 0; s < N; ++s)
+    if (!pr->row_ptr[s] || (!pr->col_idx[s] && pr->row_ptr[s][m] > 0) || (!pr->val[s] && pr->row_ptr[s][m] > 0)) {
+      set_error("null CSR array for scenario " + std::to_string(s));
+      return RPT_EINVAL;
+    }
+  for (int i = 0; i < m; ++i) {
+    if (!std::isfinite(pr->voxel_w[i]) || pr->voxel_w[i] < 0) {
+      set_error("voxel_w[" + std::to_string(i) + "] not finite or negative");
+      return RPT_EINVAL;
+    }
+    if (!std::isfinite(pr->presc[i]) || pr->presc[i] < 0) {
+      set_error("presc[" + std::to_string(i) + "] not finite or negative");
+      return RPT_EINVAL;
+    }
+  }
+  std::vector<double> cs(N, 1.0);
+  if (pr->scen_weight)
+    for (int s = 0; s < N; ++s) {
+      if (!std::isfinite(pr->scen_weight[s]) || pr->scen_weight[s] < 0) {
+        set_error("scen_weight[" + std::to_string(s) + "] not finite or negative");
+        return RPT_EINVAL;
+      }
+      cs[s] = pr->scen_weight[s];
+    }
+  std::vector<double> lb(n, 0.0), ub(n, HUGE_VAL);
+  for (int j = 0; j < n; ++j) {
+    if (pr->lb) lb[j] = pr->lb[j];
+    if (pr->ub) ub[j] = pr->ub[j];
+    if (!std::isfinite(lb[j]) || std::isnan(ub[j]) || ub[j] == -HUGE_VAL || lb[j] > ub[j]) {
+      set_error("bounds invalid at spot " + std::to_string(j) + " (need finite lb <= ub)");
+      return RPT_EINVAL;
+    }
+  }
+  // ---- CSR validation (one host thread per scenario, bounded) ----
+  std::vector<ScenarioCheck> chk(N);
+  {
+    const int hw = std::max(1u, std::thread::hardware_concurrency());
+    const int nt = std::min(N, std::min(hw, 32));
+    std::atomic<int> next(0);
+    std::vector<std::thread> th;
+    for (int t = 0; t < nt; ++t)
+      th.emplace_back([&]() {
+        for (int s = next++; s < N; s = next++) check_scenario(pr, s, &chk[s]);
+      });
+    for (auto& t : th) t.join();
+  }
+  for (int s = 0; s < N; ++s)
+    if (!chk[s].err.empty()) {
+      set_error(chk[s].err);
+      return RPT_EINVAL;
+    }
+  // ---- row compaction: drop rows with no entry in any scenario ----
+  std::vector<uint8_t> keep(m, 0);
+  for (int s = 0; s < N; ++s) {
+    const int32_t* rp = pr->row_ptr[s];
+    for (int i = 0; i < m; ++i)
+      if (rp[i + 1] > rp[i]) keep[i] = 1;
+  }
+  std::vector<int32_t> kept;
+  kept.reserve(m);
+  double const_term = 0.0;
+  for (int i = 0; i < m; ++i) {
+    if (keep[i]) kept.push_back(i);
+    else
+      for (int s = 0; s < N; ++s) const_term += cs[s] * pr->voxel_w[i] * pr->presc[i] * pr->presc[i];
+  }
+  if (kept.empty()) {   // keep one (empty) row so every launch has work items
+    kept.push_back(0);
+    for (int s = 0; s < N; ++s) const_term -= cs[s] * pr->voxel_w[0] * pr->presc[0] * pr->presc[0];
+  }
+  const int m_act = (int)kept.size();
+  std::vector<int64_t> nnz(N), base(N);
+  int64_t NNZ = 0;
+  for (int s = 0; s < N; ++s) {
+    nnz[s] = pr->row_ptr[s][m];
+    base[s] = NNZ;
+    NNZ += nnz[s];
+  }
+
+  Plan* P = new (std::nothrow) Plan();
+  if (!P) {
+    set_error("out of host memory");
+    return RPT_ENOMEM;
+  }
+  P->device = opts ? opts->device : 0;
+  cudaError_t e = cudaSetDevice(P->device);
+  if (e != cudaSuccess) {
+    free_plan(P);
+    return cuda_fail(e, "cudaSetDevice");
+  }
+  cudaDeviceGetAttribute(&P->sm_count, cudaDevAttrMultiProcessorCount, P->device);
+  if (opts && opts->stream) {
+    P->stream = (cudaStream_t)opts->stream;
+  } else {
+    if ((e = cudaStreamCreateWithFlags(&P->stream, cudaStreamNonBlocking))) {
+      free_plan(P);
+      return cuda_fail(e, "cudaStreamCreate");
+    }
+    P->own_stream = true;
+  }
+  const int n_pad = (n + 31) / 32 * 32;
+  DevPlan& dp = P->dp;
+  dp.m = m;
+  dp.n = n;
+  dp.N = N;
+  dp.m_act = m_act;
+  dp.n_pad = n_pad;
+  dp.value_format = pr->value_format;
+  dp.index_width = pr->index_width;
+  P->nchunk = (n + kVecThreads - 1) / kVecThreads;
+  P->kept_rows = kept;
+  const int bi = pr->index_width == 16 ? 2 : 4;
+  const int bv = pr->value_format == RPT_F32 ? 4 : (pr->value_format == RPT_BF16 ? 2 : 1);
+
+  // ---- row pointers over kept rows ----
+  std::vector<int32_t> rp_h((size_t)N * (m_act + 1));
+  for (int s = 0; s < N; ++s) {
+    const int32_t* rp = pr->row_ptr[s];
+    int32_t* o = &rp_h[(size_t)s * (m_act + 1)];
+    for (int k = 0; k < m_act; ++k) o[k] = rp[kept[k]];
+    o[m_act] = rp[m];
+  }
+  // ---- work decomposition: TMA ring (default) or register-direct row blocks ----
+  const double row_cost = 8.0;   // per-row overhead, in units of one entry
+  const int want_path = opts ? opts->row_path : 0;
+  std::vector<int4> blocks;
+  std::vector<int> blk_first(N + 1, 0);
+  TmaLayout tl;
+  bool use_tma = false;
+  int ctas = 0;
+  if (want_path == 2) {
+    int smem_optin = 0;
+    cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, P->device);
+    dp.cmax = std::max(64, env_int("RPT_TMA_CMAX", 4096)) & ~15;
+    dp.rmax = std::max(8, env_int("RPT_TMA_RMAX", 256));
+    dp.stages = std::min(8, std::max(2, env_int("RPT_TMA_STAGES", 3)));
+    ctas = (opts && opts->ctas_per_sm > 0) ? opts->ctas_per_sm : 1;
+    const size_t need = tma_smem_bytes(n_pad, dp.cmax, dp.rmax, dp.stages, bv, bi, true);
+    if (need * ctas <= (size_t)smem_optin * (ctas == 1 ? 1 : 1) && need <= (size_t)smem_optin)
+      use_tma = build_tma_layout(rp_h, base, N, m_act, P->sm_count * ctas, dp.cmax, dp.rmax, row_cost, &tl);
+    if (!use_tma && want_path == 2) {
+      free_plan(P);
+      set_error("bulk-copy row path not possible for this plan (shared memory or a row longer than RPT_TMA_CMAX)");
+      return RPT_EUNSUPPORTED;
+    }
+  }
+  if (use_tma) {
+    dp.path = 1;
+    dp.grid = P->sm_count * ctas;
+    dp.nblocks = (int)tl.segs.size();
+    blk_first = tl.slot_first;
+  } else {
+    dp.path = 0;
+    ctas = (opts && opts->ctas_per_sm > 0) ? opts->ctas_per_sm : 2;
+    double total = (double)NNZ + row_cost * (double)m_act * N;
+    const double target = std::max(1.0, total / (double)(P->sm_count * ctas));
+    for (int s = 0; s < N; ++s) {
+      const int32_t* o = &rp_h[(size_t)s * (m_act + 1)];
+      const double cost_s = (double)nnz[s] + row_cost * m_act;
+      int nb = std::max(1, (int)std::lround(cost_s / target));
+      nb = std::min(nb, m_act);
+      blk_first[s] = (int)blocks.size();
+      int r = 0;
+      for (int b = 0; b < nb; ++b) {
+        const double goal = cost_s * (b + 1) / nb;
+        int r1 = r;
+        if (b == nb - 1) {
+          r1 = m_act;
+        } else {
+          // smallest r1 with cost(rows [0, r1)) >= goal
+          int lo = r, hi = m_act;
+          while (lo < hi) {
+            const int mid = (lo + hi) / 2;
+            const double c = (double)o[mid] + row_cost * mid;
+            if (c >= goal) hi = mid;
+            else lo = mid + 1;
+          }
+          r1 = std::max(lo, r);
+        }
+        blocks.push_back(make_int4(s, r, r1, 0));
+        r = r1;
+      }
+    }
+    blk_first[N] = (int)blocks.size();
+    dp.nblocks = (int)blocks.size();
+    dp.grid = dp.nblocks;
+  }
+  // per-row records {row_ptr, c_s w_i, p_i, 0} for the bulk copies
+  std::vector<int4> rec_h((size_t)N * (m_act + 1));
+  for (int s = 0; s < N; ++s) {
+    const int32_t* o = &rp_h[(size_t)s * (m_act + 1)];
+    for (int k = 0; k <= m_act; ++k) {
+      const float wc = k < m_act ? (float)(cs[s] * pr->voxel_w[kept[k]]) : 0.f;
+      const float pp = k < m_act ? (float)pr->presc[kept[k]] : 0.f;
+      int4 r4;
+      r4.x = o[k];
+      std::memcpy(&r4.y, &wc, 4);
+      std::memcpy(&r4.z, &pp, 4);
+      r4.w = 0;
+      rec_h[(size_t)s * (m_act + 1) + k] = r4;
+    }
+  }
+  std::vector<float> diag_h((size_t)N * n);
+  for (int s = 0; s < N; ++s)
+    for (int j = 0; j < n; ++j) diag_h[(size_t)s * n + j] = (float)(cs[s] * chk[s].diag[j]);
+
+  // ---- device memory ----
+  // entry arrays are padded so that 16-entry aligned bulk copies stay inside them
+  constexpr int64_t kPad = 64;
+  Alloc A{P};
+  int32_t* d_rp = A.get<int32_t>(rp_h.size());
+  int64_t* d_base = A.get<int64_t>(N);
+  int32_t* d_col32 = A.get<int32_t>(NNZ + kPad);   // replaced by 16-bit indices if requested
+  float* d_val32 = A.get<float>(NNZ + kPad);       // replaced by quantised values if requested
+  int4* d_rec = A.get<int4>(rec_h.size());
+  ChunkDesc* d_chunks = use_tma ? A.get<ChunkDesc>(tl.chunks.size()) : nullptr;
+  int4* d_segs = use_tma ? A.get<int4>(tl.segs.size()) : nullptr;
+  int* d_ctaseg = use_tma ? A.get<int>(tl.cta_seg.size()) : nullptr;
+  P->err = A.get<int>(1);
+  P->diag = A.get<float>(diag_h.size());
+  float* d_w = A.get<float>(m_act);
+  float* d_p = A.get<float>(m_act);
+  float* d_cs = A.get<float>(N);
+  int4* d_blocks = use_tma ? nullptr : A.get<int4>(blocks.size());
+  int* d_bf = A.get<int>(N + 1);
+  P->lb = A.get<double>(n);
+  P->ub = A.get<double>(n);
+  const size_t Nn = (size_t)N * n;
+  P->x = A.get<double>(Nn);
+  P->r = A.get<double>(Nn);
+  P->p = A.get<double>(Nn);
+  P->u = A.get<double>(Nn);
+  P->y = A.get<double>(Nn);
+  P->d = A.get<double>(Nn);
+  P->dprev = A.get<double>(Nn);
+  P->w = A.get<double>(Nn);
+  P->q = A.get<double>(Nn);
+  P->dinv = A.get<double>(Nn);
+  P->z = A.get<double>(n);
+  P->znew = A.get<double>(n);
+  P->v32 = A.get<float>((size_t)N * n_pad);
+  P->vz32 = A.get<float>(n_pad);
+  P->partial = A.get<float>((size_t)dp.nblocks * n_pad);
+  P->objp = A.get<double>(dp.nblocks);
+  P->gam = A.get<double>(N);
+  P->tol = A.get<double>(N);
+  P->r0n = A.get<double>(N);
+  P->alpha = A.get<double>(N);
+  P->gprev = A.get<double>(N);
+  P->aprev = A.get<double>(N);
+  P->cgi = A.get<int>(N);
+  P->beta = A.get<double>(N);
+  P->act = A.get<int>(N);
+  P->act_next = A.get<int>(N);
+  P->cgcnt = A.get<int>(N);
+  P->cnt_s = A.get<unsigned int>(N);
+  P->dots = A.get<double>((size_t)N * P->nchunk * 4);
+  P->vpart = A.get<double>((size_t)(N + 1) * P->nchunk * 8);
+  P->g = A.get<double>(n);
+  P->xt = A.get<double>(n);
+  P->xp = A.get<double>(n);
+  P->ctl = A.get<Ctl>(1);
+  if (A.err != cudaSuccess) {
+    free_plan(P);
+    return cuda_fail(A.err, "device allocation");
+  }
+  if ((e = cudaMallocHost(&P->ctl_host, sizeof(Ctl)))) {
+    free_plan(P);
+    return cuda_fail(e, "pinned allocation");
+  }
+  if ((e = cudaEventCreate(&P->ev0)) || (e = cudaEventCreate(&P->ev1))) {
+    free_plan(P);
+    return cuda_fail(e, "event");
+  }
+  cudaStream_t st = P->stream;
+  std::vector<float> wf(m_act), pf(m_act), csf(N);
+  for (int k = 0; k < m_act; ++k) {
+    wf[k] = (float)pr->voxel_w[kept[k]];
+    pf[k] = (float)pr->presc[kept[k]];
+  }
+  for (int s = 0; s < N; ++s) csf[s] = (float)cs[s];
+#define RPT_CP(dst, src, bytes)                                                            \
+  do {                                                                                     \
+    if ((bytes) > 0 && (e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st))) { \
+      free_plan(P);                                                                        \
+      return cuda_fail(e, "upload");                                                       \
+    }                                                                                      \
+  } while (0)
+  RPT_CP(d_rp, rp_h.data(), rp_h.size() * sizeof(int32_t));
+  RPT_CP(d_base, base.data(), N * sizeof(int64_t));
+  for (int s = 0; s < N; ++s) {
+    RPT_CP(d_col32 + base[s], pr->col_idx[s], nnz[s] * sizeof(int32_t));
+    RPT_CP(d_val32 + base[s], pr->val[s], nnz[s] * sizeof(float));
+  }
+  RPT_CP(d_w, wf.data(), m_act * sizeof(float));
+  RPT_CP(d_p, pf.data(), m_act * sizeof(float));
+  RPT_CP(d_cs, csf.data(), N * sizeof(float));
+  if (!use_tma) RPT_CP(d_blocks, blocks.data(), blocks.size() * sizeof(int4));
+  RPT_CP(d_rec, rec_h.data(), rec_h.size() * sizeof(int4));
+  RPT_CP(P->diag, diag_h.data(), diag_h.size() * sizeof(float));
+  if (use_tma) {
+    RPT_CP(d_chunks, tl.chunks.data(), tl.chunks.size() * sizeof(ChunkDesc));
+    RPT_CP(d_segs, tl.segs.data(), tl.segs.size() * sizeof(int4));
+    RPT_CP(d_ctaseg, tl.cta_seg.data(), tl.cta_seg.size() * sizeof(int));
+  }
+  RPT_CP(d_bf, blk_first.data(), (N + 1) * sizeof(int));
+  RPT_CP(P->lb, lb.data(), n * sizeof(double));
+  RPT_CP(P->ub, ub.data(), n * sizeof(double));
+#undef RPT_CP
+  if ((e = cudaMemsetAsync(P->cnt_s, 0, sizeof(unsigned int) * N, st)) ||
+      (e = cudaMemsetAsync(P->err, 0, sizeof(int), st)) ||
+      (e = cudaMemsetAsync(d_col32 + NNZ, 0, sizeof(int32_t) * kPad, st)) ||
+      (e = cudaMemsetAsync(d_val32 + NNZ, 0, sizeof(float) * kPad, st)) ||
+      (e = cudaMemsetAsync(P->ctl, 0, sizeof(Ctl), st)) ||
+      (e = cudaMemsetAsync(P->v32, 0, sizeof(float) * (size_t)N * n_pad, st)) ||
+      (e = cudaMemsetAsync(P->vz32, 0, sizeof(float) * n_pad, st))) {
+    free_plan(P);
+    return cuda_fail(e, "memset");
+  }
+  dp.row_ptr = d_rp;
+  dp.nnz_base = d_base;
+  dp.w = d_w;
+  dp.p = d_p;
+  dp.cs = d_cs;
+  dp.blocks = d_blocks;
+  dp.rowrec = d_rec;
+  dp.chunks = d_chunks;
+  dp.segs = d_segs;
+  dp.cta_seg = d_ctaseg;
+  dp.err = P->err;
+  dp.blk_first = d_bf;
+  dp.col32 = d_col32;
+  dp.val32 = d_val32;
+  // ---- quantised values / narrow indices ----
+  const int qgrid = std::max(1, P->sm_count * 8), qblock = 256;
+  if (pr->value_format != RPT_F32) {
+    float* scale = A.get<float>((size_t)N * n_pad);
+    unsigned int* mx = A.get<unsigned int>(n_pad);
+    void* q = pr->value_format == RPT_BF16 ? (void*)A.get<__nv_bfloat16>(NNZ + kPad)
+                                           : (void*)A.get<__nv_fp8_e4m3>(NNZ + kPad);
+    if (A.err != cudaSuccess) {
+      free_plan(P);
+      return cuda_fail(A.err, "device allocation");
+    }
+    const float fmt_max = pr->value_format == RPT_BF16 ? 1.0f : 448.0f;
+    for (int s = 0; s < N && e == cudaSuccess; ++s) {
+      e = cudaMemsetAsync(mx, 0, sizeof(unsigned int) * n_pad, st);
+      if (e) break;
+      if (nnz[s] > 0) k_colmax<<<qgrid, qblock, 0, st>>>(d_val32 + base[s], d_col32 + base[s], nnz[s], mx);
+      k_scales<<<(n_pad + 255) / 256, 256, 0, st>>>(mx, n, n_pad, fmt_max, scale + (size_t)s * n_pad);
+      if (nnz[s] > 0) {
+        if (pr->value_format == RPT_BF16)
+          k_quantise<__nv_bfloat16><<<qgrid, qblock, 0, st>>>(d_val32 + base[s], d_col32 + base[s], nnz[s],
+                                                              scale + (size_t)s * n_pad,
+                                                              (__nv_bfloat16*)q + base[s]);
+        else
+          k_quantise<__nv_fp8_e4m3><<<qgrid, qblock, 0, st>>>(d_val32 + base[s], d_col32 + base[s], nnz[s],
+                                                              scale + (size_t)s * n_pad,
+                                                              (__nv_fp8_e4m3*)q + base[s]);
+      }
+      e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) {
+      free_plan(P);
+      return cuda_fail(e, "quantise");
+    }
+    dp.colscale = scale;
+    if (pr->value_format == RPT_BF16) dp.valbf = (const __nv_bfloat16*)q;
+    else dp.val8 = (const __nv_fp8_e4m3*)q;
+    dp.val32 = nullptr;
+  }
+  if (pr->index_width == 16) {
+    uint16_t* c16 = A.get<uint16_t>(NNZ + kPad);
+    if (A.err != cudaSuccess) {
+      free_plan(P);
+      return cuda_fail(A.err, "device allocation");
+    }
+    k_to_u16<<<qgrid, qblock, 0, st>>>(d_col32, NNZ + kPad, c16);
+    if ((e = cudaGetLastError())) {
+      free_plan(P);
+      return cuda_fail(e, "index conversion");
+    }
+    dp.col16 = c16;
+    dp.col32 = nullptr;
+  }
+  if ((e = cudaStreamSynchronize(st))) {
+    free_plan(P);
+    return cuda_fail(e, "plan upload");
+  }
+  // release the float32 / int32 staging copies that the stored format replaced
+  auto release = [&](void* ptr) {
+    auto it = std::find(P->allocs.begin(), P->allocs.end(), ptr);
+    if (it != P->allocs.end()) {
+      cudaFree(ptr);
+      P->allocs.erase(it);
+    }
+  };
+  if (pr->value_format != RPT_F32) release(d_val32);
+  if (pr->index_width == 16) release(d_col32);
+  if ((e = rowpass_prepare(dp))) {
+    free_plan(P);
+    return cuda_fail(e, "kernel attributes");
+  }
+  // ---- statistics ----
+  double tr = 0.0;
+  for (int s = 0; s < N; ++s) tr += cs[s] * chk[s].trace;
+  rpt_plan_stats& S = P->stats;
+  S.m = m;
+  S.n = n;
+  S.N = N;
+  S.m_active = m_act;
+  S.nnz = NNZ;
+  S.matrix_bytes = NNZ * (int64_t)(bi + bv) + (int64_t)N * (m_act + 1) * 4;
+  S.value_format = pr->value_format;
+  S.index_width = pr->index_width;
+  S.row_blocks = dp.nblocks;
+  S.sm_count = P->sm_count;
+  S.default_rho = 2.0 * (tr / N) / n;
+  S.const_term = const_term;
+  *out = reinterpret_cast<rpt_plan*>(P);
+  return RPT_OK;
+}
+
+template <typename F>
+int guarded(F&& f) {
+  try {
+    return f();
+  } catch (const std::bad_alloc&) {
+    set_error("out of host memory");
+    return RPT_ENOMEM;
+  } catch (...) {
+    set_error("internal error");
+    return RPT_ECUDA;
+  }
+}
+
+Plan* as_plan(rpt_plan* p) { return reinterpret_cast<Plan*>(p); }
+
+struct DeviceScope {
+  int prev = -1;
+  explicit DeviceScope(int dev) {
+    cudaGetDevice(&prev);
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceScope() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+}  // namespace
+}  // namespace rpt
+
+using namespace rpt;
+
+extern "C" {
+
+void rpt_admm_params_default(rpt_admm_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->rho = 0.0;
+  p->rho_scale = 1.0;
+  p->eps_abs = 1e-4;
+  p->eps_rel = 1e-4;
+  p->tol_obj = HUGE_VAL;
+  p->max_iter = 5000;
+  p->bb_mode = RPT_BB_PAPER;
+  p->bb_kappa = 10.0;
+  p->z_mode = RPT_Z_STD;
+  p->cg_max = 50;
+  p->cg_theta = 0.3;
+  p->cg_eta0 = 1e-2;
+  p->cg_floor_rel = 1e-6;
+  p->use_graph = 1;
+  p->check_every = 1;
+  p->resume = 0;
+  p->cg_precond = 1;
+}
+
+void rpt_pgd_params_default(rpt_pgd_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->alpha = 0.0;
+  p->beta = 1e-4;
+  p->gamma = 0.5;
+  p->tol_rel_df = 1e-5;
+  p->f_target = 0.0;
+  p->max_iter = 20000;
+  p->max_trials = 30;
+  p->use_graph = 1;
+}
+
+int rpt_plan_create(const rpt_problem* prob, const rpt_device_opts* opts, rpt_plan** out) {
+  return guarded([&] { return create_plan(prob, opts, out); });
+}
+
+void rpt_plan_destroy(rpt_plan* plan) {
+  if (plan) free_plan(as_plan(plan));
+}
+
+int rpt_plan_query(const rpt_plan* plan, rpt_plan_stats* out) {
+  if (!plan || !out) {
+    set_error("null argument");
+    return RPT_EINVAL;
+  }
+  *out = reinterpret_cast<const Plan*>(plan)->stats;
+  return RPT_OK;
+}
+
+int rpt_admm_bb_solve(rpt_plan* plan, const rpt_admm_params* params, const double* z0,
+                      const double* y0, double* x_out, rpt_solve_info* info) {
+  if (!plan || !params) {
+    set_error("null argument");
+    return RPT_EINVAL;
+  }
+  return guarded([&] {
+    DeviceScope ds(as_plan(plan)->device);
+    return admm_solve(as_plan(plan), params, z0, y0, x_out, info);
+  });
+}
+
+int rpt_pgd_solve(rpt_plan* plan, const rpt_pgd_params* params, const double* x0, double* x_out,
+                  rpt_solve_info* info) {
+  if (!plan || !params) {
+    set_error("null argument");
+    return RPT_EINVAL;
+  }
+  return guarded([&] {
+    DeviceScope ds(as_plan(plan)->device);
+    return pgd_solve(as_plan(plan), params, x0, x_out, info);
+  });
+}
+
+int rpt_objective(rpt_plan* plan, const double* x, double* f_out, double* dose_out) {
+  if (!plan || !x) {
+    set_error("null argument");
+    return RPT_EINVAL;
+  }
+  return guarded([&] {
+    DeviceScope ds(as_plan(plan)->device);
+    return op_objective(as_plan(plan), x, f_out, dose_out);
+  });
+}
+
+int rpt_gradient(rpt_plan* plan, const double* x, double* g_out, double* f_out) {
+  if (!plan || !x || !g_out) {
+    set_error("null argument");
+    return RPT_EINVAL;
+  }
+  return guarded([&] {
+    DeviceScope ds(as_plan(plan)->device);
+    return op_gradient(as_plan(plan), x, g_out, f_out);
+  });
+}
+
+int rpt_apply_normal(rpt_plan* plan, const double* v, double rho, double* u_out) {
+  if (!plan || !v || !u_out) {
+    set_error("null argument");
+    return RPT_EINVAL;
+  }
+  return guarded([&] {
+    DeviceScope ds(as_plan(plan)->device);
+    return op_apply_normal(as_plan(plan), v, rho, u_out);
+  });
+}
+
+int rpt_profile_row_pass(rpt_plan* plan, int mode, int reps, double* ms_per_pass,
+                         double* bytes_per_pass) {
+  if (!plan) {
+    set_error("null argument");
+    return RPT_EINVAL;
+  }
+  return guarded([&] {
+    DeviceScope ds(as_plan(plan)->device);
+    return profile_row_pass(as_plan(plan), mode, reps, ms_per_pass, bytes_per_pass);
+  });
+}
+
+int rpt_state_get(rpt_plan* plan, double* z, double* x, double* y) {
+  if (!plan) {
+    set_error("null argument");
+    return RPT_EINVAL;
+  }
+  return guarded([&] {
+    Plan* P = as_plan(plan);
+    if (!P->state_valid) {
+      set_error("the plan holds no ADMM state");
+      return RPT_EINVAL;
+    }
+    DeviceScope ds(P->device);
+    const size_t Nn = (size_t)P->dp.N * P->dp.n;
+    cudaError_t e = cudaSuccess;
+    if (z && !e) e = cudaMemcpyAsync(z, P->z, sizeof(double) * P->dp.n, cudaMemcpyDeviceToHost, P->stream);
+    if (x && !e) e = cudaMemcpyAsync(x, P->x, sizeof(double) * Nn, cudaMemcpyDeviceToHost, P->stream);
+    if (y && !e) e = cudaMemcpyAsync(y, P->y, sizeof(double) * Nn, cudaMemcpyDeviceToHost, P->stream);
+    if (!e) e = cudaStreamSynchronize(P->stream);
+    return e ? cuda_fail(e, "state copy") : RPT_OK;
+  });
+}
+
+int rpt_state_set(rpt_plan* plan, const double* z, const double* x, const double* y) {
+  if (!plan || !z || !x || !y) {
+    set_error("null argument");
+    return RPT_EINVAL;
+  }
+  return guarded([&] {
+    Plan* P = as_plan(plan);
+    const size_t Nn = (size_t)P->dp.N * P->dp.n;
+    for (int j = 0; j < P->dp.n; ++j)
+      if (!std::isfinite(z[j])) {
+        set_error("z has a non-finite entry");
+        return RPT_EINVAL;
+      }
+    for (size_t i = 0; i < Nn; ++i)
+      if (!std::isfinite(x[i]) || !std::isfinite(y[i])) {
+        set_error("x or y has a non-finite entry");
+        return RPT_EINVAL;
+      }
+    DeviceScope ds(P->device);
+    cudaError_t e = cudaMemcpyAsync(P->z, z, sizeof(double) * P->dp.n, cudaMemcpyHostToDevice, P->stream);
+    if (!e) e = cudaMemcpyAsync(P->x, x, sizeof(double) * Nn, cudaMemcpyHostToDevice, P->stream);
+    if (!e) e = cudaMemcpyAsync(P->y, y, sizeof(double) * Nn, cudaMemcpyHostToDevice, P->stream);
+    if (!e) e = cudaStreamSynchronize(P->stream);
+    if (e) return cuda_fail(e, "state copy");
+    P->state_valid = true;
+    return RPT_OK;
+  });
+}
+
+const char* rpt_status_string(int status) {
+  switch (status) {
+    case RPT_OK: return "ok";
+    case RPT_NOT_CONVERGED: return "not converged (iteration cap reached)";
+    case RPT_EINVAL: return "invalid argument";
+    case RPT_ENOMEM: return "out of memory";
+    case RPT_ECUDA: return "CUDA error";
+    case RPT_TIMEOUT: return "device wait timed out";
+    case RPT_DIVERGED: return "diverged (non-finite residual)";
+    case RPT_EUNSUPPORTED: return "unsupported by this build";
+    default: return "unknown status";
+  }
+}
+
+const char* rpt_last_error(void) { return g_last_error.c_str(); }
+
+const char* rpt_version(void) { return "librpt 0.1 (sm_103a)"; }
+
+}  // extern "C"

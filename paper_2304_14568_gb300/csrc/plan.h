@@ -1,0 +1,93 @@
+// Host-side plan object (what an rpt_plan* points to) and the solver entry
+// points implemented in solver.cu.
+#pragma once
+#include <string>
+#include <vector>
+
+#include "../../include/rpt.h"
+#include "common.cuh"
+
+namespace rpt {
+
+// Device-resident solver control block: parameters of the current solve and
+// the scalars of the iteration (written and read by the kernels).
+struct Ctl {
+  // ADMM parameters
+  double rho, inv_rho, eps_abs, eps_rel, bb_kappa, cg_theta, cg_eta0, cg_floor, tol_obj;
+  double const_term;
+  int max_iter, cg_max, bb_mode, z_mode, use_obj, precond;
+  // ADMM scalars
+  int k, kcg, cg_any, stop, status, have_prev, first, diverged;
+  long long cg_total, passes, cg_steps;
+  double r_prim, r_dual, eps_prim, eps_dual, step, step_prev, f_prev, f_cur;
+  double sz2, dz2;
+  // PGD parameters and scalars
+  double alpha, beta_a, gamma, tol_df, f_target, t, fx, ft, gd;
+  int pgd_max_iter, max_trials, trial, accepted, failed, pk, pouter, pad2;
+  long long trials_total;
+  // last-block-done counters (every finisher resets its own counter)
+  unsigned int cnt_init, cnt_dots_g, cnt_upd, cnt_d, cnt_y, cnt_z, cnt_red, cnt_pg, cnt_pt;
+  unsigned int pad3;
+};
+
+struct Plan {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int sm_count = 0;
+  rpt_plan_stats stats{};
+  DevPlan dp{};
+  int nchunk = 0;                 // column chunks of kVecThreads
+
+  // device allocations (owned)
+  std::vector<void*> allocs;
+
+  // matrix-side arrays are in dp; solver buffers:
+  double *x = nullptr, *r = nullptr, *p = nullptr, *u = nullptr, *y = nullptr;
+  double *d = nullptr, *dprev = nullptr, *z = nullptr, *znew = nullptr;
+  double *lb = nullptr, *ub = nullptr;
+  float *v32 = nullptr;           // [N][n_pad] staged per-scenario vectors
+  float *vz32 = nullptr;          // [n_pad] staged shared vector
+  float *partial = nullptr;       // [nblocks][n_pad]
+  double *objp = nullptr;         // [nblocks]
+  double *w = nullptr, *q = nullptr, *dinv = nullptr;   // CG: B u, B p, M^{-1}
+  float *diag = nullptr;          // [N][n] diag(A~_s^T A~_s)
+  double *gam = nullptr, *tol = nullptr, *r0n = nullptr, *alpha = nullptr, *beta = nullptr;
+  double *gprev = nullptr, *aprev = nullptr;
+  int *act = nullptr, *act_next = nullptr, *cgcnt = nullptr, *cgi = nullptr;
+  int *err = nullptr;             // device error word of the row passes
+  unsigned int *cnt_s = nullptr;  // [N] per-scenario counters
+  double *dots = nullptr;         // [N][nchunk][4]
+  double *vpart = nullptr;        // [nchunk*N][8]
+  double *g = nullptr, *xt = nullptr, *xp = nullptr;   // PGD [n]
+  float *dose = nullptr;          // [N][m_act] (allocated on demand)
+  Ctl *ctl = nullptr;             // device control block
+  Ctl *ctl_host = nullptr;        // pinned mirror
+
+  std::vector<int32_t> kept_rows; // original row index of each device row
+  double lipschitz = 0.0;         // cached 2 lambda_max, 0 = not computed
+  bool state_valid = false;
+
+  // CUDA graphs (built on first use)
+  cudaGraphExec_t admm_exec = nullptr;
+  int admm_exec_obj = -1;         // use_obj flag the graph was built with
+  cudaGraphExec_t pgd_exec = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};
+
+int admm_solve(Plan* P, const rpt_admm_params* prm, const double* z0, const double* y0,
+               double* x_out, rpt_solve_info* info);
+int pgd_solve(Plan* P, const rpt_pgd_params* prm, const double* x0, double* x_out,
+              rpt_solve_info* info);
+int op_apply_normal(Plan* P, const double* v, double rho, double* u_out);
+int op_gradient(Plan* P, const double* x, double* g_out, double* f_out);
+int op_objective(Plan* P, const double* x, double* f_out, double* dose_out);
+int compute_lipschitz(Plan* P, double* L);
+int profile_row_pass(Plan* P, int mode, int reps, double* ms, double* bytes);
+void destroy_graphs(Plan* P);
+
+// error reporting (api.cu)
+void set_error(const std::string& msg);
+int cuda_fail(cudaError_t e, const char* what);
+
+}  // namespace rpt

@@ -1,0 +1,1233 @@
+// ADMM-BB and PGD on the device.
+//
+// ADMM-BB (Sec. 2.2).  One iteration k:
+//   a. residual pass   g_s = A~_s^T (A~_s x_s - p~)              (row pass, kResid)
+//      r_s = c_s - B_s x_s = -g_s - (rho/2)(x_s - z) - y_s/2     (App. A: B_s, c_s)
+//   b. CG on B_s x_s = c_s for all scenarios at once, warm-started from x_s
+//      (each CG step: one row pass kNormal + two vector kernels)
+//   c. z = P_box(mean_s(x_s + y_s/rho))                          (z-update)
+//   d. d = x - 1(x)z; BB step from dd = d - d_prev and dy = step_prev d_prev (Eq. 8)
+//   e. y_s += step d_s (Eq. 7); residuals and tolerances of Eq. 9; stop test.
+// All loops are device-side: a CUDA graph with a WHILE node for the ADMM
+// iteration whose body holds a nested WHILE node for CG; the conditions are
+// set by the finishing kernels.  Every loop is capped (max_iter, cg_max,
+// max_trials), so the graph always terminates.
+//
+// Vectors are float64; the row passes see them rounded to float32 (staged in
+// shared memory).  Dot products and norms are float64; the per-CTA partials of
+// a row pass are summed in a fixed order with compensated float32 sums.
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "plan.h"
+
+namespace rpt {
+namespace {
+
+constexpr int VT = kVecThreads;
+
+__device__ __forceinline__ double clampd(double v, double lo, double hi) {
+  return fmin(fmax(v, lo), hi);
+}
+
+// Fixed-order compensated sum of the row-pass partials of blocks [b0, b1) at column j.
+__device__ __forceinline__ double sum_partials(const float* __restrict__ part, int n_pad, int b0,
+                                               int b1, int j) {
+  float s = 0.f, c = 0.f;
+  for (int b = b0; b < b1; ++b) {
+    const float v = __ldcg(part + (size_t)b * n_pad + j);
+    float t, e;
+    two_sum(s, v, t, e);
+    s = t;
+    c += e;
+  }
+  return (double)s + (double)c;
+}
+
+// Last-block-done: every block calls it once (all threads); returns true in the
+// block that arrives last; that block also resets the counter.
+__device__ __forceinline__ bool last_block(unsigned int* counter, unsigned int total) {
+  __shared__ bool am_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned int prev = atomicAdd(counter, 1u);
+    am_last = (prev + 1u == total);
+    if (am_last) *counter = 0u;
+  }
+  __syncthreads();
+  if (am_last) __threadfence();
+  return am_last;
+}
+
+__device__ __forceinline__ void set_cond(unsigned long long h, int use, int value) {
+  if (use) cudaGraphSetConditional((cudaGraphConditionalHandle)h, value ? 1u : 0u);
+}
+
+// ---------------------------------------------------------------------------
+// ADMM-BB kernels
+// ---------------------------------------------------------------------------
+
+// grid (nchunk, N).  Initial state: z = P(z0), y = y0, x_s = z, d_prev = 0;
+// with resume: keep (z, x, y), d_prev = x - z.  Stages float32 x for the first
+// residual pass; sets the CG preconditioner for this rho.
+__global__ void k_admm_init(DevPlan P, const Ctl* __restrict__ C, const double* __restrict__ z0,
+                            const double* __restrict__ y0, int has_z0, int has_y0, int resume,
+                            const double* __restrict__ lb, const double* __restrict__ ub,
+                            const float* __restrict__ diag, double* dinv, double* x, double* y, double* z,
+                            double* dprev, float* v32) {
+  const int s = blockIdx.y, j = blockIdx.x * VT + threadIdx.x;
+  if (j < P.n) {
+    const size_t o = (size_t)s * P.n + j;
+    // Jacobi preconditioner of B_s = A~_s^T A~_s + (rho/2) I, or the identity
+    dinv[o] = C->precond ? 1.0 / ((double)diag[o] + 0.5 * C->rho) : 1.0;
+    if (!resume) {
+      const double zj = clampd(has_z0 ? z0[j] : 0.0, lb[j], ub[j]);
+      x[o] = zj;
+      y[o] = has_y0 ? y0[o] : 0.0;
+      dprev[o] = 0.0;
+      if (s == 0) z[j] = zj;
+      v32[(size_t)s * P.n_pad + j] = (float)zj;
+    } else {
+      dprev[o] = x[o] - z[j];
+      v32[(size_t)s * P.n_pad + j] = (float)x[o];
+    }
+  } else if (j < P.n_pad) {
+    v32[(size_t)s * P.n_pad + j] = 0.f;
+  }
+}
+
+// Subproblem solves (App. A: B_s x_s = c_s) by preconditioned conjugate
+// gradients in the Chronopoulos-Gear arrangement: each step applies B_s once,
+// to u = M^{-1} r (M = I, or the Jacobi diagonal of B_s), so the vector a row
+// pass needs is known before the step's reductions; both inner products of a
+// step are reduced explicitly (no algebraic norm updates).
+//   w = B u;  delta = (w, u);  beta = gamma / gamma_prev;
+//   alpha = gamma / (delta - beta gamma / alpha_prev)          (first step: gamma / delta)
+//   p = u + beta p;  q = w + beta q;  x += alpha p;  r -= alpha q;  u = M^{-1} r
+//   gamma = (r, u);  stop scenario s when ||r|| <= tol_s.
+
+// grid (nchunk, N).  r = -g - (rho/2)(x - z) - y/2 with g from the residual pass
+// (this is c_s - B_s x_s); u = M^{-1} r; per-scenario gamma, ||r||, tolerance, activity.
+__global__ void k_cg_init(DevPlan P, Ctl* C, const float* __restrict__ partial,
+                          const double* __restrict__ x, const double* __restrict__ y,
+                          const double* __restrict__ z, const double* __restrict__ dinv, double* r,
+                          double* u, float* v32, double* dots, int nchunk, double* gam, double* tol,
+                          double* r0n, int* act, int* cgi, unsigned int* cnt_s, unsigned long long hcg,
+                          int use_cond) {
+  __shared__ double sh[2 * 32];
+  const int s = blockIdx.y, j = blockIdx.x * VT + threadIdx.x;
+  const double rho = C->rho;
+  double v[2] = {0.0, 0.0};
+  if (j < P.n) {
+    const size_t o = (size_t)s * P.n + j;
+    const double gj = sum_partials(partial, P.n_pad, P.blk_first[s], P.blk_first[s + 1], j);
+    const double ri = -gj - 0.5 * rho * (x[o] - z[j]) - 0.5 * y[o];
+    const double ui = dinv[o] * ri;
+    r[o] = ri;
+    u[o] = ui;
+    v32[(size_t)s * P.n_pad + j] = (float)ui;
+    v[0] = ri * ui;
+    v[1] = ri * ri;
+  } else if (j < P.n_pad) {
+    v32[(size_t)s * P.n_pad + j] = 0.f;
+  }
+  block_sum_d<2>(v, sh);
+  if (threadIdx.x == 0) {
+    double* d = &dots[((size_t)s * nchunk + blockIdx.x) * 4];
+    d[0] = v[0];
+    d[1] = v[1];
+  }
+  if (!last_block(&cnt_s[s], gridDim.x)) return;
+  if (threadIdx.x == 0) {
+    double g = 0.0, rr = 0.0;
+    for (int c = 0; c < nchunk; ++c) {
+      g += __ldcg(&dots[((size_t)s * nchunk + c) * 4]);
+      rr += __ldcg(&dots[((size_t)s * nchunk + c) * 4 + 1]);
+    }
+    const double rn = sqrt(rr);
+    double t;
+    if (C->first) {
+      r0n[s] = rn;
+      t = C->cg_eta0 * rn;
+    } else {
+      t = fmax(C->cg_theta * 0.5 * rho * fmax(C->r_prim, C->eps_prim) / sqrt((double)P.N),
+               C->cg_floor * __ldcg(&r0n[s]));
+    }
+    gam[s] = g;
+    tol[s] = t;
+    cgi[s] = 0;
+    act[s] = (rn > t && g > 0.0 && C->cg_max > 0) ? 1 : 0;
+  }
+  if (!last_block(&C->cnt_init, P.N)) return;
+  if (threadIdx.x == 0) {
+    int any = 0;
+    for (int k = 0; k < P.N; ++k) any += __ldcg(&act[k]);
+    C->cg_any = any;
+    C->kcg = 0;
+    C->passes += 1;
+    set_cond(hcg, use_cond, any > 0);
+  }
+}
+
+// grid (nchunk, N).  w = B u = (row-pass partials) + (rho/2) u; delta = (w, u);
+// per scenario: beta and alpha of the step.
+__global__ void k_cg_dots(DevPlan P, Ctl* C, const float* __restrict__ partial,
+                          const double* __restrict__ u, double* w, double* dots, int nchunk,
+                          const double* __restrict__ gam, const double* __restrict__ gprev,
+                          const double* __restrict__ aprev, double* alpha, double* beta,
+                          const int* __restrict__ act, const int* __restrict__ cgi, unsigned int* cnt_s) {
+  __shared__ double sh[32];
+  const int s = blockIdx.y, j = blockIdx.x * VT + threadIdx.x;
+  if (__ldcg(&act[s]) == 0) return;
+  double v[1] = {0.0};
+  if (j < P.n) {
+    const size_t o = (size_t)s * P.n + j;
+    const double uj = u[o];
+    const double wj = sum_partials(partial, P.n_pad, P.blk_first[s], P.blk_first[s + 1], j) +
+                      0.5 * C->rho * uj;
+    w[o] = wj;
+    v[0] = wj * uj;
+  }
+  block_sum_d<1>(v, sh);
+  if (threadIdx.x == 0) dots[((size_t)s * nchunk + blockIdx.x) * 4 + 2] = v[0];
+  if (!last_block(&cnt_s[s], gridDim.x)) return;
+  if (threadIdx.x == 0) {
+    double delta = 0.0;
+    for (int c = 0; c < nchunk; ++c) delta += __ldcg(&dots[((size_t)s * nchunk + c) * 4 + 2]);
+    const double g = __ldcg(&gam[s]);
+    const bool first = __ldcg(&cgi[s]) == 0;
+    const double b = first ? 0.0 : g / __ldcg(&gprev[s]);
+    const double den = first ? delta : delta - b * g / __ldcg(&aprev[s]);
+    const double a = (den > 0.0 && isfinite(den) && isfinite(b)) ? g / den : 0.0;
+    alpha[s] = a;
+    beta[s] = b;
+  }
+}
+
+// grid (nchunk, N).  p = u + beta p; q = w + beta q; x += alpha p; r -= alpha q;
+// u = M^{-1} r (staged); gamma = (r, u), ||r||; activity; loop condition.
+__global__ void k_cg_update(DevPlan P, Ctl* C, double* x, double* r, double* u, const double* __restrict__ w,
+                            double* p, double* q, const double* __restrict__ dinv, float* v32,
+                            double* dots, int nchunk, const double* __restrict__ alpha,
+                            const double* __restrict__ beta, double* gam, double* gprev, double* aprev,
+                            const double* __restrict__ tol, int* act, int* act_next, int* cgi, int* cgcnt,
+                            unsigned int* cnt_s, unsigned long long hcg, int use_cond) {
+  __shared__ double sh[2 * 32];
+  const int s = blockIdx.y, j = blockIdx.x * VT + threadIdx.x;
+  const int any = __ldcg(&C->cg_any);
+  if (__ldcg(&act[s]) == 0) return;
+  const double a = __ldcg(&alpha[s]);
+  const bool first = __ldcg(&cgi[s]) == 0;
+  double v[2] = {0.0, 0.0};
+  if (j < P.n) {
+    const size_t o = (size_t)s * P.n + j;
+    const double b = __ldcg(&beta[s]);
+    const double pj = first ? u[o] : fma(b, p[o], u[o]);
+    const double qj = first ? w[o] : fma(b, q[o], w[o]);
+    p[o] = pj;
+    q[o] = qj;
+    x[o] = fma(a, pj, x[o]);
+    const double rj = fma(-a, qj, r[o]);
+    const double uj = dinv[o] * rj;
+    r[o] = rj;
+    u[o] = uj;
+    v32[(size_t)s * P.n_pad + j] = (float)uj;
+    v[0] = rj * uj;
+    v[1] = rj * rj;
+  }
+  block_sum_d<2>(v, sh);
+  if (threadIdx.x == 0) {
+    double* d = &dots[((size_t)s * nchunk + blockIdx.x) * 4];
+    d[0] = v[0];
+    d[1] = v[1];
+  }
+  if (last_block(&cnt_s[s], gridDim.x)) {
+    if (threadIdx.x == 0) {
+      double g = 0.0, rr = 0.0;
+      for (int c = 0; c < nchunk; ++c) {
+        g += __ldcg(&dots[((size_t)s * nchunk + c) * 4]);
+        rr += __ldcg(&dots[((size_t)s * nchunk + c) * 4 + 1]);
+      }
+      gprev[s] = __ldcg(&gam[s]);
+      aprev[s] = a;
+      gam[s] = g;
+      cgi[s] += 1;
+      cgcnt[s] += 1;
+      act_next[s] = (a > 0.0 && g > 0.0 && sqrt(rr) > __ldcg(&tol[s])) ? 1 : 0;
+    }
+    if (!last_block(&C->cnt_upd, (unsigned int)any)) return;
+    if (threadIdx.x == 0) {
+      int na = 0;
+      for (int k = 0; k < P.N; ++k) {
+        if (act[k]) {
+          C->cg_total += 1;
+          act[k] = __ldcg(&act_next[k]);
+          na += act[k];
+        }
+      }
+      C->cg_any = na;
+      C->kcg += 1;
+      C->cg_steps += 1;
+      C->passes += 1;
+      set_cond(hcg, use_cond, na > 0 && C->kcg < C->cg_max);
+    }
+  }
+}
+
+// grid (nchunk).  z_new = P_box(mean_s(x_s + y_s/rho)) [std] or P_box(mean_s x_s) [lit].
+__global__ void k_admm_z(DevPlan P, Ctl* C, const double* __restrict__ x, const double* __restrict__ y,
+                         const double* __restrict__ z, double* znew, const double* __restrict__ lb,
+                         const double* __restrict__ ub, double* vpart) {
+  __shared__ double sh[2 * 32];
+  const int j = blockIdx.x * VT + threadIdx.x;
+  double v[2] = {0.0, 0.0};
+  if (j < P.n) {
+    const double ir = C->inv_rho;
+    const bool std_form = (C->z_mode == 0);
+    double acc = 0.0;
+    for (int s = 0; s < P.N; ++s) {
+      const size_t o = (size_t)s * P.n + j;
+      acc += std_form ? fma(y[o], ir, x[o]) : x[o];
+    }
+    const double zn = clampd(acc / (double)P.N, lb[j], ub[j]);
+    znew[j] = zn;
+    const double dz = zn - z[j];
+    v[0] = zn * zn;
+    v[1] = dz * dz;
+  }
+  block_sum_d<2>(v, sh);
+  if (threadIdx.x == 0) {
+    vpart[blockIdx.x * 8 + 0] = v[0];
+    vpart[blockIdx.x * 8 + 1] = v[1];
+  }
+  if (!last_block(&C->cnt_z, gridDim.x)) return;
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0;
+    for (int c = 0; c < (int)gridDim.x; ++c) {
+      a += __ldcg(&vpart[c * 8 + 0]);
+      b += __ldcg(&vpart[c * 8 + 1]);
+    }
+    C->sz2 = a;
+    C->dz2 = b;
+  }
+}
+
+// grid (nchunk, N).  d = x - z_new; BB sums dd'd_prev and ||dd||^2; ||d||^2, ||x||^2.
+// Last block: BB step (Eq. 8), r_prim, r_dual, eps_prim (Eq. 9).
+__global__ void k_admm_d(DevPlan P, Ctl* C, const double* __restrict__ x,
+                         const double* __restrict__ znew, const double* __restrict__ dprev, double* d,
+                         double* vpart, int nchunk) {
+  __shared__ double sh[4 * 32];
+  const int s = blockIdx.y, j = blockIdx.x * VT + threadIdx.x;
+  double v[4] = {0.0, 0.0, 0.0, 0.0};
+  if (j < P.n) {
+    const size_t o = (size_t)s * P.n + j;
+    const double xj = x[o];
+    const double dj = xj - znew[j];
+    const double dp = dprev[o];
+    const double dd = dj - dp;
+    d[o] = dj;
+    v[0] = dd * dp;
+    v[1] = dd * dd;
+    v[2] = dj * dj;
+    v[3] = xj * xj;
+  }
+  block_sum_d<4>(v, sh);
+  const int blk = s * nchunk + blockIdx.x;
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < 4; ++k) vpart[(size_t)(nchunk + blk) * 8 + k] = v[k];
+  }
+  if (!last_block(&C->cnt_d, gridDim.x * gridDim.y)) return;
+  if (threadIdx.x == 0) {
+    double S[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int b = 0; b < (int)(gridDim.x * gridDim.y); ++b)
+      for (int k = 0; k < 4; ++k) S[k] += __ldcg(&vpart[(size_t)(nchunk + b) * 8 + k]);
+    const double rho = C->rho;
+    double step = rho;
+    if (C->bb_mode != 2 && C->have_prev && S[1] > 0.0) {
+      const double bb = -C->step_prev * S[0] / S[1];
+      if (isfinite(bb) && bb > 0.0) {
+        step = bb;
+        if (C->bb_mode == 1) step = fmin(fmax(step, rho / C->bb_kappa), C->bb_kappa * rho);
+      }
+    }
+    const double sN = sqrt((double)P.N);
+    C->step = step;
+    C->r_prim = sqrt(S[2]);
+    C->r_dual = sN * rho * sqrt(C->dz2);
+    C->eps_prim = C->eps_abs * sqrt((double)P.N * P.n) +
+                  C->eps_rel * fmax(sqrt(S[3]), sN * sqrt(C->sz2));
+  }
+}
+
+// grid (nchunk, N).  y += step d (Eq. 7); z <- z_new; d_prev <- d; stage x and z.
+// Last block: eps_dual, stop test, next iteration's condition.
+__global__ void k_admm_y(DevPlan P, Ctl* C, const double* __restrict__ x, double* y, double* z,
+                         const double* __restrict__ znew, const double* __restrict__ d, double* dprev,
+                         float* v32, float* vz32, double* vpart, int nchunk, unsigned long long hadmm,
+                         int use_cond) {
+  __shared__ double sh[32];
+  const int s = blockIdx.y, j = blockIdx.x * VT + threadIdx.x;
+  const double step = __ldcg(&C->step);
+  double v[1] = {0.0};
+  if (j < P.n) {
+    const size_t o = (size_t)s * P.n + j;
+    const double dj = d[o];
+    const double yn = fma(step, dj, y[o]);
+    y[o] = yn;
+    dprev[o] = dj;
+    v32[(size_t)s * P.n_pad + j] = (float)x[o];
+    v[0] = yn * yn;
+    if (s == 0) {
+      const double zn = znew[j];
+      z[j] = zn;
+      vz32[j] = (float)zn;
+    }
+  } else if (s == 0 && j < P.n_pad) {
+    vz32[j] = 0.f;
+  }
+  block_sum_d<1>(v, sh);
+  const int blk = s * nchunk + blockIdx.x;
+  if (threadIdx.x == 0) vpart[(size_t)(nchunk + blk) * 8 + 4] = v[0];
+  if (!last_block(&C->cnt_y, gridDim.x * gridDim.y)) return;
+  if (threadIdx.x == 0) {
+    double Y = 0.0;
+    for (int b = 0; b < (int)(gridDim.x * gridDim.y); ++b) Y += __ldcg(&vpart[(size_t)(nchunk + b) * 8 + 4]);
+    C->eps_dual = C->eps_abs * sqrt((double)P.N * P.n) + C->eps_rel * sqrt(Y);
+    const int conv = (C->r_prim <= C->eps_prim) && (C->r_dual <= C->eps_dual);
+    C->k += 1;
+    C->have_prev = 1;
+    C->step_prev = step;
+    C->first = 0;
+    if (!(isfinite(C->r_prim) && isfinite(C->r_dual) && isfinite(Y))) C->diverged = 1;
+    C->status = conv;
+    if (!C->use_obj) {
+      C->stop = conv || C->diverged || C->k >= C->max_iter;
+      set_cond(hadmm, use_cond, !C->stop);
+    }
+  }
+}
+
+// <<<1, 256>>>.  Objective of z (after a kObj row pass): optional relative-change test
+// AND-ed with Eq. 9 (Sec. 2.3).
+__global__ void k_admm_obj(Ctl* C, const double* __restrict__ objp, int nblocks,
+                           unsigned long long hadmm, int use_cond) {
+  __shared__ double sh[32];
+  double v[1] = {0.0};
+  for (int b = threadIdx.x; b < nblocks; b += blockDim.x) v[0] += objp[b];
+  block_sum_d<1>(v, sh);
+  if (threadIdx.x == 0) {
+    const double f = v[0] + C->const_term;
+    const int conv_obj = fabs(C->f_prev - f) <= C->tol_obj * fmax(fabs(f), 1e-300);
+    C->f_prev = f;
+    C->f_cur = f;
+    C->passes += 1;
+    C->status = C->status && conv_obj;
+    C->stop = C->status || C->diverged || C->k >= C->max_iter;
+    set_cond(hadmm, use_cond, !C->stop);
+  }
+}
+
+// <<<1, 256>>>.  f = sum of block objectives + constant.
+__global__ void k_final_obj(Ctl* C, const double* __restrict__ objp, int nblocks, int pgd) {
+  __shared__ double sh[32];
+  double v[1] = {0.0};
+  for (int b = threadIdx.x; b < nblocks; b += blockDim.x) v[0] += objp[b];
+  block_sum_d<1>(v, sh);
+  if (threadIdx.x == 0) {
+    C->f_cur = v[0] + C->const_term;
+    C->passes += 1;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// PGD kernels (Sec. 2.1)
+// ---------------------------------------------------------------------------
+
+// grid (nchunk).  x = P(x0); stage float32 x (shared by all scenarios).
+__global__ void k_pgd_init(DevPlan P, const double* __restrict__ x0, int has_x0,
+                           const double* __restrict__ lb, const double* __restrict__ ub, double* x,
+                           float* vz32) {
+  const int j = blockIdx.x * VT + threadIdx.x;
+  if (j < P.n) {
+    const double xj = clampd(has_x0 ? x0[j] : 0.0, lb[j], ub[j]);
+    x[j] = xj;
+    vz32[j] = (float)xj;
+  } else if (j < P.n_pad) {
+    vz32[j] = 0.f;
+  }
+}
+
+// grid (nchunk).  g = 2 sum_s A~_s^T (A~_s x - p~) (Eq. 4 summed over s) from a kResid
+// pass over all scenarios; f(x); start the Armijo trials at t = alpha.
+__global__ void k_pgd_grad(DevPlan P, Ctl* C, const float* __restrict__ partial,
+                           const double* __restrict__ objp, double* g, unsigned long long htrial,
+                           int use_cond) {
+  __shared__ double sh[32];
+  const int j = blockIdx.x * VT + threadIdx.x;
+  if (j < P.n) g[j] = 2.0 * sum_partials(partial, P.n_pad, 0, P.nblocks, j);
+  if (!last_block(&C->cnt_pg, gridDim.x)) return;
+  double v[1] = {0.0};
+  for (int b = threadIdx.x; b < P.nblocks; b += blockDim.x) v[0] += __ldcg(&objp[b]);
+  block_sum_d<1>(v, sh);
+  if (threadIdx.x == 0) {
+    C->fx = v[0] + C->const_term;
+    C->t = C->alpha;
+    C->trial = 0;
+    C->accepted = 0;
+    C->passes += 1;
+    set_cond(htrial, use_cond, 1);
+  }
+}
+
+// grid (nchunk).  Trial point x_t = P(x - t g), staged; g'(x_t - x).
+__global__ void k_pgd_trial(DevPlan P, Ctl* C, const double* __restrict__ x,
+                            const double* __restrict__ g, const double* __restrict__ lb,
+                            const double* __restrict__ ub, double* xt, float* vt32, double* vpart) {
+  __shared__ double sh[32];
+  const int j = blockIdx.x * VT + threadIdx.x;
+  const double t = __ldcg(&C->t);
+  double v[1] = {0.0};
+  if (j < P.n) {
+    const double xj = x[j], gj = g[j];
+    const double xn = clampd(xj - t * gj, lb[j], ub[j]);
+    xt[j] = xn;
+    vt32[j] = (float)xn;
+    v[0] = gj * (xn - xj);
+  } else if (j < P.n_pad) {
+    vt32[j] = 0.f;
+  }
+  block_sum_d<1>(v, sh);
+  if (threadIdx.x == 0) vpart[blockIdx.x * 8] = v[0];
+  if (!last_block(&C->cnt_pt, gridDim.x)) return;
+  if (threadIdx.x == 0) {
+    double a = 0.0;
+    for (int c = 0; c < (int)gridDim.x; ++c) a += __ldcg(&vpart[c * 8]);
+    C->gd = a;
+  }
+}
+
+// <<<1, 256>>>.  Sufficient-decrease test (Eq. 3 read as f(x_t) <= f(x) + beta g'(x_t - x)).
+__global__ void k_pgd_accept(Ctl* C, const double* __restrict__ objp, int nblocks,
+                             unsigned long long htrial, int use_cond) {
+  __shared__ double sh[32];
+  double v[1] = {0.0};
+  for (int b = threadIdx.x; b < nblocks; b += blockDim.x) v[0] += objp[b];
+  block_sum_d<1>(v, sh);
+  if (threadIdx.x == 0) {
+    const double ft = v[0] + C->const_term;
+    C->ft = ft;
+    C->trials_total += 1;
+    C->passes += 1;
+    int more = 0;
+    if (ft <= C->fx + C->beta_a * C->gd) {
+      C->accepted = 1;
+    } else {
+      C->t *= C->gamma;
+      C->trial += 1;
+      if (C->trial >= C->max_trials) C->failed = 1;
+      else more = 1;
+    }
+    set_cond(htrial, use_cond, more);
+  }
+}
+
+// grid (nchunk).  Accept x_t, stage it; stopping rule on the relative change of f.
+__global__ void k_pgd_finish(DevPlan P, Ctl* C, double* x, const double* __restrict__ xt,
+                             float* vz32, unsigned long long houter, int use_cond) {
+  const int j = blockIdx.x * VT + threadIdx.x;
+  const int acc = __ldcg(&C->accepted);
+  if (acc && j < P.n) {
+    const double xn = xt[j];
+    x[j] = xn;
+    vz32[j] = (float)xn;
+  }
+  if (!last_block(&C->cnt_red, gridDim.x)) return;
+  if (threadIdx.x == 0) {
+    int stop = 0;
+    C->pouter += 1;
+    if (acc) {
+      const double fx = C->fx, ft = C->ft;
+      const double rel = fabs(fx - ft) / fmax(fabs(fx), 1e-300);
+      C->pk += 1;
+      C->fx = ft;
+      C->f_cur = ft;
+      C->step = C->t;
+      stop = (rel <= C->tol_df) || (C->f_target > 0.0 && ft <= C->f_target) ||
+             (C->pk >= C->pgd_max_iter) || !isfinite(ft);
+      if (!isfinite(ft)) C->diverged = 1;
+      C->status = (rel <= C->tol_df) || (C->f_target > 0.0 && ft <= C->f_target);
+    } else {
+      stop = 1;
+      C->f_cur = C->fx;
+    }
+    C->stop = stop;
+    set_cond(houter, use_cond, !stop);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// operator kernels
+// ---------------------------------------------------------------------------
+
+// grid (nchunk, N): out_s = partials of scenario s + half_rho * v_s.
+__global__ void k_reduce_scen(DevPlan P, const float* __restrict__ partial,
+                              const double* __restrict__ v, double half_rho, double* out) {
+  const int s = blockIdx.y, j = blockIdx.x * VT + threadIdx.x;
+  if (j >= P.n) return;
+  const size_t o = (size_t)s * P.n + j;
+  out[o] = sum_partials(partial, P.n_pad, P.blk_first[s], P.blk_first[s + 1], j) + half_rho * v[o];
+}
+
+// grid (nchunk): out = scale * sum over all blocks.
+__global__ void k_reduce_all(DevPlan P, const float* __restrict__ partial, double scale, double* out) {
+  const int j = blockIdx.x * VT + threadIdx.x;
+  if (j >= P.n) return;
+  out[j] = scale * sum_partials(partial, P.n_pad, 0, P.nblocks, j);
+}
+
+// ---------------------------------------------------------------------------
+// host-side launch helpers: one code path that either launches into a stream
+// or appends kernel nodes to a CUDA graph
+// ---------------------------------------------------------------------------
+
+struct Exec {
+  cudaStream_t st = nullptr;       // stream mode
+  cudaGraph_t g = nullptr;         // graph mode
+  cudaGraphNode_t last = nullptr;
+  cudaError_t err = cudaSuccess;
+
+  bool graph() const { return g != nullptr; }
+
+  void kernel(void* fn, dim3 grid, dim3 block, size_t smem, void** args) {
+    if (err != cudaSuccess) return;
+    if (!graph()) {
+      err = cudaLaunchKernel(fn, grid, block, args, smem, st);
+      return;
+    }
+    cudaKernelNodeParams kp{};
+    kp.func = fn;
+    kp.gridDim = grid;
+    kp.blockDim = block;
+    kp.sharedMemBytes = (unsigned int)smem;
+    kp.kernelParams = args;
+    cudaGraphNode_t node;
+    err = cudaGraphAddKernelNode(&node, g, last ? &last : nullptr, last ? 1 : 0, &kp);
+    if (err == cudaSuccess) last = node;
+  }
+
+  // Append a WHILE node; returns an Exec that appends to its body.
+  Exec while_body(cudaGraphConditionalHandle h) {
+    Exec body;
+    if (err != cudaSuccess) {
+      body.err = err;
+      return body;
+    }
+    cudaGraphNodeParams np{};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    err = cudaGraphAddNode(&node, g, last ? &last : nullptr, nullptr, last ? 1 : 0, &np);
+    if (err != cudaSuccess) {
+      body.err = err;
+      return body;
+    }
+    last = node;
+    body.g = np.conditional.phGraph_out[0];
+    return body;
+  }
+};
+
+template <typename... A>
+void launch(Exec& e, void (*fn)(A...), dim3 grid, dim3 block, size_t smem, A... args) {
+  void* ptrs[] = {(void*)&args...};
+  e.kernel((void*)fn, grid, block, smem, ptrs);
+}
+
+void rowpass(Exec& e, Plan* P, int mode, const float* v, int v_stride, const int* active,
+             float* dose = nullptr) {
+  const DevPlan& dp = P->dp;
+  void* fn = rowpass_kernel(dp, mode);
+  float* partial = P->partial;
+  double* objp = P->objp;
+  void* args[] = {(void*)&dp, (void*)&v, (void*)&v_stride, (void*)&active,
+                  (void*)&partial, (void*)&objp, (void*)&dose};
+  e.kernel(fn, dim3(dp.grid), dim3(rowpass_threads(dp)), rowpass_smem(dp, mode), args);
+}
+
+// ---- ADMM pieces ---------------------------------------------------------------
+
+void admm_iteration_head(Exec& e, Plan* P, unsigned long long hcg, int uc) {
+  const DevPlan& dp = P->dp;
+  dim3 g2(P->nchunk, dp.N);
+  rowpass(e, P, kResid, P->v32, dp.n_pad, nullptr);
+  launch(e, k_cg_init, g2, dim3(VT), 0, dp, P->ctl, (const float*)P->partial, (const double*)P->x,
+         (const double*)P->y, (const double*)P->z, (const double*)P->dinv, P->r, P->u, P->v32, P->dots,
+         P->nchunk, P->gam, P->tol, P->r0n, P->act, P->cgi, P->cnt_s, hcg, uc);
+}
+
+void cg_body(Exec& e, Plan* P, unsigned long long hcg, int uc) {
+  const DevPlan& dp = P->dp;
+  dim3 g2(P->nchunk, dp.N);
+  rowpass(e, P, kNormal, P->v32, dp.n_pad, P->act);
+  launch(e, k_cg_dots, g2, dim3(VT), 0, dp, P->ctl, (const float*)P->partial, (const double*)P->u,
+         P->w, P->dots, P->nchunk, (const double*)P->gam, (const double*)P->gprev,
+         (const double*)P->aprev, P->alpha, P->beta, (const int*)P->act, (const int*)P->cgi, P->cnt_s);
+  launch(e, k_cg_update, g2, dim3(VT), 0, dp, P->ctl, P->x, P->r, P->u, (const double*)P->w, P->p,
+         P->q, (const double*)P->dinv, P->v32, P->dots, P->nchunk, (const double*)P->alpha,
+         (const double*)P->beta, P->gam, P->gprev, P->aprev, (const double*)P->tol, P->act,
+         P->act_next, P->cgi, P->cgcnt, P->cnt_s, hcg, uc);
+}
+
+void admm_iteration_tail(Exec& e, Plan* P, int use_obj, unsigned long long hadmm, int uc) {
+  const DevPlan& dp = P->dp;
+  dim3 g1(P->nchunk), g2(P->nchunk, dp.N);
+  launch(e, k_admm_z, g1, dim3(VT), 0, dp, P->ctl, (const double*)P->x, (const double*)P->y,
+         (const double*)P->z, P->znew, (const double*)P->lb, (const double*)P->ub, P->vpart);
+  launch(e, k_admm_d, g2, dim3(VT), 0, dp, P->ctl, (const double*)P->x, (const double*)P->znew,
+         (const double*)P->dprev, P->d, P->vpart, P->nchunk);
+  launch(e, k_admm_y, g2, dim3(VT), 0, dp, P->ctl, (const double*)P->x, P->y, P->z,
+         (const double*)P->znew, (const double*)P->d, P->dprev, P->v32, P->vz32, P->vpart, P->nchunk,
+         hadmm, use_obj ? 0 : uc);
+  if (use_obj) {
+    rowpass(e, P, kObj, P->vz32, 0, nullptr);
+    launch(e, k_admm_obj, dim3(1), dim3(256), 0, P->ctl, (const double*)P->objp, dp.nblocks, hadmm, uc);
+  }
+}
+
+void admm_tail_final(Exec& e, Plan* P) {
+  rowpass(e, P, kObj, P->vz32, 0, nullptr);
+  launch(e, k_final_obj, dim3(1), dim3(256), 0, P->ctl, (const double*)P->objp, P->dp.nblocks, 0);
+}
+
+cudaError_t build_admm_graph(Plan* P, int use_obj, double* z0d, double* y0d) {
+  (void)z0d;
+  (void)y0d;
+  cudaGraph_t g = nullptr;
+  cudaError_t err = cudaGraphCreate(&g, 0);
+  if (err != cudaSuccess) return err;
+  cudaGraphConditionalHandle hadmm = 0, hcg = 0;
+  err = cudaGraphConditionalHandleCreate(&hadmm, g, 1, cudaGraphCondAssignDefault);
+  Exec top;
+  top.g = g;
+  top.err = err;
+  Exec body = top.while_body(hadmm);
+  if (body.err == cudaSuccess)
+    body.err = cudaGraphConditionalHandleCreate(&hcg, body.g, 0, cudaGraphCondAssignDefault);
+  admm_iteration_head(body, P, (unsigned long long)hcg, 1);
+  Exec cg = body.while_body(hcg);
+  cg_body(cg, P, (unsigned long long)hcg, 1);
+  if (cg.err != cudaSuccess) body.err = cg.err;
+  admm_iteration_tail(body, P, use_obj, (unsigned long long)hadmm, 1);
+  if (body.err != cudaSuccess) top.err = body.err;
+  admm_tail_final(top, P);
+  err = top.err;
+  if (err == cudaSuccess) {
+    if (P->admm_exec) cudaGraphExecDestroy(P->admm_exec);
+    P->admm_exec = nullptr;
+    err = cudaGraphInstantiate(&P->admm_exec, g, 0);
+    if (err == cudaSuccess) P->admm_exec_obj = use_obj;
+  }
+  cudaGraphDestroy(g);
+  return err;
+}
+
+// ---- PGD pieces ------------------------------------------------------------------
+
+void pgd_head(Exec& e, Plan* P, unsigned long long htrial, int uc) {
+  const DevPlan& dp = P->dp;
+  rowpass(e, P, kResid, P->vz32, 0, nullptr);
+  launch(e, k_pgd_grad, dim3(P->nchunk), dim3(VT), 0, dp, P->ctl, (const float*)P->partial,
+         (const double*)P->objp, P->g, htrial, uc);
+}
+
+void pgd_trial(Exec& e, Plan* P, unsigned long long htrial, int uc) {
+  const DevPlan& dp = P->dp;
+  launch(e, k_pgd_trial, dim3(P->nchunk), dim3(VT), 0, dp, P->ctl, (const double*)P->xp,
+         (const double*)P->g, (const double*)P->lb, (const double*)P->ub, P->xt, P->v32, P->vpart);
+  rowpass(e, P, kObj, P->v32, 0, nullptr);
+  launch(e, k_pgd_accept, dim3(1), dim3(256), 0, P->ctl, (const double*)P->objp, dp.nblocks, htrial, uc);
+}
+
+void pgd_tail(Exec& e, Plan* P, unsigned long long houter, int uc) {
+  launch(e, k_pgd_finish, dim3(P->nchunk), dim3(VT), 0, P->dp, P->ctl, P->xp, (const double*)P->xt,
+         P->vz32, houter, uc);
+}
+
+cudaError_t build_pgd_graph(Plan* P) {
+  cudaGraph_t g = nullptr;
+  cudaError_t err = cudaGraphCreate(&g, 0);
+  if (err != cudaSuccess) return err;
+  cudaGraphConditionalHandle hout = 0, htr = 0;
+  err = cudaGraphConditionalHandleCreate(&hout, g, 1, cudaGraphCondAssignDefault);
+  Exec top;
+  top.g = g;
+  top.err = err;
+  Exec body = top.while_body(hout);
+  if (body.err == cudaSuccess)
+    body.err = cudaGraphConditionalHandleCreate(&htr, body.g, 0, cudaGraphCondAssignDefault);
+  pgd_head(body, P, (unsigned long long)htr, 1);
+  Exec tr = body.while_body(htr);
+  pgd_trial(tr, P, (unsigned long long)htr, 1);
+  if (tr.err != cudaSuccess) body.err = tr.err;
+  pgd_tail(body, P, (unsigned long long)hout, 1);
+  if (body.err != cudaSuccess) top.err = body.err;
+  err = top.err;
+  if (err == cudaSuccess) {
+    if (P->pgd_exec) cudaGraphExecDestroy(P->pgd_exec);
+    P->pgd_exec = nullptr;
+    err = cudaGraphInstantiate(&P->pgd_exec, g, 0);
+  }
+  cudaGraphDestroy(g);
+  return err;
+}
+
+// RPT_TIMEOUT if a row pass recorded a bounded wait that ran out (and clear it).
+int check_err(Plan* P) {
+  int h = 0;
+  cudaError_t e = cudaMemcpyAsync(&h, P->err, sizeof(int), cudaMemcpyDeviceToHost, P->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(P->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "read error word");
+  if (h != 0) {
+    cudaMemsetAsync(P->err, 0, sizeof(int), P->stream);
+    set_error("a row-pass pipeline wait ran out (code " + std::to_string(h) + ")");
+    return RPT_TIMEOUT;
+  }
+  return RPT_OK;
+}
+
+cudaError_t read_ctl(Plan* P) {
+  cudaError_t e = cudaMemcpyAsync(P->ctl_host, P->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, P->stream);
+  if (e != cudaSuccess) return e;
+  return cudaStreamSynchronize(P->stream);
+}
+
+}  // namespace
+
+// ===========================================================================
+// entry points
+// ===========================================================================
+
+void destroy_graphs(Plan* P) {
+  if (P->admm_exec) cudaGraphExecDestroy(P->admm_exec);
+  if (P->pgd_exec) cudaGraphExecDestroy(P->pgd_exec);
+  P->admm_exec = nullptr;
+  P->pgd_exec = nullptr;
+}
+
+int admm_solve(Plan* P, const rpt_admm_params* prm, const double* z0, const double* y0,
+               double* x_out, rpt_solve_info* info) {
+  const DevPlan& dp = P->dp;
+  const int n = dp.n, N = dp.N;
+  double rho = prm->rho > 0 ? prm->rho : prm->rho_scale * P->stats.default_rho;
+  if (!(rho > 0) || !std::isfinite(rho)) {
+    set_error("rho must be positive and finite (default rule gave " + std::to_string(rho) + ")");
+    return RPT_EINVAL;
+  }
+  if (prm->max_iter < 1 || prm->cg_max < 0 || prm->eps_abs < 0 || prm->eps_rel < 0 ||
+      prm->bb_mode < 0 || prm->bb_mode > 2 || prm->z_mode < 0 || prm->z_mode > 1 ||
+      prm->cg_precond < 0 || prm->cg_precond > 1 ||
+      !(prm->bb_kappa >= 1.0) || !(prm->cg_theta > 0) || !(prm->cg_eta0 > 0) ||
+      !(prm->cg_floor_rel >= 0) || std::isnan(prm->tol_obj)) {
+    set_error("invalid ADMM parameters");
+    return RPT_EINVAL;
+  }
+  if (prm->resume && !P->state_valid) {
+    set_error("resume requested but the plan holds no ADMM state");
+    return RPT_EINVAL;
+  }
+  for (int pass = 0; pass < 2; ++pass) {
+    const double* a = pass ? y0 : z0;
+    const size_t cnt = pass ? (size_t)N * n : (size_t)n;
+    if (a)
+      for (size_t i = 0; i < cnt; ++i)
+        if (!std::isfinite(a[i])) {
+          set_error(pass ? "y0 has a non-finite entry" : "z0 has a non-finite entry");
+          return RPT_EINVAL;
+        }
+  }
+  const int use_obj = std::isfinite(prm->tol_obj) ? 1 : 0;
+  cudaStream_t st = P->stream;
+  cudaError_t e;
+  // inputs: z0 -> znew (scratch until the first z-update), y0 -> u (scratch until CG)
+  if (z0 && (e = cudaMemcpyAsync(P->znew, z0, sizeof(double) * n, cudaMemcpyHostToDevice, st)))
+    return cuda_fail(e, "copy z0");
+  if (y0 && (e = cudaMemcpyAsync(P->u, y0, sizeof(double) * N * n, cudaMemcpyHostToDevice, st)))
+    return cuda_fail(e, "copy y0");
+  Ctl& c = *P->ctl_host;
+  std::memset(&c, 0, sizeof(Ctl));
+  c.rho = rho;
+  c.inv_rho = 1.0 / rho;
+  c.eps_abs = prm->eps_abs;
+  c.eps_rel = prm->eps_rel;
+  c.bb_kappa = prm->bb_kappa;
+  c.cg_theta = prm->cg_theta;
+  c.cg_eta0 = prm->cg_eta0;
+  c.cg_floor = prm->cg_floor_rel;
+  c.tol_obj = prm->tol_obj;
+  c.const_term = P->stats.const_term;
+  c.max_iter = prm->max_iter;
+  c.cg_max = prm->cg_max;
+  c.bb_mode = prm->bb_mode;
+  c.z_mode = prm->z_mode;
+  c.precond = prm->cg_precond;
+  c.use_obj = use_obj;
+  c.first = 1;
+  c.step_prev = rho;
+  c.step = rho;
+  c.f_prev = HUGE_VAL;
+  if ((e = cudaMemcpyAsync(P->ctl, &c, sizeof(Ctl), cudaMemcpyHostToDevice, st)))
+    return cuda_fail(e, "upload control block");
+  if ((e = cudaMemsetAsync(P->cgcnt, 0, sizeof(int) * N, st))) return cuda_fail(e, "memset");
+  if ((e = cudaEventRecord(P->ev0, st))) return cuda_fail(e, "event");
+  {
+    Exec ex;
+    ex.st = st;
+    launch(ex, k_admm_init, dim3(P->nchunk, N), dim3(VT), 0, dp, (const Ctl*)P->ctl,
+           (const double*)P->znew, (const double*)P->u, z0 ? 1 : 0, y0 ? 1 : 0, prm->resume ? 1 : 0,
+           (const double*)P->lb, (const double*)P->ub, (const float*)P->diag, P->dinv, P->x, P->y,
+           P->z, P->dprev, P->v32);
+    if (ex.err) return cuda_fail(ex.err, "launch init");
+  }
+  if (prm->use_graph) {
+    if (!P->admm_exec || P->admm_exec_obj != use_obj) {
+      if ((e = build_admm_graph(P, use_obj, nullptr, nullptr))) return cuda_fail(e, "build ADMM graph");
+    }
+    if ((e = cudaGraphLaunch(P->admm_exec, st))) return cuda_fail(e, "launch ADMM graph");
+  } else {
+    const int every = prm->check_every > 0 ? prm->check_every : 1;
+    for (;;) {
+      Exec ex;
+      ex.st = st;
+      admm_iteration_head(ex, P, 0, 0);
+      if (ex.err) return cuda_fail(ex.err, "launch");
+      if ((e = read_ctl(P))) return cuda_fail(e, "read control");
+      while (P->ctl_host->cg_any > 0 && P->ctl_host->kcg < prm->cg_max) {
+        cg_body(ex, P, 0, 0);
+        if (ex.err) return cuda_fail(ex.err, "launch");
+        if ((e = read_ctl(P))) return cuda_fail(e, "read control");
+      }
+      admm_iteration_tail(ex, P, use_obj, 0, 0);
+      if (ex.err) return cuda_fail(ex.err, "launch");
+      const int k_done = P->ctl_host->k + 1;
+      if (k_done % every == 0 || k_done >= prm->max_iter) {
+        if ((e = read_ctl(P))) return cuda_fail(e, "read control");
+        if (P->ctl_host->stop) break;
+      }
+    }
+    Exec ex;
+    ex.st = st;
+    admm_tail_final(ex, P);
+    if (ex.err) return cuda_fail(ex.err, "launch");
+  }
+  if ((e = cudaEventRecord(P->ev1, st))) return cuda_fail(e, "event");
+  if ((e = read_ctl(P))) return cuda_fail(e, "read control");
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, P->ev0, P->ev1);
+  const Ctl& h = *P->ctl_host;
+  P->state_valid = true;
+  if (int rc = check_err(P)) return rc;
+  int status = h.diverged ? RPT_DIVERGED : (h.status ? RPT_OK : RPT_NOT_CONVERGED);
+  if (status != RPT_DIVERGED && x_out) {
+    if ((e = cudaMemcpyAsync(x_out, P->z, sizeof(double) * n, cudaMemcpyDeviceToHost, st)))
+      return cuda_fail(e, "copy x_out");
+    if ((e = cudaStreamSynchronize(st))) return cuda_fail(e, "sync");
+  }
+  if (info) {
+    std::memset(info, 0, sizeof(*info));
+    info->status = status;
+    info->iterations = h.k;
+    info->inner = h.cg_total;
+    info->row_passes = h.passes;
+    // init + per iteration (residual pass, CG init, 3 per CG step, z/d/y, 2 for the
+    // optional objective test) + final objective pass and its reduction
+    info->kernels = 3 + 5LL * h.k + 3LL * h.cg_steps + (use_obj ? 2LL * h.k : 0LL);
+    info->seconds = ms * 1e-3;
+    info->f = h.f_cur;
+    info->r_prim = h.r_prim;
+    info->r_dual = h.r_dual;
+    info->eps_prim = h.eps_prim;
+    info->eps_dual = h.eps_dual;
+    info->step = h.step;
+    info->rho = rho;
+  }
+  if (status == RPT_DIVERGED) set_error("ADMM residuals became non-finite");
+  return status;
+}
+
+int pgd_solve(Plan* P, const rpt_pgd_params* prm, const double* x0, double* x_out,
+              rpt_solve_info* info) {
+  const DevPlan& dp = P->dp;
+  const int n = dp.n;
+  if (!(prm->beta > 0 && prm->beta < 1) || !(prm->gamma > 0 && prm->gamma < 1) ||
+      prm->max_iter < 1 || prm->max_trials < 1 || !(prm->tol_rel_df >= 0) || std::isnan(prm->alpha)) {
+    set_error("invalid PGD parameters");
+    return RPT_EINVAL;
+  }
+  if (x0)
+    for (int j = 0; j < n; ++j)
+      if (!std::isfinite(x0[j])) {
+        set_error("x0 has a non-finite entry");
+        return RPT_EINVAL;
+      }
+  double alpha = prm->alpha;
+  double L = 0.0;
+  if (!(alpha > 0)) {
+    int rc = compute_lipschitz(P, &L);
+    if (rc != RPT_OK) return rc;
+    if (!(L > 0)) {
+      set_error("Lipschitz estimate is zero (empty problem?)");
+      return RPT_EINVAL;
+    }
+    alpha = 4.0 / L;
+  }
+  cudaStream_t st = P->stream;
+  cudaError_t e;
+  if (x0 && (e = cudaMemcpyAsync(P->xt, x0, sizeof(double) * n, cudaMemcpyHostToDevice, st)))
+    return cuda_fail(e, "copy x0");
+  Ctl& c = *P->ctl_host;
+  std::memset(&c, 0, sizeof(Ctl));
+  c.const_term = P->stats.const_term;
+  c.alpha = alpha;
+  c.beta_a = prm->beta;
+  c.gamma = prm->gamma;
+  c.tol_df = prm->tol_rel_df;
+  c.f_target = prm->f_target;
+  c.pgd_max_iter = prm->max_iter;
+  c.max_trials = prm->max_trials;
+  if ((e = cudaMemcpyAsync(P->ctl, &c, sizeof(Ctl), cudaMemcpyHostToDevice, st)))
+    return cuda_fail(e, "upload control block");
+  if ((e = cudaEventRecord(P->ev0, st))) return cuda_fail(e, "event");
+  {
+    Exec ex;
+    ex.st = st;
+    launch(ex, k_pgd_init, dim3(P->nchunk), dim3(VT), 0, dp, (const double*)P->xt, x0 ? 1 : 0,
+           (const double*)P->lb, (const double*)P->ub, P->xp, P->vz32);
+    if (ex.err) return cuda_fail(ex.err, "launch init");
+  }
+  if (prm->use_graph) {
+    if (!P->pgd_exec && (e = build_pgd_graph(P))) return cuda_fail(e, "build PGD graph");
+    if ((e = cudaGraphLaunch(P->pgd_exec, st))) return cuda_fail(e, "launch PGD graph");
+  } else {
+    for (;;) {
+      Exec ex;
+      ex.st = st;
+      pgd_head(ex, P, 0, 0);
+      do {
+        pgd_trial(ex, P, 0, 0);
+        if (ex.err) return cuda_fail(ex.err, "launch");
+        if ((e = read_ctl(P))) return cuda_fail(e, "read control");
+      } while (!P->ctl_host->accepted && !P->ctl_host->failed);
+      pgd_tail(ex, P, 0, 0);
+      if (ex.err) return cuda_fail(ex.err, "launch");
+      if ((e = read_ctl(P))) return cuda_fail(e, "read control");
+      if (P->ctl_host->stop) break;
+    }
+  }
+  if ((e = cudaEventRecord(P->ev1, st))) return cuda_fail(e, "event");
+  if ((e = read_ctl(P))) return cuda_fail(e, "read control");
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, P->ev0, P->ev1);
+  const Ctl& h = *P->ctl_host;
+  if (int rc = check_err(P)) return rc;
+  int status = h.diverged ? RPT_DIVERGED : (h.status ? RPT_OK : RPT_NOT_CONVERGED);
+  if (status != RPT_DIVERGED && x_out) {
+    if ((e = cudaMemcpyAsync(x_out, P->xp, sizeof(double) * n, cudaMemcpyDeviceToHost, st)))
+      return cuda_fail(e, "copy x_out");
+    if ((e = cudaStreamSynchronize(st))) return cuda_fail(e, "sync");
+  }
+  if (info) {
+    std::memset(info, 0, sizeof(*info));
+    info->status = status;
+    info->iterations = h.pk;
+    info->inner = h.trials_total;
+    info->row_passes = h.passes;
+    // init + per iteration (residual pass, gradient, finish) + 3 per Armijo trial
+    info->kernels = 1 + 3LL * h.pouter + 3LL * h.trials_total;
+    info->seconds = ms * 1e-3;
+    info->f = h.f_cur;
+    info->step = h.step;
+    info->rho = L > 0 ? L : P->lipschitz;
+  }
+  if (status == RPT_DIVERGED) set_error("PGD objective became non-finite");
+  return status;
+}
+
+// ---- operators -----------------------------------------------------------------
+
+static cudaError_t stage_host_vector(Plan* P, float* dst, const double* src, int count_vecs) {
+  const DevPlan& dp = P->dp;
+  std::vector<float> h((size_t)count_vecs * dp.n_pad, 0.f);
+  for (int s = 0; s < count_vecs; ++s)
+    for (int j = 0; j < dp.n; ++j) h[(size_t)s * dp.n_pad + j] = (float)src[(size_t)s * dp.n + j];
+  cudaError_t e = cudaMemcpyAsync(dst, h.data(), sizeof(float) * h.size(), cudaMemcpyHostToDevice, P->stream);
+  if (e != cudaSuccess) return e;
+  return cudaStreamSynchronize(P->stream);
+}
+
+int op_apply_normal(Plan* P, const double* v, double rho, double* u_out) {
+  const DevPlan& dp = P->dp;
+  for (size_t i = 0; i < (size_t)dp.N * dp.n; ++i)
+    if (!std::isfinite(v[i])) {
+      set_error("v has a non-finite entry");
+      return RPT_EINVAL;
+    }
+  if (!(rho >= 0) || !std::isfinite(rho)) {
+    set_error("rho must be finite and >= 0");
+    return RPT_EINVAL;
+  }
+  cudaError_t e;
+  if ((e = stage_host_vector(P, P->v32, v, dp.N))) return cuda_fail(e, "stage");
+  if ((e = cudaMemcpyAsync(P->x, v, sizeof(double) * dp.N * dp.n, cudaMemcpyHostToDevice, P->stream)))
+    return cuda_fail(e, "copy");
+  Exec ex;
+  ex.st = P->stream;
+  rowpass(ex, P, kNormal, P->v32, dp.n_pad, nullptr);
+  launch(ex, k_reduce_scen, dim3(P->nchunk, dp.N), dim3(VT), 0, dp, (const float*)P->partial,
+         (const double*)P->x, 0.5 * rho, P->u);
+  if (ex.err) return cuda_fail(ex.err, "launch");
+  if ((e = cudaMemcpyAsync(u_out, P->u, sizeof(double) * dp.N * dp.n, cudaMemcpyDeviceToHost, P->stream)))
+    return cuda_fail(e, "copy out");
+  if ((e = cudaStreamSynchronize(P->stream))) return cuda_fail(e, "sync");
+  P->state_valid = false;   // x was used as scratch
+  return check_err(P);
+}
+
+int op_gradient(Plan* P, const double* x, double* g_out, double* f_out) {
+  const DevPlan& dp = P->dp;
+  for (int j = 0; j < dp.n; ++j)
+    if (!std::isfinite(x[j])) {
+      set_error("x has a non-finite entry");
+      return RPT_EINVAL;
+    }
+  cudaError_t e;
+  if ((e = stage_host_vector(P, P->vz32, x, 1))) return cuda_fail(e, "stage");
+  Exec ex;
+  ex.st = P->stream;
+  rowpass(ex, P, kResid, P->vz32, 0, nullptr);
+  launch(ex, k_reduce_all, dim3(P->nchunk), dim3(VT), 0, dp, (const float*)P->partial, 2.0, P->g);
+  if (ex.err) return cuda_fail(ex.err, "launch");
+  std::vector<double> objp(dp.nblocks);
+  if ((e = cudaMemcpyAsync(g_out, P->g, sizeof(double) * dp.n, cudaMemcpyDeviceToHost, P->stream)))
+    return cuda_fail(e, "copy out");
+  if ((e = cudaMemcpyAsync(objp.data(), P->objp, sizeof(double) * dp.nblocks, cudaMemcpyDeviceToHost, P->stream)))
+    return cuda_fail(e, "copy out");
+  if ((e = cudaStreamSynchronize(P->stream))) return cuda_fail(e, "sync");
+  if (int rc = check_err(P)) return rc;
+  if (f_out) {
+    double f = P->stats.const_term;
+    for (double v : objp) f += v;
+    *f_out = f;
+  }
+  return RPT_OK;
+}
+
+int op_objective(Plan* P, const double* x, double* f_out, double* dose_out) {
+  const DevPlan& dp = P->dp;
+  for (int j = 0; j < dp.n; ++j)
+    if (!std::isfinite(x[j])) {
+      set_error("x has a non-finite entry");
+      return RPT_EINVAL;
+    }
+  cudaError_t e;
+  if (dose_out && !P->dose) {
+    if ((e = cudaMalloc(&P->dose, sizeof(float) * (size_t)dp.N * dp.m_act))) {
+      P->dose = nullptr;
+      set_error("out of device memory for doses");
+      return RPT_ENOMEM;
+    }
+    P->allocs.push_back(P->dose);
+  }
+  if ((e = stage_host_vector(P, P->vz32, x, 1))) return cuda_fail(e, "stage");
+  Exec ex;
+  ex.st = P->stream;
+  rowpass(ex, P, dose_out ? kDose : kObj, P->vz32, 0, nullptr, P->dose);
+  if (ex.err) return cuda_fail(ex.err, "launch");
+  std::vector<double> objp(dp.nblocks);
+  if ((e = cudaMemcpyAsync(objp.data(), P->objp, sizeof(double) * dp.nblocks, cudaMemcpyDeviceToHost, P->stream)))
+    return cuda_fail(e, "copy out");
+  std::vector<float> dose;
+  if (dose_out) {
+    dose.resize((size_t)dp.N * dp.m_act);
+    if ((e = cudaMemcpyAsync(dose.data(), P->dose, sizeof(float) * dose.size(), cudaMemcpyDeviceToHost, P->stream)))
+      return cuda_fail(e, "copy out");
+  }
+  if ((e = cudaStreamSynchronize(P->stream))) return cuda_fail(e, "sync");
+  if (int rc = check_err(P)) return rc;
+  if (f_out) {
+    double f = P->stats.const_term;
+    for (double v : objp) f += v;
+    *f_out = f;
+  }
+  if (dose_out) {
+    std::memset(dose_out, 0, sizeof(double) * (size_t)dp.N * dp.m);
+    for (int s = 0; s < dp.N; ++s)
+      for (int k = 0; k < dp.m_act; ++k)
+        dose_out[(size_t)s * dp.m + P->kept_rows[k]] = dose[(size_t)s * dp.m_act + k];
+  }
+  return RPT_OK;
+}
+
+int profile_row_pass(Plan* P, int mode, int reps, double* ms, double* bytes) {
+  if ((mode != kNormal && mode != kResid) || reps < 1) {
+    set_error("profile_row_pass: mode must be 0 or 1 and reps >= 1");
+    return RPT_EINVAL;
+  }
+  const DevPlan& dp = P->dp;
+  cudaError_t e;
+  Exec ex;
+  ex.st = P->stream;
+  rowpass(ex, P, mode, P->v32, dp.n_pad, nullptr);   // warm-up launch
+  if ((e = cudaEventRecord(P->ev0, P->stream))) return cuda_fail(e, "event");
+  for (int r = 0; r < reps; ++r) rowpass(ex, P, mode, P->v32, dp.n_pad, nullptr);
+  if (ex.err) return cuda_fail(ex.err, "launch");
+  if ((e = cudaEventRecord(P->ev1, P->stream))) return cuda_fail(e, "event");
+  if ((e = cudaEventSynchronize(P->ev1))) return cuda_fail(e, "sync");
+  float t = 0.f;
+  cudaEventElapsedTime(&t, P->ev0, P->ev1);
+  if (int rc = check_err(P)) return rc;
+  if (ms) *ms = (double)t / reps;
+  if (bytes) {
+    const double per_row = 4.0 * (mode == kResid ? 2 : 1);   // weight (+ prescription)
+    *bytes = (double)P->stats.matrix_bytes + per_row * (double)dp.N * dp.m_act +
+             2.0 * 4.0 * (double)dp.N * dp.n;
+  }
+  return RPT_OK;
+}
+
+int compute_lipschitz(Plan* P, double* L) {
+  if (P->lipschitz > 0) {
+    *L = P->lipschitz;
+    return RPT_OK;
+  }
+  const DevPlan& dp = P->dp;
+  std::vector<double> v(dp.n, 1.0 / std::sqrt((double)dp.n)), u(dp.n);
+  double lam = 0.0;
+  cudaError_t e;
+  for (int it = 0; it < 30; ++it) {
+    if ((e = stage_host_vector(P, P->vz32, v.data(), 1))) return cuda_fail(e, "stage");
+    Exec ex;
+    ex.st = P->stream;
+    rowpass(ex, P, kNormal, P->vz32, 0, nullptr);
+    launch(ex, k_reduce_all, dim3(P->nchunk), dim3(VT), 0, dp, (const float*)P->partial, 1.0, P->g);
+    if (ex.err) return cuda_fail(ex.err, "launch");
+    if ((e = cudaMemcpyAsync(u.data(), P->g, sizeof(double) * dp.n, cudaMemcpyDeviceToHost, P->stream)))
+      return cuda_fail(e, "copy");
+    if ((e = cudaStreamSynchronize(P->stream))) return cuda_fail(e, "sync");
+    double nrm = 0.0;
+    for (double a : u) nrm += a * a;
+    nrm = std::sqrt(nrm);
+    lam = nrm;
+    if (nrm == 0.0) break;
+    for (int j = 0; j < dp.n; ++j) v[j] = u[j] / nrm;
+  }
+  P->lipschitz = 2.0 * lam;
+  *L = P->lipschitz;
+  return RPT_OK;
+}
+
+}  // namespace rpt

@@ -1,0 +1,290 @@
+"""Thin ctypes binding of librpt (include/rpt.h).  Argument marshalling only:
+every step of the solvers runs in the library's CUDA kernels.  Importing this
+module fails loudly if the library has not been built; there is no CPU path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "librpt.so")
+
+OK, NOT_CONVERGED, EINVAL, ENOMEM, ECUDA, TIMEOUT, DIVERGED, EUNSUPPORTED = 0, 1, -1, -2, -3, -4, -5, -6
+F32, BF16, FP8E4M3 = 0, 1, 2
+BB_PAPER, BB_GUARDED, BB_OFF = 0, 1, 2
+Z_STD, Z_LIT = 0, 1
+MAX_SPOTS = 24576
+
+EXPORTED = [
+    "rpt_admm_params_default", "rpt_pgd_params_default", "rpt_plan_create", "rpt_plan_destroy",
+    "rpt_plan_query", "rpt_admm_bb_solve", "rpt_pgd_solve", "rpt_objective", "rpt_gradient",
+    "rpt_apply_normal", "rpt_profile_row_pass", "rpt_state_get", "rpt_state_set", "rpt_status_string", "rpt_last_error",
+    "rpt_version",
+]
+
+
+class RptError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{msg} (status {status})")
+        self.status = status
+
+
+class _Problem(C.Structure):
+    _fields_ = [("m", C.c_int32), ("n", C.c_int32), ("N", C.c_int32),
+                ("row_ptr", C.POINTER(C.POINTER(C.c_int32))),
+                ("col_idx", C.POINTER(C.POINTER(C.c_int32))),
+                ("val", C.POINTER(C.POINTER(C.c_float))),
+                ("voxel_w", C.POINTER(C.c_double)), ("presc", C.POINTER(C.c_double)),
+                ("scen_weight", C.POINTER(C.c_double)),
+                ("lb", C.POINTER(C.c_double)), ("ub", C.POINTER(C.c_double)),
+                ("value_format", C.c_int32), ("index_width", C.c_int32)]
+
+
+class _DeviceOpts(C.Structure):
+    _fields_ = [("device", C.c_int32), ("stream", C.c_void_p), ("ctas_per_sm", C.c_int32),
+                ("row_path", C.c_int32)]
+
+
+class AdmmParams(C.Structure):
+    _fields_ = [("rho", C.c_double), ("rho_scale", C.c_double), ("eps_abs", C.c_double),
+                ("eps_rel", C.c_double), ("tol_obj", C.c_double), ("max_iter", C.c_int32),
+                ("bb_mode", C.c_int32), ("bb_kappa", C.c_double), ("z_mode", C.c_int32),
+                ("cg_max", C.c_int32), ("cg_theta", C.c_double), ("cg_eta0", C.c_double),
+                ("cg_floor_rel", C.c_double), ("use_graph", C.c_int32), ("check_every", C.c_int32),
+                ("resume", C.c_int32), ("cg_precond", C.c_int32)]
+
+
+class PgdParams(C.Structure):
+    _fields_ = [("alpha", C.c_double), ("beta", C.c_double), ("gamma", C.c_double),
+                ("tol_rel_df", C.c_double), ("f_target", C.c_double), ("max_iter", C.c_int32),
+                ("max_trials", C.c_int32), ("use_graph", C.c_int32), ("reserved", C.c_int32)]
+
+
+class _Info(C.Structure):
+    _fields_ = [("status", C.c_int32), ("iterations", C.c_int32), ("inner", C.c_int64),
+                ("row_passes", C.c_int64), ("kernels", C.c_int64), ("seconds", C.c_double), ("f", C.c_double),
+                ("r_prim", C.c_double), ("r_dual", C.c_double), ("eps_prim", C.c_double),
+                ("eps_dual", C.c_double), ("step", C.c_double), ("rho", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class _Stats(C.Structure):
+    _fields_ = [("m", C.c_int32), ("n", C.c_int32), ("N", C.c_int32), ("m_active", C.c_int32),
+                ("nnz", C.c_int64), ("matrix_bytes", C.c_int64), ("value_format", C.c_int32),
+                ("index_width", C.c_int32), ("row_blocks", C.c_int32), ("sm_count", C.c_int32),
+                ("default_rho", C.c_double), ("const_term", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def lib():
+    """Load librpt.so (in-tree build).  Raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"librpt.so not built ({LIB_PATH}); run paper_2304_14568_gb300.build.build()")
+    L = C.CDLL(LIB_PATH)
+    dp = C.POINTER(C.c_double)
+    L.rpt_admm_params_default.argtypes = [C.POINTER(AdmmParams)]
+    L.rpt_admm_params_default.restype = None
+    L.rpt_pgd_params_default.argtypes = [C.POINTER(PgdParams)]
+    L.rpt_pgd_params_default.restype = None
+    L.rpt_plan_create.argtypes = [C.POINTER(_Problem), C.POINTER(_DeviceOpts), C.POINTER(C.c_void_p)]
+    L.rpt_plan_create.restype = C.c_int
+    L.rpt_plan_destroy.argtypes = [C.c_void_p]
+    L.rpt_plan_destroy.restype = None
+    L.rpt_plan_query.argtypes = [C.c_void_p, C.POINTER(_Stats)]
+    L.rpt_plan_query.restype = C.c_int
+    L.rpt_admm_bb_solve.argtypes = [C.c_void_p, C.POINTER(AdmmParams), dp, dp, dp, C.POINTER(_Info)]
+    L.rpt_admm_bb_solve.restype = C.c_int
+    L.rpt_pgd_solve.argtypes = [C.c_void_p, C.POINTER(PgdParams), dp, dp, C.POINTER(_Info)]
+    L.rpt_pgd_solve.restype = C.c_int
+    L.rpt_objective.argtypes = [C.c_void_p, dp, dp, dp]
+    L.rpt_objective.restype = C.c_int
+    L.rpt_gradient.argtypes = [C.c_void_p, dp, dp, dp]
+    L.rpt_gradient.restype = C.c_int
+    L.rpt_apply_normal.argtypes = [C.c_void_p, dp, C.c_double, dp]
+    L.rpt_apply_normal.restype = C.c_int
+    L.rpt_profile_row_pass.argtypes = [C.c_void_p, C.c_int, C.c_int, dp, dp]
+    L.rpt_profile_row_pass.restype = C.c_int
+    L.rpt_state_get.argtypes = [C.c_void_p, dp, dp, dp]
+    L.rpt_state_get.restype = C.c_int
+    L.rpt_state_set.argtypes = [C.c_void_p, dp, dp, dp]
+    L.rpt_state_set.restype = C.c_int
+    L.rpt_status_string.argtypes = [C.c_int]
+    L.rpt_status_string.restype = C.c_char_p
+    L.rpt_last_error.argtypes = []
+    L.rpt_last_error.restype = C.c_char_p
+    L.rpt_version.argtypes = []
+    L.rpt_version.restype = C.c_char_p
+    _lib = L
+    return L
+
+
+def _dptr(a):
+    return None if a is None else a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _check(rc, allow=(OK,)):
+    if rc not in allow:
+        raise RptError(rc, lib().rpt_last_error().decode() or lib().rpt_status_string(rc).decode())
+    return rc
+
+
+def admm_params(**kw) -> AdmmParams:
+    p = AdmmParams()
+    lib().rpt_admm_params_default(C.byref(p))
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+def pgd_params(**kw) -> PgdParams:
+    p = PgdParams()
+    lib().rpt_pgd_params_default(C.byref(p))
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+class Plan:
+    """A device-resident plan (rpt_plan_create / rpt_plan_destroy)."""
+
+    def __init__(self, m, n, N, row_ptr, col_idx, val, voxel_w, presc, scen_weight=None,
+                 lb=None, ub=None, value_format=F32, index_width=32, device=0, stream=None,
+                 ctas_per_sm=0, row_path=0):
+        L = lib()
+        rp = [np.ascontiguousarray(a, dtype=np.int32) for a in row_ptr]
+        ci = [np.ascontiguousarray(a, dtype=np.int32) for a in col_idx]
+        va = [np.ascontiguousarray(a, dtype=np.float32) for a in val]
+        w = np.ascontiguousarray(voxel_w, dtype=np.float64)
+        p = np.ascontiguousarray(presc, dtype=np.float64)
+        sw = None if scen_weight is None else np.ascontiguousarray(scen_weight, dtype=np.float64)
+        lbv = None if lb is None else np.ascontiguousarray(lb, dtype=np.float64)
+        ubv = None if ub is None else np.ascontiguousarray(ub, dtype=np.float64)
+        RP = (C.POINTER(C.c_int32) * N)(*[a.ctypes.data_as(C.POINTER(C.c_int32)) for a in rp])
+        CI = (C.POINTER(C.c_int32) * N)(*[a.ctypes.data_as(C.POINTER(C.c_int32)) for a in ci])
+        VA = (C.POINTER(C.c_float) * N)(*[a.ctypes.data_as(C.POINTER(C.c_float)) for a in va])
+        pr = _Problem(m, n, N, RP, CI, VA, _dptr(w), _dptr(p), _dptr(sw), _dptr(lbv), _dptr(ubv),
+                      value_format, index_width)
+        opts = _DeviceOpts(device, stream, ctas_per_sm, row_path)
+        h = C.c_void_p()
+        _check(L.rpt_plan_create(C.byref(pr), C.byref(opts), C.byref(h)))
+        self._h = h
+        self.m, self.n, self.N = m, n, N
+
+    @classmethod
+    def from_problem(cls, prob, **kw):
+        """Build from any object with the fields of the C struct rpt_problem."""
+        return cls(prob.m, prob.n, prob.N, prob.row_ptr, prob.col_idx, prob.val, prob.voxel_w,
+                   prob.presc, prob.scen_weight, prob.lb, prob.ub, **kw)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().rpt_plan_destroy(self._h)
+            self._h = None
+
+    plan_destroy = close
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def stats(self) -> dict:
+        s = _Stats()
+        _check(lib().rpt_plan_query(self._h, C.byref(s)))
+        return s.as_dict()
+
+    def admm_bb_solve(self, params: AdmmParams | None = None, z0=None, y0=None, **kw):
+        prm = params if params is not None else admm_params(**kw)
+        x = np.empty(self.n)
+        z0a = None if z0 is None else np.ascontiguousarray(z0, dtype=np.float64)
+        y0a = None if y0 is None else np.ascontiguousarray(y0, dtype=np.float64).reshape(-1)
+        info = _Info()
+        rc = lib().rpt_admm_bb_solve(self._h, C.byref(prm), _dptr(z0a), _dptr(y0a), _dptr(x), C.byref(info))
+        _check(rc, allow=(OK, NOT_CONVERGED))
+        return x, info.as_dict()
+
+    def pgd_solve(self, params: PgdParams | None = None, x0=None, **kw):
+        prm = params if params is not None else pgd_params(**kw)
+        x = np.empty(self.n)
+        x0a = None if x0 is None else np.ascontiguousarray(x0, dtype=np.float64)
+        info = _Info()
+        rc = lib().rpt_pgd_solve(self._h, C.byref(prm), _dptr(x0a), _dptr(x), C.byref(info))
+        _check(rc, allow=(OK, NOT_CONVERGED))
+        return x, info.as_dict()
+
+    def objective(self, x, dose=False):
+        xa = np.ascontiguousarray(x, dtype=np.float64)
+        f = C.c_double()
+        d = np.empty(self.N * self.m) if dose else None
+        _check(lib().rpt_objective(self._h, _dptr(xa), C.byref(f), _dptr(d)))
+        return (f.value, d.reshape(self.N, self.m)) if dose else f.value
+
+    def gradient(self, x):
+        xa = np.ascontiguousarray(x, dtype=np.float64)
+        g = np.empty(self.n)
+        f = C.c_double()
+        _check(lib().rpt_gradient(self._h, _dptr(xa), _dptr(g), C.byref(f)))
+        return g, f.value
+
+    def apply_normal(self, v, rho=0.0):
+        va = np.ascontiguousarray(v, dtype=np.float64).reshape(-1)
+        u = np.empty(self.N * self.n)
+        _check(lib().rpt_apply_normal(self._h, _dptr(va), float(rho), _dptr(u)))
+        return u.reshape(self.N, self.n)
+
+    def profile_row_pass(self, mode=0, reps=20):
+        """(milliseconds per launch, algorithmic bytes per launch) of the row pass."""
+        ms = C.c_double()
+        by = C.c_double()
+        _check(lib().rpt_profile_row_pass(self._h, int(mode), int(reps), C.byref(ms), C.byref(by)))
+        return ms.value, by.value
+
+    def state_get(self):
+        z = np.empty(self.n)
+        x = np.empty(self.N * self.n)
+        y = np.empty(self.N * self.n)
+        _check(lib().rpt_state_get(self._h, _dptr(z), _dptr(x), _dptr(y)))
+        return z, x.reshape(self.N, self.n), y.reshape(self.N, self.n)
+
+    def state_set(self, z, x, y):
+        za = np.ascontiguousarray(z, dtype=np.float64)
+        xa = np.ascontiguousarray(x, dtype=np.float64).reshape(-1)
+        ya = np.ascontiguousarray(y, dtype=np.float64).reshape(-1)
+        _check(lib().rpt_state_set(self._h, _dptr(za), _dptr(xa), _dptr(ya)))
+
+
+def plan_create(prob, **kw) -> Plan:
+    return Plan.from_problem(prob, **kw)
+
+
+def version() -> str:
+    return lib().rpt_version().decode()
+
+
+def inf():
+    return math.inf

@@ -1,0 +1,245 @@
+"""ADMM-BB and PGD through the C ABI against the float64 oracle (Sec. 2.1-2.2).
+
+Iterates are compared element by element (z, x_s, y_s after k iterations, with
+the subproblems solved tightly on both sides); converged solutions are compared
+on the objective and the stacked weighted dose, which are unique at the
+optimum, and on z where the Hessian is well conditioned."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from synthetic import from_dense, random_problem, config_tiny_plain
+from oracle import Weighted, admm_bb, pgd, lsq_box, certificates, default_rho, lipschitz
+from tests.gpu_util import gpu_lib, plan_of
+
+pytestmark = pytest.mark.gpu
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+TIGHT_CG = dict(cg_theta=1e-12, cg_eta0=1e-12, cg_floor_rel=0.0, cg_max=200)
+
+
+@pytest.fixture(scope="module")
+def rpt():
+    return gpu_lib()
+
+
+@pytest.fixture(scope="module")
+def tiny_plain():
+    prob = config_tiny_plain(0)
+    W = Weighted(prob)
+    xs = lsq_box(W)
+    return prob, W, xs, W.f(xs)
+
+
+def test_hand_worked_iterates(rpt):
+    g = json.load(open(os.path.join(GOLD, "hand_admm_bb_2x1.json")))
+    pr = g["problem"]
+    prob = from_dense(pr["A"], pr["w"], pr["p"], pr["lb"], pr["ub"])
+    with plan_of(rpt, prob) as P:
+        for k, it in enumerate(g["iterates"], start=1):
+            for graph in (1, 0):
+                x, info = P.admm_bb_solve(rho=g["params"]["rho"], max_iter=k, eps_abs=0.0, eps_rel=0.0,
+                                          use_graph=graph, **TIGHT_CG)
+                z, X, Y = P.state_get()
+                np.testing.assert_allclose(z, it["z"], rtol=1e-6)
+                np.testing.assert_allclose(X, it["x"], rtol=1e-6)
+                np.testing.assert_allclose(Y, it["y"], rtol=1e-6, atol=1e-7)
+                assert info["step"] == pytest.approx(it["step"], rel=1e-5)
+                assert info["iterations"] == k
+                if "r_prim" in it:
+                    assert info["r_prim"] == pytest.approx(it["r_prim"], rel=1e-6)
+                    assert info["r_dual"] == pytest.approx(it["r_dual"], rel=1e-6)
+        x, info = P.admm_bb_solve(rho=2.0, eps_abs=1e-7, eps_rel=1e-7, max_iter=2000)
+        assert info["status"] == 0
+        assert x[0] == pytest.approx(g["optimum"]["x"][0], rel=1e-6)
+        assert info["f"] == pytest.approx(g["optimum"]["f"], rel=1e-5)
+
+
+ITER_CASES = [("paper", "std"), ("off", "std"), ("guarded", "std"), ("paper", "lit")]
+
+
+@pytest.mark.parametrize("bb,zm", ITER_CASES)
+def test_iterates_match_oracle(rpt, bb, zm):
+    """After k iterations the GPU state (z, x_s, y_s) equals the oracle's (exact
+    Cholesky subproblems).  Error budget: each GPU subproblem is solved to the
+    float32 floor of the operator, |e_s| <= kf * mag_s with kf the float32 factor
+    of the row pass and mag_s = (|A~_s|'|A~_s| + rho/2)|x_s| + |b_s|; the solution
+    error is ||B_s^{-1} e_s||_2 <= (2/rho) ||e_s||_2, and k iterations add up."""
+    from tests.gpu_util import fp32_op_bound
+    prob = random_problem(21, m=300, n=40, N=3, mean_row=8.0, scen_weight=True, ub=6.0)
+    W = Weighted(prob)
+    rho = 0.3 * default_rho(W)
+    kf = fp32_op_bound(prob)
+    Aa = [abs(M) for M in W.At]
+    bb_c = {"paper": rpt.BB_PAPER, "off": rpt.BB_OFF, "guarded": rpt.BB_GUARDED}[bb]
+    zc = {"std": rpt.Z_STD, "lit": rpt.Z_LIT}[zm]
+    with plan_of(rpt, prob) as P:
+        for k in (1, 2, 3, 6, 12):
+            ref = admm_bb(W, rho=rho, max_iter=k, eps_abs=0.0, eps_rel=0.0, bb=bb, zmode=zm)
+            x, info = P.admm_bb_solve(rho=rho, max_iter=k, eps_abs=0.0, eps_rel=0.0, bb_mode=bb_c,
+                                      z_mode=zc, **TIGHT_CG)
+            z, X, Y = P.state_get()
+            e2 = 0.0
+            for s in range(prob.N):
+                xs = np.abs(ref["x"][s])
+                mag = Aa[s].T @ (Aa[s] @ xs) + 0.5 * rho * xs + np.abs(W.b(s))
+                e2 += float(np.sum(mag ** 2))
+            bound = 10.0 * k * (2.0 / rho) * kf * math.sqrt(e2)
+            assert np.linalg.norm(X - ref["x"]) <= bound, (k, np.linalg.norm(X - ref["x"]), bound)
+            assert np.linalg.norm(z - ref["z"]) <= bound
+            assert np.linalg.norm(Y - ref["y"]) <= 4.0 * rho * bound + 1e-9 * np.linalg.norm(ref["y"])
+            # and much closer than the bound in practice
+            sz = np.abs(ref["z"]).max()
+            np.testing.assert_allclose(z, ref["z"], rtol=1e-4, atol=1e-5 * sz)
+            assert info["step"] == pytest.approx(ref["step"], rel=1e-3)
+            assert info["r_prim"] == pytest.approx(ref["r_prim"], rel=1e-3, abs=1e-5 * sz)
+
+
+def test_converges_to_exact_optimum_tiny_plain(rpt, tiny_plain):
+    """Default parameters, tight tolerances: objective within 1e-6 of the exact
+    box-constrained optimum (lsq_linear), certificates near zero."""
+    prob, W, xs, fstar = tiny_plain
+    with plan_of(rpt, prob) as P:
+        z, info = P.admm_bb_solve(eps_abs=1e-7, eps_rel=1e-7, max_iter=20000)
+    f_gpu = W.f(z)
+    assert np.all(z >= prob.lb) and np.all(z <= prob.ub)
+    assert (f_gpu - fstar) / fstar <= 1e-6, ((f_gpu - fstar) / fstar, info)
+    assert info["f"] == pytest.approx(f_gpu, rel=1e-6)
+    c = certificates(W, z)
+    assert c["pg"] < 1e-3
+    Ds = W.stacked_weighted_dose(xs)
+    Dg = W.stacked_weighted_dose(z)
+    rel_dose = np.linalg.norm(Dg - Ds) / np.linalg.norm(Ds)
+    assert rel_dose <= 1e-3, rel_dose
+
+
+def test_time_to_tolerance_setting_matches_oracle(rpt, tiny_plain):
+    """At eps = 1e-4 (the benchmark's tolerance) GPU and oracle CG-ADMM stop with
+    the same objective to 1e-6 and similar iteration counts."""
+    prob, W, xs, fstar = tiny_plain
+    rho = 0.3 * default_rho(W)
+    ref = admm_bb(W, rho=rho, eps_abs=1e-4, eps_rel=1e-4, max_iter=5000, subproblem="cg",
+                  cg_theta=0.3, cg_eta0=1e-2, cg_floor_rel=1e-6, cg_precond="jacobi")
+    with plan_of(rpt, prob) as P:
+        z, info = P.admm_bb_solve(rho=rho)
+    assert info["status"] == 0
+    assert abs(W.f(z) - ref["f"]) / ref["f"] <= 1e-5
+    assert 0.7 * ref["iterations"] <= info["iterations"] <= 1.3 * ref["iterations"] + 5
+
+
+@pytest.mark.parametrize("precond", [0, 1])
+def test_plain_and_jacobi_cg_reach_the_optimum(rpt, precond):
+    prob = random_problem(28, m=500, n=60, N=3, mean_row=10.0, ub=8.0, scen_weight=True)
+    W = Weighted(prob)
+    xs = lsq_box(W)
+    with plan_of(rpt, prob) as P:
+        z, info = P.admm_bb_solve(eps_abs=1e-6, eps_rel=1e-6, cg_precond=precond)
+    assert info["status"] == 0
+    assert (W.f(z) - W.f(xs)) / W.f(xs) < 1e-6
+
+
+def test_graph_and_host_loop_agree(rpt):
+    prob = random_problem(22, m=400, n=60, N=4, mean_row=10.0, ub=8.0)
+    with plan_of(rpt, prob) as P:
+        z1, i1 = P.admm_bb_solve(use_graph=1, eps_abs=1e-6, eps_rel=1e-6)
+        z0, i0 = P.admm_bb_solve(use_graph=0, eps_abs=1e-6, eps_rel=1e-6)
+        z2, i2 = P.admm_bb_solve(use_graph=0, check_every=5, eps_abs=1e-6, eps_rel=1e-6)
+    assert abs(i1["iterations"] - i0["iterations"]) <= 2
+    np.testing.assert_allclose(z1, z0, rtol=1e-4, atol=1e-5 * np.abs(z1).max())
+    assert i2["iterations"] >= i0["iterations"] and i2["iterations"] % 5 == 0
+
+
+def test_status_and_resume(rpt):
+    prob = random_problem(23, m=300, n=50, N=3, mean_row=9.0, ub=8.0)
+    W = Weighted(prob)
+    with plan_of(rpt, prob) as P:
+        x, info = P.admm_bb_solve(max_iter=3, eps_abs=1e-12, eps_rel=1e-12)
+        assert info["status"] == 1 and info["iterations"] == 3      # RPT_NOT_CONVERGED, x written
+        assert np.all(np.isfinite(x))
+        z, X, Y = P.state_get()
+        np.testing.assert_array_equal(z, x)
+        # round trip and resume from the stored state
+        P.state_set(z, X, Y)
+        x2, info2 = P.admm_bb_solve(max_iter=2000, eps_abs=1e-6, eps_rel=1e-6, resume=1)
+        assert info2["status"] == 0
+        x3, info3 = P.admm_bb_solve(max_iter=2000, eps_abs=1e-6, eps_rel=1e-6)
+        assert abs(W.f(x2) - W.f(x3)) / W.f(x3) < 1e-6
+        # resume from a converged state stops at once
+        x4, info4 = P.admm_bb_solve(max_iter=2000, eps_abs=1e-6, eps_rel=1e-6, resume=1)
+        assert info4["status"] == 0 and info4["iterations"] <= 10
+
+
+def test_objective_change_rule(rpt):
+    """tol_obj is AND-ed with the residual rule (Sec. 2.3): a loose objective
+    tolerance changes nothing but adds one objective pass per iteration."""
+    prob = random_problem(24, m=300, n=50, N=3, mean_row=9.0, ub=8.0)
+    W = Weighted(prob)
+    with plan_of(rpt, prob) as P:
+        z_a, ia = P.admm_bb_solve(eps_abs=1e-5, eps_rel=1e-5, max_iter=3000)
+        z_b, ib = P.admm_bb_solve(eps_abs=1e-5, eps_rel=1e-5, max_iter=3000, tol_obj=1e30)
+    assert ia["status"] == 0 and ib["status"] == 0
+    # per iteration: the residual pass, the CG passes and one objective pass
+    assert ib["row_passes"] >= 2 * ib["iterations"] + 1
+    assert ib["kernels"] >= 7 * ib["iterations"]
+    assert ib["f"] == pytest.approx(W.f(z_b), rel=1e-6)
+
+
+def test_warm_start_and_dual_start(rpt):
+    prob = random_problem(25, m=300, n=50, N=3, mean_row=9.0, ub=8.0)
+    W = Weighted(prob)
+    xs = lsq_box(W)
+    with plan_of(rpt, prob) as P:
+        _, cold = P.admm_bb_solve(eps_abs=1e-6, eps_rel=1e-6)
+        y0 = np.stack([-W.grad_s(s, xs) for s in range(prob.N)])
+        z, warm = P.admm_bb_solve(eps_abs=1e-6, eps_rel=1e-6, z0=xs, y0=y0)
+    assert warm["iterations"] < cold["iterations"]
+    assert abs(W.f(z) - W.f(xs)) / W.f(xs) < 1e-6
+
+
+def test_pgd_matches_oracle(rpt, tiny_plain):
+    prob, W, xs, fstar = tiny_plain
+    L = lipschitz(W)
+    ref = pgd(W, alpha=4.0 / L, tol_rel_df=1e-6, max_iter=300, record=True)
+    with plan_of(rpt, prob) as P:
+        x, info = P.pgd_solve(alpha=4.0 / L, tol_rel_df=1e-6, max_iter=300)
+        _, info_auto = P.pgd_solve(tol_rel_df=1e-6, max_iter=5)
+    assert info_auto["rho"] == pytest.approx(L, rel=1e-4)          # the library's own estimate
+    assert abs(info["iterations"] - ref["iterations"]) <= max(3, 0.05 * ref["iterations"])
+    assert abs(W.f(x) - ref["f"]) / ref["f"] < 1e-5
+    assert info["f"] == pytest.approx(W.f(x), rel=1e-6)
+    assert np.all(x >= prob.lb) and np.all(x <= prob.ub)
+
+
+def test_pgd_and_admm_reach_same_optimum(rpt):
+    prob = random_problem(26, m=400, n=30, N=3, mean_row=8.0, ub=6.0)
+    W = Weighted(prob)
+    xs = lsq_box(W)
+    fs = W.f(xs)
+    with plan_of(rpt, prob) as P:
+        za, _ = P.admm_bb_solve(eps_abs=1e-8, eps_rel=1e-8, max_iter=20000)
+        zp, _ = P.pgd_solve(tol_rel_df=1e-12, max_iter=20000)
+    assert (W.f(za) - fs) / fs < 1e-6
+    assert (W.f(zp) - fs) / fs < 1e-5
+
+
+def test_input_errors(rpt):
+    prob = random_problem(27, m=50, n=8, N=2, mean_row=3.0)
+    with plan_of(rpt, prob) as P:
+        with pytest.raises(rpt.RptError) as e:
+            P.admm_bb_solve(z0=np.full(prob.n, np.nan))
+        assert e.value.status == rpt.EINVAL
+        with pytest.raises(rpt.RptError) as e:
+            P.admm_bb_solve(rho=-1.0, rho_scale=-1.0)
+        assert e.value.status == rpt.EINVAL
+        with pytest.raises(rpt.RptError) as e:
+            P.pgd_solve(beta=2.0)
+        assert e.value.status == rpt.EINVAL
+        with pytest.raises(rpt.RptError) as e:
+            P.state_get()
+        assert e.value.status == rpt.EINVAL
+        # the plan stays usable after errors
+        x, info = P.admm_bb_solve()
+        assert info["status"] in (0, 1)
