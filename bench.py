@@ -178,6 +178,9 @@ def main():
     ap.add_argument("--no-pgd", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--ref-budget", type=float, default=15.0)
+    ap.add_argument("--max-iter", type=int, default=0,
+                    help="cap ADMM iterations (short profiling runs; not a benchmark setting)")
+    ap.add_argument("--row-path", type=int, default=0, help="0 default, 1 register, 2 bulk-copy ring")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -202,9 +205,11 @@ def main():
     prob = _workload(args.seed, args.workers)
     t_gen = time.perf_counter() - t_gen
     stream = torch.cuda.Stream(device=dev)
-    plan = rpt.Plan.from_problem(prob, device=dev, stream=stream.cuda_stream)
+    plan = rpt.Plan.from_problem(prob, device=dev, stream=stream.cuda_stream, row_path=args.row_path)
     st = plan.stats()
     params = rpt.admm_params()          # eps_abs = eps_rel = 1e-4, defaults of the library
+    if args.max_iter > 0:
+        params.max_iter = args.max_iter
 
     def barrier():
         if world > 1:
@@ -299,7 +304,7 @@ def main():
         for _ in range(2):
             torch.cuda.synchronize(dev)
             t0 = time.perf_counter()
-            p2 = rpt.Plan.from_problem(prob, device=dev, stream=stream.cuda_stream)
+            p2 = rpt.Plan.from_problem(prob, device=dev, stream=stream.cuda_stream, row_path=args.row_path)
             x2, i2 = p2.admm_bb_solve(params)
             torch.cuda.synchronize(dev)
             e2e.append(time.perf_counter() - t0)

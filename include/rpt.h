@@ -84,7 +84,7 @@ typedef struct {
   int32_t device;                   /* CUDA device ordinal */
   void*   stream;                   /* cudaStream_t to run on, or NULL for a stream owned by the plan */
   int32_t ctas_per_sm;              /* row-pass CTAs per SM (0 = library choice) */
-  int32_t row_path;                 /* 0 default (= 1), 1 register-direct loads, 2 bulk-copy (TMA) ring */
+  int32_t row_path;                 /* 1 register-direct loads, 2 bulk-copy (TMA) ring; 0: RPT_ROW_PATH from the environment, else 1 */
 } rpt_device_opts;
 
 /* ADMM-BB parameters (Sec. 2.2).  Fill with rpt_admm_params_default(). */

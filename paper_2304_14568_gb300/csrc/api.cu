@@ -156,78 +156,58 @@ void free_plan(Plan* P) {
   delete P;
 }
 
-struct TmaLayout {
-  std::vector<ChunkDesc> chunks;
-  std::vector<int4> segs;      // (s, chunk_begin, chunk_end, slot)
-  std::vector<int> cta_seg;    // [G+1]
-  std::vector<int> slot_first; // [N+1]
+// Lanes per row: the smallest power of two G with G * kKeep >= len (1..32).
+constexpr int kKeep = 8;   // entries per lane held in registers by the row-pass kernels
+int lanes_for(int len) {
+  int g = 1;
+  while (g < 32 && g * kKeep < len) g <<= 1;
+  return g;
+}
+
+// Per-scenario row lists (non-empty rows only, sorted by decreasing length):
+// rec_base[s] .. rec_base[s] + nrows[s] are the rows of scenario s, followed by
+// a terminator record holding the scenario's entry count.
+struct RowLists {
+  std::vector<int> rec_base;   // [N+1]
+  std::vector<int> nrows;      // [N]
+  std::vector<int4> rec;       // {start, c_s w, p, kept-row index}
 };
 
-// Cut the scenario-major sequence of all rows into G equal-cost slices (one
-// persistent CTA each), split slices at scenario boundaries into segments and
-// segments into row-aligned chunks of at most cmax copied entries (16-entry
-// aligned span) and rmax rows.  Returns false if a single row does not fit.
-bool build_tma_layout(const std::vector<int32_t>& rp_h, const std::vector<int64_t>& base, int N,
-                      int m_act, int G, int cmax, int rmax, double row_cost, TmaLayout* L) {
-  const int64_t R = (int64_t)N * m_act;
-  auto rowlen = [&](int64_t idx) {
-    const int s = (int)(idx / m_act), r = (int)(idx % m_act);
-    const int32_t* o = &rp_h[(size_t)s * (m_act + 1)];
-    return (double)(o[r + 1] - o[r]);
-  };
-  double total = 0.0;
-  for (int64_t i = 0; i < R; ++i) total += rowlen(i) + row_cost;
-  std::vector<int64_t> cut(G + 1, R);
-  cut[0] = 0;
-  {
-    double acc = 0.0;
-    int g = 1;
-    for (int64_t i = 0; i < R && g < G; ++i) {
-      while (g < G && acc >= total * g / G) cut[g++] = i;
-      acc += rowlen(i) + row_cost;
-    }
-    while (g < G) cut[g++] = R;
-  }
-  L->cta_seg.assign(G + 1, 0);
-  L->slot_first.assign(N + 1, -1);
-  for (int c = 0; c < G; ++c) {
-    L->cta_seg[c] = (int)L->segs.size();
-    int64_t a = cut[c];
-    const int64_t b = cut[c + 1];
-    while (a < b) {
-      const int s = (int)(a / m_act);
-      const int r0 = (int)(a % m_act);
-      const int r1 = (int)std::min<int64_t>(b - (int64_t)s * m_act, m_act);
-      const int32_t* o = &rp_h[(size_t)s * (m_act + 1)];
-      const int slot = (int)L->segs.size();
-      if (L->slot_first[s] < 0) L->slot_first[s] = slot;
-      const int cb = (int)L->chunks.size();
-      int r = r0;
-      while (r < r1) {
-        const int64_t g_al = (base[s] + o[r]) & ~(int64_t)15;
-        int re = r;
-        while (re < r1 && re - r < rmax) {
-          const int64_t g_end = (base[s] + o[re + 1] + 15) & ~(int64_t)15;
-          if (g_end - g_al > cmax) break;
-          ++re;
-        }
-        if (re == r) return false;
-        ChunkDesc ch{};
-        ch.g_al = g_al;
-        ch.row_begin = r;
-        ch.n_rows = re - r;
-        ch.n_ent = (int)std::max<int64_t>(16, ((base[s] + o[re] + 15) & ~(int64_t)15) - g_al);
-        L->chunks.push_back(ch);
-        r = re;
+double row_cost(int len, double per_lane) { return (double)len + per_lane * lanes_for(len); }
+
+// Cut every scenario's row list into chunks of rows with the same lanes-per-row
+// class, at most cmax copied entries (16-entry aligned span) and rmax rows.
+// scen_chunk[s]..scen_chunk[s+1] are scenario s's chunks.  Returns false if a
+// single row does not fit a stage.
+bool build_chunks(const RowLists& R, const std::vector<int64_t>& base, int N, int cmax, int rmax,
+                  std::vector<ChunkDesc>* chunks, std::vector<int>* scen_chunk) {
+  scen_chunk->assign(N + 1, 0);
+  for (int s = 0; s < N; ++s) {
+    (*scen_chunk)[s] = (int)chunks->size();
+    const int4* r = &R.rec[R.rec_base[s]];
+    int q = 0;
+    while (q < R.nrows[s]) {
+      const int g0 = lanes_for(r[q + 1].x - r[q].x);
+      const int64_t g_al = (base[s] + r[q].x) & ~(int64_t)15;
+      int qe = q;
+      while (qe < R.nrows[s] && qe - q < rmax && lanes_for(r[qe + 1].x - r[qe].x) == g0) {
+        const int64_t g_end = (base[s] + r[qe + 1].x + 15) & ~(int64_t)15;
+        if (g_end - g_al > cmax) break;
+        ++qe;
       }
-      L->segs.push_back(make_int4(s, cb, (int)L->chunks.size(), slot));
-      a = (int64_t)s * m_act + r1;
+      if (qe == q) return false;
+      ChunkDesc ch{};
+      ch.g_al = g_al;
+      ch.row_begin = q;
+      ch.n_rows = qe - q;
+      ch.n_ent = (int)std::max<int64_t>(16, ((base[s] + r[qe].x + 15) & ~(int64_t)15) - g_al);
+      ch.group = g0;
+      ch.s = s;
+      chunks->push_back(ch);
+      q = qe;
     }
   }
-  L->cta_seg[G] = (int)L->segs.size();
-  L->slot_first[N] = (int)L->segs.size();
-  for (int s = N - 1; s >= 0; --s)
-    if (L->slot_first[s] < 0) L->slot_first[s] = L->slot_first[s + 1];
+  (*scen_chunk)[N] = (int)chunks->size();
   return true;
 }
 
@@ -381,94 +361,140 @@ int create_plan(const rpt_problem* pr, const rpt_device_opts* opts, rpt_plan** o
   const int bi = pr->index_width == 16 ? 2 : 4;
   const int bv = pr->value_format == RPT_F32 ? 4 : (pr->value_format == RPT_BF16 ? 2 : 1);
 
-  // ---- row pointers over kept rows ----
-  std::vector<int32_t> rp_h((size_t)N * (m_act + 1));
+  // ---- per-scenario row lists, sorted by decreasing length; entries permuted to match ----
+  RowLists R;
+  R.rec_base.assign(N + 1, 0);
+  R.nrows.assign(N, 0);
+  std::vector<std::vector<int32_t>> order(N);
   for (int s = 0; s < N; ++s) {
     const int32_t* rp = pr->row_ptr[s];
-    int32_t* o = &rp_h[(size_t)s * (m_act + 1)];
-    for (int k = 0; k < m_act; ++k) o[k] = rp[kept[k]];
-    o[m_act] = rp[m];
+    for (int k = 0; k < m_act; ++k) {
+      const int len = rp[kept[k] + 1] - rp[kept[k]];
+      if (len > 0) order[s].push_back(k);
+      else const_term += cs[s] * pr->voxel_w[kept[k]] * pr->presc[kept[k]] * pr->presc[kept[k]];
+    }
+    std::stable_sort(order[s].begin(), order[s].end(), [&](int32_t a, int32_t b) {
+      return rp[kept[a] + 1] - rp[kept[a]] > rp[kept[b] + 1] - rp[kept[b]];
+    });
+    R.nrows[s] = (int)order[s].size();
+    R.rec_base[s + 1] = R.rec_base[s] + R.nrows[s] + 1;
   }
-  // ---- work decomposition: TMA ring (default) or register-direct row blocks ----
-  const double row_cost = 8.0;   // per-row overhead, in units of one entry
-  const int want_path = opts ? opts->row_path : 0;
+  R.rec.resize(R.rec_base[N]);
+  std::vector<int32_t> col_h((size_t)NNZ);
+  std::vector<float> val_h((size_t)NNZ);
+  {
+    auto fill = [&](int s) {
+      const int32_t* rp = pr->row_ptr[s];
+      int4* out = &R.rec[R.rec_base[s]];
+      int32_t pos = 0;
+      for (int q = 0; q < R.nrows[s]; ++q) {
+        const int k = order[s][q];
+        const int32_t a = rp[kept[k]], len = rp[kept[k] + 1] - a;
+        const float wc = (float)(cs[s] * pr->voxel_w[kept[k]]);
+        const float pp = (float)pr->presc[kept[k]];
+        int4 r4;
+        r4.x = pos;
+        std::memcpy(&r4.y, &wc, 4);
+        std::memcpy(&r4.z, &pp, 4);
+        r4.w = k;
+        out[q] = r4;
+        std::memcpy(&col_h[base[s] + pos], pr->col_idx[s] + a, sizeof(int32_t) * len);
+        std::memcpy(&val_h[base[s] + pos], pr->val[s] + a, sizeof(float) * len);
+        pos += len;
+      }
+      out[R.nrows[s]] = make_int4(pos, 0, 0, 0);
+    };
+    const int hw = std::max(1u, std::thread::hardware_concurrency());
+    const int nt = std::min(N, std::min(hw, 32));
+    std::atomic<int> next(0);
+    std::vector<std::thread> th;
+    for (int t = 0; t < nt; ++t)
+      th.emplace_back([&]() {
+        for (int s = next++; s < N; s = next++) fill(s);
+      });
+    for (auto& t : th) t.join();
+  }
+  // ---- work decomposition: register-direct row blocks (default) or bulk-copy ring ----
+  const double per_lane = std::max(0, env_int("RPT_ROW_COST_LANE", 4));   // per-row overhead per lane, in entries
+  // row path: the caller's choice, else RPT_ROW_PATH from the environment, else 1
+  const int want_path = (opts && opts->row_path) ? opts->row_path : env_int("RPT_ROW_PATH", 0);
   std::vector<int4> blocks;
   std::vector<int> blk_first(N + 1, 0);
-  TmaLayout tl;
+  std::vector<ChunkDesc> chunks;
+  std::vector<int> scen_chunk;
   bool use_tma = false;
   int ctas = 0;
   if (want_path == 2) {
     int smem_optin = 0;
     cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, P->device);
     dp.cmax = std::max(64, env_int("RPT_TMA_CMAX", 4096)) & ~15;
-    dp.rmax = std::max(8, env_int("RPT_TMA_RMAX", 256));
-    dp.stages = std::min(8, std::max(2, env_int("RPT_TMA_STAGES", 3)));
+    dp.rmax = std::max(8, env_int("RPT_TMA_RMAX", 512));
+    dp.stages = std::min(8, std::max(2, env_int("RPT_TMA_STAGES", 4)));
     ctas = (opts && opts->ctas_per_sm > 0) ? opts->ctas_per_sm : 1;
     const size_t need = tma_smem_bytes(n_pad, dp.cmax, dp.rmax, dp.stages, bv, bi, true);
-    if (need * ctas <= (size_t)smem_optin * (ctas == 1 ? 1 : 1) && need <= (size_t)smem_optin)
-      use_tma = build_tma_layout(rp_h, base, N, m_act, P->sm_count * ctas, dp.cmax, dp.rmax, row_cost, &tl);
-    if (!use_tma && want_path == 2) {
+    if (need + 1024 <= (size_t)smem_optin)
+      use_tma = build_chunks(R, base, N, dp.cmax, dp.rmax, &chunks, &scen_chunk);
+    if (!use_tma) {
       free_plan(P);
-      set_error("bulk-copy row path not possible for this plan (shared memory or a row longer than RPT_TMA_CMAX)");
+      set_error("bulk-copy row path not possible for this plan (shared memory, or a row longer than RPT_TMA_CMAX)");
       return RPT_EUNSUPPORTED;
     }
-  }
-  if (use_tma) {
     dp.path = 1;
     dp.grid = P->sm_count * ctas;
-    dp.nblocks = (int)tl.segs.size();
-    blk_first = tl.slot_first;
+    dp.nblocks = dp.grid * N;          // one slot per (CTA, scenario)
+    dp.slot_cap = dp.grid;
   } else {
     dp.path = 0;
     ctas = (opts && opts->ctas_per_sm > 0) ? opts->ctas_per_sm : 2;
-    double total = (double)NNZ + row_cost * (double)m_act * N;
+    double total = 0.0;
+    for (int s = 0; s < N; ++s) {
+      const int4* r = &R.rec[R.rec_base[s]];
+      for (int q = 0; q < R.nrows[s]; ++q) total += row_cost(r[q + 1].x - r[q].x, per_lane);
+    }
     const double target = std::max(1.0, total / (double)(P->sm_count * ctas));
     for (int s = 0; s < N; ++s) {
-      const int32_t* o = &rp_h[(size_t)s * (m_act + 1)];
-      const double cost_s = (double)nnz[s] + row_cost * m_act;
-      int nb = std::max(1, (int)std::lround(cost_s / target));
-      nb = std::min(nb, m_act);
+      const int4* r = &R.rec[R.rec_base[s]];
       blk_first[s] = (int)blocks.size();
-      int r = 0;
-      for (int b = 0; b < nb; ++b) {
-        const double goal = cost_s * (b + 1) / nb;
-        int r1 = r;
-        if (b == nb - 1) {
-          r1 = m_act;
-        } else {
-          // smallest r1 with cost(rows [0, r1)) >= goal
-          int lo = r, hi = m_act;
-          while (lo < hi) {
-            const int mid = (lo + hi) / 2;
-            const double c = (double)o[mid] + row_cost * mid;
-            if (c >= goal) hi = mid;
-            else lo = mid + 1;
-          }
-          r1 = std::max(lo, r);
+      // runs of equal lanes-per-row, each cut into blocks of about `target` cost
+      int q = 0;
+      while (q < R.nrows[s]) {
+        const int g0 = lanes_for(r[q + 1].x - r[q].x);
+        int q1 = q;
+        double run = 0.0;
+        while (q1 < R.nrows[s] && lanes_for(r[q1 + 1].x - r[q1].x) == g0) {
+          run += row_cost(r[q1 + 1].x - r[q1].x, per_lane);
+          ++q1;
         }
-        blocks.push_back(make_int4(s, r, r1, 0));
-        r = r1;
+        const int nb = std::max(1, (int)std::lround(run / target));
+        double acc = 0.0, goal = run / nb;
+        int qb = q;
+        for (int k = q; k < q1; ++k) {
+          acc += row_cost(r[k + 1].x - r[k].x, per_lane);
+          if (acc >= goal - 1e-9 && (int)blocks.size() - blk_first[s] < 1 << 30) {
+            blocks.push_back(make_int4(s, qb, k + 1, g0));
+            qb = k + 1;
+            acc = 0.0;
+          }
+        }
+        if (qb < q1) blocks.push_back(make_int4(s, qb, q1, g0));
+        q = q1;
       }
+      if ((int)blocks.size() == blk_first[s]) blocks.push_back(make_int4(s, 0, 0, 1));   // empty scenario
     }
     blk_first[N] = (int)blocks.size();
     dp.nblocks = (int)blocks.size();
     dp.grid = dp.nblocks;
+    dp.slot_cap = 1;
+    for (int s = 0; s < N; ++s) dp.slot_cap = std::max(dp.slot_cap, blk_first[s + 1] - blk_first[s]);
   }
-  // per-row records {row_ptr, c_s w_i, p_i, 0} for the bulk copies
-  std::vector<int4> rec_h((size_t)N * (m_act + 1));
-  for (int s = 0; s < N; ++s) {
-    const int32_t* o = &rp_h[(size_t)s * (m_act + 1)];
-    for (int k = 0; k <= m_act; ++k) {
-      const float wc = k < m_act ? (float)(cs[s] * pr->voxel_w[kept[k]]) : 0.f;
-      const float pp = k < m_act ? (float)pr->presc[kept[k]] : 0.f;
-      int4 r4;
-      r4.x = o[k];
-      std::memcpy(&r4.y, &wc, 4);
-      std::memcpy(&r4.z, &pp, 4);
-      r4.w = 0;
-      rec_h[(size_t)s * (m_act + 1) + k] = r4;
+  // slot lists: static for the register path (block b of scenario s), written
+  // by the kernel for the bulk-copy path
+  std::vector<int> slot_count(N, 0), slot_list((size_t)N * dp.slot_cap, 0);
+  if (!use_tma)
+    for (int s = 0; s < N; ++s) {
+      slot_count[s] = blk_first[s + 1] - blk_first[s];
+      for (int k = 0; k < slot_count[s]; ++k) slot_list[(size_t)s * dp.slot_cap + k] = blk_first[s] + k;
     }
-  }
   std::vector<float> diag_h((size_t)N * n);
   for (int s = 0; s < N; ++s)
     for (int j = 0; j < n; ++j) diag_h[(size_t)s * n + j] = (float)(cs[s] * chk[s].diag[j]);
@@ -477,21 +503,22 @@ int create_plan(const rpt_problem* pr, const rpt_device_opts* opts, rpt_plan** o
   // entry arrays are padded so that 16-entry aligned bulk copies stay inside them
   constexpr int64_t kPad = 64;
   Alloc A{P};
-  int32_t* d_rp = A.get<int32_t>(rp_h.size());
   int64_t* d_base = A.get<int64_t>(N);
   int32_t* d_col32 = A.get<int32_t>(NNZ + kPad);   // replaced by 16-bit indices if requested
   float* d_val32 = A.get<float>(NNZ + kPad);       // replaced by quantised values if requested
-  int4* d_rec = A.get<int4>(rec_h.size());
-  ChunkDesc* d_chunks = use_tma ? A.get<ChunkDesc>(tl.chunks.size()) : nullptr;
-  int4* d_segs = use_tma ? A.get<int4>(tl.segs.size()) : nullptr;
-  int* d_ctaseg = use_tma ? A.get<int>(tl.cta_seg.size()) : nullptr;
+  int4* d_rec = A.get<int4>(R.rec.size());
+  int* d_recbase = A.get<int>(N + 1);
+  ChunkDesc* d_chunks = use_tma ? A.get<ChunkDesc>(chunks.size()) : nullptr;
+  int* d_scen_chunk = use_tma ? A.get<int>(N + 1) : nullptr;
+  int* d_qnext = use_tma ? A.get<int>(N) : nullptr;
+  unsigned char* d_visited = use_tma ? A.get<unsigned char>((size_t)N * dp.grid) : nullptr;
+  int* d_slot_count = A.get<int>(N);
+  int* d_slot_list = A.get<int>(slot_list.size());
+  double* d_objs = A.get<double>(N);
+  unsigned int* d_done = A.get<unsigned int>(1);
   P->err = A.get<int>(1);
   P->diag = A.get<float>(diag_h.size());
-  float* d_w = A.get<float>(m_act);
-  float* d_p = A.get<float>(m_act);
-  float* d_cs = A.get<float>(N);
   int4* d_blocks = use_tma ? nullptr : A.get<int4>(blocks.size());
-  int* d_bf = A.get<int>(N + 1);
   P->lb = A.get<double>(n);
   P->ub = A.get<double>(n);
   const size_t Nn = (size_t)N * n;
@@ -542,12 +569,6 @@ int create_plan(const rpt_problem* pr, const rpt_device_opts* opts, rpt_plan** o
     return cuda_fail(e, "event");
   }
   cudaStream_t st = P->stream;
-  std::vector<float> wf(m_act), pf(m_act), csf(N);
-  for (int k = 0; k < m_act; ++k) {
-    wf[k] = (float)pr->voxel_w[kept[k]];
-    pf[k] = (float)pr->presc[kept[k]];
-  }
-  for (int s = 0; s < N; ++s) csf[s] = (float)cs[s];
 #define RPT_CP(dst, src, bytes)                                                            \
   do {                                                                                     \
     if ((bytes) > 0 && (e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st))) { \
@@ -555,29 +576,28 @@ int create_plan(const rpt_problem* pr, const rpt_device_opts* opts, rpt_plan** o
       return cuda_fail(e, "upload");                                                       \
     }                                                                                      \
   } while (0)
-  RPT_CP(d_rp, rp_h.data(), rp_h.size() * sizeof(int32_t));
   RPT_CP(d_base, base.data(), N * sizeof(int64_t));
-  for (int s = 0; s < N; ++s) {
-    RPT_CP(d_col32 + base[s], pr->col_idx[s], nnz[s] * sizeof(int32_t));
-    RPT_CP(d_val32 + base[s], pr->val[s], nnz[s] * sizeof(float));
-  }
-  RPT_CP(d_w, wf.data(), m_act * sizeof(float));
-  RPT_CP(d_p, pf.data(), m_act * sizeof(float));
-  RPT_CP(d_cs, csf.data(), N * sizeof(float));
+  RPT_CP(d_col32, col_h.data(), (size_t)NNZ * sizeof(int32_t));
+  RPT_CP(d_val32, val_h.data(), (size_t)NNZ * sizeof(float));
+  RPT_CP(d_rec, R.rec.data(), R.rec.size() * sizeof(int4));
+  RPT_CP(d_recbase, R.rec_base.data(), (N + 1) * sizeof(int));
   if (!use_tma) RPT_CP(d_blocks, blocks.data(), blocks.size() * sizeof(int4));
-  RPT_CP(d_rec, rec_h.data(), rec_h.size() * sizeof(int4));
   RPT_CP(P->diag, diag_h.data(), diag_h.size() * sizeof(float));
   if (use_tma) {
-    RPT_CP(d_chunks, tl.chunks.data(), tl.chunks.size() * sizeof(ChunkDesc));
-    RPT_CP(d_segs, tl.segs.data(), tl.segs.size() * sizeof(int4));
-    RPT_CP(d_ctaseg, tl.cta_seg.data(), tl.cta_seg.size() * sizeof(int));
+    RPT_CP(d_chunks, chunks.data(), chunks.size() * sizeof(ChunkDesc));
+    RPT_CP(d_scen_chunk, scen_chunk.data(), (N + 1) * sizeof(int));
   }
-  RPT_CP(d_bf, blk_first.data(), (N + 1) * sizeof(int));
+  RPT_CP(d_slot_count, slot_count.data(), N * sizeof(int));
+  RPT_CP(d_slot_list, slot_list.data(), slot_list.size() * sizeof(int));
   RPT_CP(P->lb, lb.data(), n * sizeof(double));
   RPT_CP(P->ub, ub.data(), n * sizeof(double));
 #undef RPT_CP
   if ((e = cudaMemsetAsync(P->cnt_s, 0, sizeof(unsigned int) * N, st)) ||
       (e = cudaMemsetAsync(P->err, 0, sizeof(int), st)) ||
+      (e = cudaMemsetAsync(d_done, 0, sizeof(unsigned int), st)) ||
+      (e = cudaMemsetAsync(d_objs, 0, sizeof(double) * N, st)) ||
+      (use_tma && (e = cudaMemsetAsync(d_qnext, 0, sizeof(int) * N, st))) ||
+      (use_tma && (e = cudaMemsetAsync(d_visited, 0, (size_t)N * dp.grid, st))) ||
       (e = cudaMemsetAsync(d_col32 + NNZ, 0, sizeof(int32_t) * kPad, st)) ||
       (e = cudaMemsetAsync(d_val32 + NNZ, 0, sizeof(float) * kPad, st)) ||
       (e = cudaMemsetAsync(P->ctl, 0, sizeof(Ctl), st)) ||
@@ -586,18 +606,20 @@ int create_plan(const rpt_problem* pr, const rpt_device_opts* opts, rpt_plan** o
     free_plan(P);
     return cuda_fail(e, "memset");
   }
-  dp.row_ptr = d_rp;
   dp.nnz_base = d_base;
-  dp.w = d_w;
-  dp.p = d_p;
-  dp.cs = d_cs;
   dp.blocks = d_blocks;
   dp.rowrec = d_rec;
+  dp.rec_base = d_recbase;
   dp.chunks = d_chunks;
-  dp.segs = d_segs;
-  dp.cta_seg = d_ctaseg;
+  dp.scen_chunk = d_scen_chunk;
+  dp.qnext = d_qnext;
+  dp.visited = d_visited;
+  dp.slot_count = d_slot_count;
+  dp.slot_list = d_slot_list;
+  dp.objs = d_objs;
+  dp.objp = P->objp;
+  dp.done_ctr = d_done;
   dp.err = P->err;
-  dp.blk_first = d_bf;
   dp.col32 = d_col32;
   dp.val32 = d_val32;
   // ---- quantised values / narrow indices ----
@@ -679,7 +701,9 @@ int create_plan(const rpt_problem* pr, const rpt_device_opts* opts, rpt_plan** o
   S.N = N;
   S.m_active = m_act;
   S.nnz = NNZ;
-  S.matrix_bytes = NNZ * (int64_t)(bi + bv) + (int64_t)N * (m_act + 1) * 4;
+  // values and indices, plus one 4-byte row offset per stored row (the records'
+  // weight and prescription are counted by the kernels' algorithmic bytes)
+  S.matrix_bytes = NNZ * (int64_t)(bi + bv) + (int64_t)(R.rec_base[N]) * 4;
   S.value_format = pr->value_format;
   S.index_width = pr->index_width;
   S.row_blocks = dp.nblocks;

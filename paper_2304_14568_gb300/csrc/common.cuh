@@ -3,23 +3,27 @@
 // Layout in HBM (one plan):
 //   rows      : the m_act voxel rows kept on the device (rows with no entry in
 //               any scenario are dropped; their constant w p^2 goes to const_term)
-//   row_ptr   : int32 [N][m_act+1], offsets within scenario s
-//   rowrec    : int4  [N][m_act+1] per-row record {row_ptr, c_s w_i, p_i, 0}
-//               (16 bytes, so a run of rows is one bulk copy)
+//   row lists : per scenario, its non-empty rows sorted by decreasing length
+//               (rows empty in that scenario add c_s w p^2 to const_term); the
+//               entries are stored permuted into that order, so each row is
+//               contiguous and consecutive rows are adjacent
+//   rowrec    : int4 per listed row {entry offset, c_s w_i, p_i, kept-row index},
+//               rec_base[s]..: scenario s's rows plus a terminator record
+//               holding its entry count (16 bytes: a run of rows is one bulk copy)
 //   col, val  : concatenated over scenarios, scenario s starts at nnz_base[s];
 //               allocations are padded so that 16-entry aligned bulk copies
 //               never leave them
-//   w, p      : float32 [m_act] voxel weight and prescription (shared by scenarios)
-//   cs        : float32 [N] scenario weights c_s
 //   colscale  : float32 [N][n_pad] per-column scales of quantised values
 // Work decomposition of one row pass:
-//   path 0 (register): `blocks` = nnz-balanced row blocks, one CTA each
-//   path 1 (TMA ring): the scenario-major sequence of all rows is cut into
-//               `grid` equal-cost slices, one persistent CTA each; a slice is
-//               1..3 `segs` (one scenario each), a segment is a run of
-//               row-aligned `chunks` that each fit one shared-memory stage.
-//   Either way every work unit (block or segment) owns one partial slot of
-//   n_pad floats; the slots of scenario s are [blk_first[s], blk_first[s+1]).
+//   path 0 (register): `blocks` = cost-balanced runs of rows, one CTA and one
+//               partial slot each
+//   path 1 (TMA ring): every scenario's row list is cut into row-aligned
+//               `chunks` that each fit one shared-memory stage; one persistent
+//               CTA per SM pulls chunks from per-scenario queues (starting at a
+//               home scenario, moving on when it is exhausted), and keeps one
+//               partial slot per scenario it visited (slot = cta * N + s).
+//   The CTA that finishes last compacts the slots of every scenario into an
+//   ordered list, sums the objective per scenario and resets the queues.
 #pragma once
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
@@ -34,9 +38,11 @@ constexpr int kVecThreads = 256;      // threads of a vector CTA (one column eac
 
 struct ChunkDesc {
   long long g_al;                     // first copied entry (global index, multiple of 16)
-  int row_begin;                      // first row of the chunk (scenario-relative)
-  int n_rows;                         // rows in the chunk
+  int row_begin;                      // first row of the chunk (index in the scenario's row list)
+  int n_rows;                         // rows in the chunk (-1: end-of-work marker)
   int n_ent;                          // copied entries (multiple of 16)
+  int group;                          // lanes per row (1..32), the same for every row of the chunk
+  int s;                              // scenario
   int pad;
 };
 
@@ -47,8 +53,7 @@ struct DevPlan {
   int path;                           // 0 register, 1 TMA ring
   int grid;                           // CTAs of one row pass
   int cmax, rmax, stages;             // TMA path: entries / rows per stage, ring depth
-  int pad0;
-  const int32_t* row_ptr;             // [N][m_act+1]
+  int slot_cap;                       // capacity of each scenario's slot list
   const int64_t* nnz_base;            // [N]
   const int32_t* col32;               // [NNZ] (index_width 32)
   const uint16_t* col16;              // [NNZ] (index_width 16)
@@ -56,15 +61,22 @@ struct DevPlan {
   const __nv_bfloat16* valbf;         // [NNZ] (RPT_BF16)
   const __nv_fp8_e4m3* val8;          // [NNZ] (RPT_FP8E4M3)
   const float* colscale;              // [N][n_pad] (quantised formats) or null
-  const float* w;                     // [m_act]
-  const float* p;                     // [m_act]
-  const float* cs;                    // [N]
-  const int4* blocks;                 // path 0: [nblocks] (s, row_begin, row_end, 0)
-  const int* blk_first;               // [N+1]
-  const int4* rowrec;                 // [N][m_act+1]
-  const ChunkDesc* chunks;            // path 1
-  const int4* segs;                   // path 1: (s, chunk_begin, chunk_end, slot)
-  const int* cta_seg;                 // path 1: [grid+1]
+  const int4* blocks;                 // path 0: [grid] (s, first row, end row, lanes per row)
+  // Partial slots of the last pass, per scenario: slot_count[s] slots listed in
+  // slot_list[s * slot_cap ...] in increasing order (static for path 0, written
+  // by the finishing CTA of every pass for path 1); objs[s] = objective of
+  // scenario s in the last objective pass.
+  int* slot_count;                    // [N]
+  int* slot_list;                     // [N][slot_cap]
+  double* objs;                       // [N]
+  double* objp;                       // [nblocks] per-slot objective partial sums
+  unsigned int* done_ctr;             // finishing-CTA counter (self-resetting)
+  int* qnext;                         // path 1: [N] per-scenario chunk queues (self-resetting)
+  unsigned char* visited;             // path 1: [N][grid] slots written in this pass
+  const int* scen_chunk;              // path 1: [N+1] chunk range of each scenario
+  const int4* rowrec;                 // row records {start, c_s w_i, p_i, kept-row index}
+  const int* rec_base;                // [N+1] first record of each scenario's row list
+  const ChunkDesc* chunks;            // path 1: scenario-major chunk list
   int* err;                           // device error word (bounded waits that ran out)
 };
 
@@ -126,8 +138,8 @@ namespace rpt {
 //         vector (v_stride = 0)
 // active: [N] int flags or null (work of inactive scenarios is skipped)
 // partial: [nblocks][n_pad] per-slot accumulators (modes kNormal, kResid)
-// objp:    [nblocks] per-slot objective partial sums (modes kResid, kObj, kDose)
 // dose:    [N][m_act] (mode kDose)
+// The per-slot objective sums go to P.objp and, per scenario, to P.objs.
 void* rowpass_kernel(const DevPlan& P, int mode);
 size_t rowpass_smem(const DevPlan& P, int mode);
 int rowpass_threads(const DevPlan& P);

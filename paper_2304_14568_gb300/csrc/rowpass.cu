@@ -18,9 +18,10 @@
 //    matrix through an S-stage shared-memory ring.  One producer lane issues
 //    bulk asynchronous copies (cp.async.bulk, completion counted on an
 //    mbarrier) of row-aligned chunks: the row records, the values and the
-//    indices.  Fifteen consumer warps take rows of a resident chunk from a
-//    shared counter, one warp per row, and release the stage through a second
-//    mbarrier.  Every wait is bounded; a wait that runs out sets the plan's
+//    indices; it publishes each chunk's descriptor in shared memory and
+//    prefetches the next one.  Fifteen consumer warps split the rows of a
+//    resident chunk statically (warp w takes rows w, w+15, ...), one warp per
+//    row, and release the stage through a second mbarrier.  Every wait is bounded; a wait that runs out sets the plan's
 //    error word and the kernel drains its copies and returns.
 //  * k_rowpass (register path): nnz-balanced row blocks, one CTA each; warps
 //    load row entries straight into registers with a one-row prefetch.
@@ -138,10 +139,105 @@ __device__ __forceinline__ void flush_acc(const DevPlan& P, int s, const float* 
   }
 }
 
+// One group of G lanes processes one row (G in {1, 2, ..., 32}); a warp covers
+// 32/G rows at once.  Each lane keeps up to KR of its row's entries in
+// registers between the dot and the scatter; longer rows (only with G = 32)
+// re-read the rest.  Returns nothing; accumulates into acc / obj / dose.
+template <int MODE, typename VT, typename IT, int KR, bool kSmem>
+__device__ __forceinline__ void process_rows(const int4* __restrict__ rec, int r, bool valid, int G, int sl,
+                                             const VT* __restrict__ val, const IT* __restrict__ col,
+                                             long long off, const float* sv, float* acc, double& obj,
+                                             float* __restrict__ dose, size_t dose_base) {
+  constexpr bool kScatter = (MODE == kNormal || MODE == kResid);
+  int4 ra = make_int4(0, 0, 0, 0);
+  int lo = 0, hi = 0;
+  if (valid) {
+    ra = rec[r];
+    lo = (int)(ra.x + off);
+    hi = (int)(rec[r + 1].x + off);
+  }
+  float vr[KR];
+  int cr[KR];
+  float t = 0.f;
+#pragma unroll
+  for (int k = 0; k < KR; ++k) {
+    const int idx = lo + sl + G * k;
+    if (idx < hi) {
+      vr[k] = to_f<VT>(val[idx]);
+      cr[k] = (int)col[idx];
+      t = fmaf(vr[k], sv[cr[k]], t);
+    } else {
+      vr[k] = 0.f;
+      cr[k] = 0;
+    }
+  }
+  for (int idx = lo + G * KR + sl; idx < hi; idx += G) t = fmaf(to_f<VT>(val[idx]), sv[(int)col[idx]], t);
+  for (int o = G >> 1; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  const float wc = __int_as_float(ra.y);
+  float coef;
+  if (MODE == kNormal) {
+    coef = wc * t;
+  } else {
+    const float rr = t - __int_as_float(ra.z);
+    coef = wc * rr;
+    if (valid && sl == 0) {
+      obj += (double)(coef * rr);
+      if (MODE == kDose) dose[dose_base + ra.w] = t;
+    }
+  }
+  if (kScatter) {
+#pragma unroll
+    for (int k = 0; k < KR; ++k)
+      if (lo + sl + G * k < hi) atomicAdd(&acc[cr[k]], coef * vr[k]);
+    for (int idx = lo + G * KR + sl; idx < hi; idx += G)
+      atomicAdd(&acc[(int)col[idx]], coef * to_f<VT>(val[idx]));
+  }
+}
+
+// The CTA that finishes last publishes the pass's bookkeeping: per scenario,
+// the ordered list of partial slots that were written (path 1; static for
+// path 0) and the objective summed in slot order; it also resets the chunk
+// queues and the finishing counter for the next pass.  Every CTA must call it.
+template <bool kObjective>
+__device__ __forceinline__ void finish_pass(const DevPlan& P) {
+  __shared__ bool last_cta;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last_cta = (atomicAdd(P.done_ctr, 1u) + 1u == gridDim.x);
+  }
+  __syncthreads();
+  if (!last_cta) return;
+  __threadfence();
+  for (int s = threadIdx.x; s < P.N; s += blockDim.x) {
+    double o = 0.0;
+    if (P.path == 1) {
+      int cnt = 0;
+      for (int c = 0; c < P.grid; ++c) {
+        volatile unsigned char* vis = P.visited + (size_t)s * P.grid + c;
+        if (*vis) {
+          const int slot = c * P.N + s;
+          P.slot_list[(size_t)s * P.slot_cap + cnt++] = slot;
+          if (kObjective) o += __ldcg(&P.objp[slot]);
+          *vis = 0;
+        }
+      }
+      P.slot_count[s] = cnt;
+      P.qnext[s] = 0;
+    } else if (kObjective) {
+      const int cnt = P.slot_count[s];
+      for (int k = 0; k < cnt; ++k) o += __ldcg(&P.objp[P.slot_list[(size_t)s * P.slot_cap + k]]);
+    }
+    if (kObjective) P.objs[s] = o;
+  }
+  if (threadIdx.x == 0) *P.done_ctr = 0u;
+}
+
 // ---------------------------------------------------------------------------
 // TMA-ring row pass
 // ---------------------------------------------------------------------------
-constexpr int kHdr = 512;   // mbarriers (2 x 8), row counters (8), per-warp objective (16 doubles)
+constexpr int kHdr = 1024;  // mbarriers (2 x 8 x 8 B), chunk descriptors (8 x 32 B), per-warp objective (16 doubles)
+constexpr int kBatch = 4;   // chunks per queue pull
 
 template <int MODE, typename VT, typename IT>
 __global__ void __launch_bounds__(kTmaThreads, 1)
@@ -153,8 +249,8 @@ k_rowpass_tma(DevPlan P, const float* __restrict__ vin, int v_stride, const int*
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t* full = reinterpret_cast<uint64_t*>(smem);
   uint64_t* empty = full + 8;
-  int* rowctr = reinterpret_cast<int*>(smem + 128);
-  double* wobj = reinterpret_cast<double*>(smem + 256);
+  ChunkDesc* sdesc = reinterpret_cast<ChunkDesc*>(smem + 128);   // one per stage
+  double* wobj = reinterpret_cast<double*>(smem + 512);
   float* sv = reinterpret_cast<float*>(smem + kHdr);
   float* acc = sv + P.n_pad;
   const int S = P.stages;
@@ -173,157 +269,165 @@ k_rowpass_tma(DevPlan P, const float* __restrict__ vin, int v_stride, const int*
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
-  const int seg0 = P.cta_seg[blockIdx.x], seg1 = P.cta_seg[blockIdx.x + 1];
 
   if (warp == 0) {
-    // ---------------- producer ----------------
+    // ---------------- producer (one lane) ----------------
     if (lane == 0) {
       const VT* gval = vals<VT>(P);
       const IT* gcol = cols<IT>(P);
-      int gk = 0;
+      int st = 0, ph = 0, issued = 0;
       bool ok = true;
-      for (int sg = seg0; sg < seg1 && ok; ++sg) {
-        const int4 seg = P.segs[sg];
-        if (active != nullptr && active[seg.x] == 0) continue;
-        const int4* rec = P.rowrec + (size_t)seg.x * (P.m_act + 1);
-        for (int c = seg.y; c < seg.z; ++c, ++gk) {
-          const int st = gk % S;
-          if (gk >= S && !mbar_wait(smem_u32(&empty[st]), (uint32_t)((gk / S) - 1) & 1u)) {
+      // walk the scenarios starting at this CTA's home scenario, taking chunks
+      // from each scenario's queue until all queues are empty
+      const int home = (int)(((long long)blockIdx.x * P.N) / gridDim.x);
+      for (int k = 0; k < P.N && ok; ++k) {
+        const int sc = (home + k) % P.N;
+        if (active != nullptr && active[sc] == 0) continue;
+        const int c0 = P.scen_chunk[sc], c1 = P.scen_chunk[sc + 1];
+        // chunks are pulled in batches of kBatch; the next batch is requested when
+        // a batch starts and each descriptor is fetched one chunk ahead, so the
+        // queue and descriptor latencies overlap the stage waits
+        int cb = c0 + kBatch * atomicAdd(&P.qnext[sc], 1);
+        ChunkDesc nxt{};
+        if (cb < c1) nxt = P.chunks[cb];
+        while (cb < c1 && ok) {
+          const int cbn = c0 + kBatch * atomicAdd(&P.qnext[sc], 1);
+          const int ce = min(cb + kBatch, c1);
+          for (int c = cb; c < ce; ++c) {
+          const ChunkDesc ch = nxt;
+          const int nn = (c + 1 < ce) ? c + 1 : cbn;
+          if (nn < c1) nxt = P.chunks[nn];
+          // stage st is free once its previous use (phase ph ^ 1) was released
+          if (issued >= S && !mbar_wait(smem_u32(&empty[st]), (uint32_t)(ph ^ 1))) {
             ok = false;
             break;
           }
-          const ChunkDesc ch = P.chunks[c];
           unsigned char* sp = stage0 + (size_t)st * stage_bytes;
           const uint32_t rb = (uint32_t)(ch.n_rows + 1) * 16u;
           const uint32_t vb = (uint32_t)ch.n_ent * (uint32_t)sizeof(VT);
           const uint32_t cb = (uint32_t)ch.n_ent * (uint32_t)sizeof(IT);
-          rowctr[st] = 0;
+          const int4* rec = P.rowrec + P.rec_base[sc];
+          sdesc[st] = ch;
           const uint32_t fb = smem_u32(&full[st]);
           mbar_arrive_expect_tx(fb, rb + vb + cb);
           bulk_g2s(smem_u32(sp), rec + ch.row_begin, rb, fb);
           bulk_g2s(smem_u32(sp + rec_bytes), gval + ch.g_al, vb, fb);
           bulk_g2s(smem_u32(sp + rec_bytes + val_bytes), gcol + ch.g_al, cb, fb);
+          ++issued;
+          if (++st == S) {
+            st = 0;
+            ph ^= 1;
+          }
+          }
+          cb = cbn;
         }
+      }
+      // end-of-work marker in the next stage
+      if (ok && (issued < S || mbar_wait(smem_u32(&empty[st]), (uint32_t)(ph ^ 1)))) {
+        ChunkDesc endm{};
+        endm.n_rows = -1;
+        sdesc[st] = endm;
+        mbar_arrive(smem_u32(&full[st]));
+        ++issued;
+        if (++st == S) {
+          st = 0;
+          ph ^= 1;
+        }
+      } else {
+        ok = false;
       }
       if (!ok) atomicExch(P.err, 1);
       // drain: the last use of every stage has completed before the CTA exits
-      for (int q = (gk > S ? gk - S : 0); q < gk; ++q)
-        if (!mbar_wait(smem_u32(&full[q % S]), (uint32_t)(q / S) & 1u)) atomicExch(P.err, 2);
+      for (int q = 0; q < S && q < issued; ++q) {
+        if (--st < 0) {
+          st = S - 1;
+          ph ^= 1;
+        }
+        if (!mbar_wait(smem_u32(&full[st]), (uint32_t)ph)) atomicExch(P.err, 2);
+      }
     }
   } else {
     // ---------------- consumers ----------------
     const int cw = warp - 1;
     const int ct = tid - 32;
-    int gk = 0;
-    bool ok = true;
-    for (int sg = seg0; sg < seg1; ++sg) {
-      const int4 seg = P.segs[sg];
-      const int s = seg.x;
-      if (active != nullptr && active[s] == 0) continue;
-      named_sync(1, NCW * 32);                     // previous segment fully flushed
-      stage_vector<kScatter>(P, vin, v_stride, s, sv, acc, ct, NCW * 32);
-      named_sync(1, NCW * 32);
-      const long long base = P.nnz_base[s];
-      double obj = 0.0;
-      for (int c = seg.y; c < seg.z; ++c, ++gk) {
-        const int st = gk % S;
-        if (ok && !mbar_wait(smem_u32(&full[st]), (uint32_t)(gk / S) & 1u)) {
-          ok = false;
-          if (lane == 0) atomicExch(P.err, 3);
-        }
-        if (ok) {
-          const ChunkDesc ch = P.chunks[c];
-          const unsigned char* sp = stage0 + (size_t)st * stage_bytes;
-          const int4* rec = reinterpret_cast<const int4*>(sp);
-          const VT* val = reinterpret_cast<const VT*>(sp + rec_bytes);
-          const IT* col = reinterpret_cast<const IT*>(sp + rec_bytes + val_bytes);
-          const long long off = base - ch.g_al;
-          for (;;) {
-            int r = 0;
-            if (lane == 0) r = atomicAdd(&rowctr[st], 1);
-            r = __shfl_sync(0xffffffffu, r, 0);
-            if (r >= ch.n_rows) break;
-            const int4 ra = rec[r];
-            const int lo = (int)(ra.x + off);
-            const int hi = (int)(rec[r + 1].x + off);
-            float vr[KR];
-            int cr[KR];
-            float t = 0.f;
-#pragma unroll
-            for (int k = 0; k < KR; ++k) {
-              const int idx = lo + lane + 32 * k;
-              if (idx < hi) {
-                vr[k] = to_f<VT>(val[idx]);
-                cr[k] = (int)col[idx];
-                t = fmaf(vr[k], sv[cr[k]], t);
-              } else {
-                vr[k] = 0.f;
-                cr[k] = 0;
-              }
-            }
-            for (int idx = lo + 32 * KR + lane; idx < hi; idx += 32)
-              t = fmaf(to_f<VT>(val[idx]), sv[(int)col[idx]], t);
-            t = warp_sum(t);
-            const float wc = __int_as_float(ra.y);
-            float coef;
-            if (MODE == kNormal) {
-              coef = wc * t;
-            } else {
-              const float rr = t - __int_as_float(ra.z);
-              coef = wc * rr;
-              if (lane == 0) {
-                obj += (double)(coef * rr);
-                if (MODE == kDose) dose[(size_t)s * P.m_act + ch.row_begin + r] = t;
-              }
-            }
-            if (kScatter) {
-#pragma unroll
-              for (int k = 0; k < KR; ++k)
-                if (lo + lane + 32 * k < hi) atomicAdd(&acc[cr[k]], coef * vr[k]);
-              for (int idx = lo + 32 * KR + lane; idx < hi; idx += 32)
-                atomicAdd(&acc[(int)col[idx]], coef * to_f<VT>(val[idx]));
-            }
-          }
-        }
-        __syncwarp();
-        if (lane == 0) mbar_arrive(smem_u32(&empty[st]));
+    int st = 0, ph = 0;
+    int s = -1;                 // scenario whose vector is staged
+    long long base = 0;
+    double obj = 0.0;
+    for (;;) {
+      if (!mbar_wait(smem_u32(&full[st]), (uint32_t)ph)) {
+        if (lane == 0) atomicExch(P.err, 3);
+        break;
       }
+      const ChunkDesc ch = sdesc[st];
+      if (ch.n_rows >= 0 && ch.s != s) {
+        // scenario switch: publish the finished scenario's slot, stage the next vector
+        if (s >= 0) {
+          obj = warp_sum_d(obj);
+          if (lane == 0) wobj[cw] = obj;
+          obj = 0.0;
+          named_sync(1, NCW * 32);
+          const int slot = blockIdx.x * P.N + s;
+          flush_acc<kScatter>(P, s, acc, partial + (size_t)slot * P.n_pad, ct, NCW * 32);
+          if (ct == 0) {
+            if (MODE != kNormal) {
+              double tsum = 0.0;
+              for (int k = 0; k < NCW; ++k) tsum += wobj[k];
+              objp[slot] = tsum;
+            }
+            P.visited[(size_t)s * P.grid + blockIdx.x] = 1;
+          }
+          named_sync(1, NCW * 32);
+        }
+        s = ch.s;
+        base = P.nnz_base[s];
+        stage_vector<kScatter>(P, vin, v_stride, s, sv, acc, ct, NCW * 32);
+        named_sync(1, NCW * 32);
+      }
+      if (ch.n_rows < 0) break;   // end of work (every consumer warp sees it)
+      const unsigned char* sp = stage0 + (size_t)st * stage_bytes;
+      const int4* rec = reinterpret_cast<const int4*>(sp);
+      const VT* val = reinterpret_cast<const VT*>(sp + rec_bytes);
+      const IT* col = reinterpret_cast<const IT*>(sp + rec_bytes + val_bytes);
+      const long long off = base - ch.g_al;
+      const int G = ch.group;                // lanes per row
+      const int rpw = 32 / G;                // rows per warp step
+      const int sl = lane & (G - 1), sub = lane / G;
+      const size_t dose_base = (size_t)s * P.m_act;
+      for (int r0 = cw * rpw; r0 < ch.n_rows; r0 += NCW * rpw) {
+        const int r = r0 + sub;
+        process_rows<MODE, VT, IT, KR, true>(rec, r, r < ch.n_rows, G, sl, val, col, off, sv, acc, obj,
+                                              dose, dose_base);
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&empty[st]));
+      if (++st == S) {
+        st = 0;
+        ph ^= 1;
+      }
+    }
+    if (s >= 0) {
+      obj = warp_sum_d(obj);
       if (lane == 0) wobj[cw] = obj;
       named_sync(1, NCW * 32);
-      flush_acc<kScatter>(P, s, acc, partial + (size_t)seg.w * P.n_pad, ct, NCW * 32);
-      if (MODE != kNormal && ct == 0) {
-        double tsum = 0.0;
-        for (int k = 0; k < NCW; ++k) tsum += wobj[k];
-        objp[seg.w] = tsum;
+      const int slot = blockIdx.x * P.N + s;
+      flush_acc<kScatter>(P, s, acc, partial + (size_t)slot * P.n_pad, ct, NCW * 32);
+      if (ct == 0) {
+        if (MODE != kNormal) {
+          double tsum = 0.0;
+          for (int k = 0; k < NCW; ++k) tsum += wobj[k];
+          objp[slot] = tsum;
+        }
+        P.visited[(size_t)s * P.grid + blockIdx.x] = 1;
       }
     }
   }
-  __syncthreads();
+  finish_pass<MODE != kNormal>(P);
 }
 
 // ---------------------------------------------------------------------------
 // register-path row pass
 // ---------------------------------------------------------------------------
-template <int KR, typename VT, typename IT>
-struct RowRegs {
-  float v[KR];
-  int c[KR];
-  __device__ __forceinline__ void load(const VT* __restrict__ val, const IT* __restrict__ col,
-                                       int a, int b, int lane) {
-#pragma unroll
-    for (int k = 0; k < KR; ++k) {
-      const int idx = a + lane + 32 * k;
-      if (idx < b) {
-        v[k] = to_f<VT>(val[idx]);
-        c[k] = (int)col[idx];
-      } else {
-        v[k] = 0.f;
-        c[k] = 0;
-      }
-    }
-  }
-};
-
 template <int MODE, typename VT, typename IT, int KR>
 __global__ void __launch_bounds__(kRowThreads, 2)
 k_rowpass(DevPlan P, const float* __restrict__ vin, int v_stride, const int* __restrict__ active,
@@ -336,94 +440,46 @@ k_rowpass(DevPlan P, const float* __restrict__ vin, int v_stride, const int* __r
   __shared__ int next_row;
   __shared__ double wobj[kRowThreads / 32];
 
-  const int4 blk = P.blocks[blockIdx.x];
+  const int4 blk = P.blocks[blockIdx.x];      // (s, first row, end row, lanes per row)
   const int s = blk.x;
-  if (active != nullptr && active[s] == 0) return;   // uniform over the CTA
+  const bool run = (active == nullptr || active[s] != 0);   // uniform over the CTA
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  stage_vector<kScatter>(P, vin, v_stride, s, sv, acc, tid, kRowThreads);
-  if (tid == 0) next_row = blk.y;
-  __syncthreads();
-
-  const int32_t* rp = P.row_ptr + (size_t)s * (P.m_act + 1);
-  const VT* __restrict__ val = vals<VT>(P) + P.nnz_base[s];
-  const IT* __restrict__ col = cols<IT>(P) + P.nnz_base[s];
-  const float cs = P.cs[s];
-  double obj = 0.0;
-
-  for (;;) {
-    int r0 = 0;
-    if (lane == 0) r0 = atomicAdd(&next_row, 32);
-    r0 = __shfl_sync(0xffffffffu, r0, 0);
-    if (r0 >= blk.z) break;
-    const int nr = min(32, blk.z - r0);
-    int ra = 0, rb = 0;
-    float wl = 0.f, pl = 0.f;
-    if (lane < nr) {
-      ra = rp[r0 + lane];
-      rb = rp[r0 + lane + 1];
-      wl = P.w[r0 + lane] * cs;
-      if (kObjective) pl = P.p[r0 + lane];
+  if (run) {
+    stage_vector<kScatter>(P, vin, v_stride, s, sv, acc, tid, kRowThreads);
+    if (tid == 0) next_row = blk.y;
+    __syncthreads();
+    const int4* __restrict__ rec = P.rowrec + P.rec_base[s];
+    const VT* __restrict__ val = vals<VT>(P) + P.nnz_base[s];
+    const IT* __restrict__ col = cols<IT>(P) + P.nnz_base[s];
+    const int G = blk.w, rpw = 32 / G;
+    const int sl = lane & (G - 1), sub = lane / G;
+    const size_t dose_base = (size_t)s * P.m_act;
+    double obj = 0.0;
+    for (;;) {
+      int r0 = 0;
+      if (lane == 0) r0 = atomicAdd(&next_row, rpw);
+      r0 = __shfl_sync(0xffffffffu, r0, 0);
+      if (r0 >= blk.z) break;
+      const int r = r0 + sub;
+      process_rows<MODE, VT, IT, KR, false>(rec, r, r < blk.z, G, sl, val, col, 0, sv, acc, obj, dose,
+                                            dose_base);
     }
-    RowRegs<KR, VT, IT> cur, nxt;
-    int a = __shfl_sync(0xffffffffu, ra, 0);
-    int b = __shfl_sync(0xffffffffu, rb, 0);
-    cur.load(val, col, a, b, lane);
-    for (int q = 0; q < nr; ++q) {
-      int an = 0, bn = 0;
-      if (q + 1 < nr) {   // prefetch the next row while this one is processed
-        an = __shfl_sync(0xffffffffu, ra, q + 1);
-        bn = __shfl_sync(0xffffffffu, rb, q + 1);
-        nxt.load(val, col, an, bn, lane);
-      }
-      float t = 0.f;
-#pragma unroll
-      for (int k = 0; k < KR; ++k) t = fmaf(cur.v[k], sv[cur.c[k]], t);
-      // rest of a long row: batches of 32*KR independent loads
-      for (int base = a + 32 * KR; base < b; base += 32 * KR) {
-        RowRegs<KR, VT, IT> tl;
-        tl.load(val, col, base, b, lane);
-#pragma unroll
-        for (int k = 0; k < KR; ++k) t = fmaf(tl.v[k], sv[tl.c[k]], t);
-      }
-      t = warp_sum(t);
-      const float wc = __shfl_sync(0xffffffffu, wl, q);
-      float coef = 0.f;
-      if (MODE == kNormal) {
-        coef = wc * t;
-      } else {
-        const float r = t - __shfl_sync(0xffffffffu, pl, q);
-        coef = wc * r;
-        if (lane == 0) {
-          obj += (double)(coef * r);
-          if (MODE == kDose) dose[(size_t)s * P.m_act + r0 + q] = t;
-        }
-      }
-      if (kScatter && b > a) {
-#pragma unroll
-        for (int k = 0; k < KR; ++k)
-          if (a + lane + 32 * k < b) atomicAdd(&acc[cur.c[k]], coef * cur.v[k]);
-        for (int idx = a + 32 * KR + lane; idx < b; idx += 32)
-          atomicAdd(&acc[(int)col[idx]], coef * to_f<VT>(val[idx]));
-      }
-      if (q + 1 < nr) {
-        cur = nxt;
-        a = an;
-        b = bn;
-      }
+    if (kObjective) {
+      obj = warp_sum_d(obj);
+      if (lane == 0) wobj[wid] = obj;
+    }
+    __syncthreads();
+    flush_acc<kScatter>(P, s, acc, partial + (size_t)blockIdx.x * P.n_pad, tid, kRowThreads);
+    if (kObjective && tid == 0) {
+      double t = 0.0;
+      for (int k = 0; k < kRowThreads / 32; ++k) t += wobj[k];
+      objp[blockIdx.x] = t;
     }
   }
-
-  if (kObjective && lane == 0) wobj[wid] = obj;
-  __syncthreads();
-  flush_acc<kScatter>(P, s, acc, partial + (size_t)blockIdx.x * P.n_pad, tid, kRowThreads);
-  if (kObjective && tid == 0) {
-    double t = 0.0;
-    for (int k = 0; k < kRowThreads / 32; ++k) t += wobj[k];
-    objp[blockIdx.x] = t;
-  }
+  finish_pass<kObjective>(P);
 }
 
-constexpr int kKR = 4;
+constexpr int kKR = 8;
 
 template <int MODE>
 void* pick(const DevPlan& P) {

@@ -31,18 +31,27 @@ __device__ __forceinline__ double clampd(double v, double lo, double hi) {
   return fmin(fmax(v, lo), hi);
 }
 
-// Fixed-order compensated sum of the row-pass partials of blocks [b0, b1) at column j.
-__device__ __forceinline__ double sum_partials(const float* __restrict__ part, int n_pad, int b0,
-                                               int b1, int j) {
-  float s = 0.f, c = 0.f;
-  for (int b = b0; b < b1; ++b) {
-    const float v = __ldcg(part + (size_t)b * n_pad + j);
+// Compensated sum, in the slot list's fixed order, of scenario s's row-pass
+// partials at column j.
+__device__ __forceinline__ double sum_partials(const DevPlan& P, const float* __restrict__ part, int s, int j) {
+  float sum = 0.f, c = 0.f;
+  const int cnt = __ldcg(&P.slot_count[s]);
+  const int* list = P.slot_list + (size_t)s * P.slot_cap;
+  for (int k = 0; k < cnt; ++k) {
+    const float v = __ldcg(part + (size_t)__ldcg(&list[k]) * P.n_pad + j);
     float t, e;
-    two_sum(s, v, t, e);
-    s = t;
+    two_sum(sum, v, t, e);
+    sum = t;
     c += e;
   }
-  return (double)s + (double)c;
+  return (double)sum + (double)c;
+}
+
+// Objective of the last objective pass: sum over scenarios (fixed order).
+__device__ __forceinline__ double objective_sum(const DevPlan& P) {
+  double f = 0.0;
+  for (int s = 0; s < P.N; ++s) f += __ldcg(&P.objs[s]);
+  return f;
 }
 
 // Last-block-done: every block calls it once (all threads); returns true in the
@@ -122,7 +131,7 @@ __global__ void k_cg_init(DevPlan P, Ctl* C, const float* __restrict__ partial,
   double v[2] = {0.0, 0.0};
   if (j < P.n) {
     const size_t o = (size_t)s * P.n + j;
-    const double gj = sum_partials(partial, P.n_pad, P.blk_first[s], P.blk_first[s + 1], j);
+    const double gj = sum_partials(P, partial, s, j);
     const double ri = -gj - 0.5 * rho * (x[o] - z[j]) - 0.5 * y[o];
     const double ui = dinv[o] * ri;
     r[o] = ri;
@@ -185,8 +194,7 @@ __global__ void k_cg_dots(DevPlan P, Ctl* C, const float* __restrict__ partial,
   if (j < P.n) {
     const size_t o = (size_t)s * P.n + j;
     const double uj = u[o];
-    const double wj = sum_partials(partial, P.n_pad, P.blk_first[s], P.blk_first[s + 1], j) +
-                      0.5 * C->rho * uj;
+    const double wj = sum_partials(P, partial, s, j) + 0.5 * C->rho * uj;
     w[o] = wj;
     v[0] = wj * uj;
   }
@@ -412,14 +420,9 @@ __global__ void k_admm_y(DevPlan P, Ctl* C, const double* __restrict__ x, double
 
 // <<<1, 256>>>.  Objective of z (after a kObj row pass): optional relative-change test
 // AND-ed with Eq. 9 (Sec. 2.3).
-__global__ void k_admm_obj(Ctl* C, const double* __restrict__ objp, int nblocks,
-                           unsigned long long hadmm, int use_cond) {
-  __shared__ double sh[32];
-  double v[1] = {0.0};
-  for (int b = threadIdx.x; b < nblocks; b += blockDim.x) v[0] += objp[b];
-  block_sum_d<1>(v, sh);
+__global__ void k_admm_obj(DevPlan P, Ctl* C, unsigned long long hadmm, int use_cond) {
   if (threadIdx.x == 0) {
-    const double f = v[0] + C->const_term;
+    const double f = objective_sum(P) + C->const_term;
     const int conv_obj = fabs(C->f_prev - f) <= C->tol_obj * fmax(fabs(f), 1e-300);
     C->f_prev = f;
     C->f_cur = f;
@@ -431,13 +434,9 @@ __global__ void k_admm_obj(Ctl* C, const double* __restrict__ objp, int nblocks,
 }
 
 // <<<1, 256>>>.  f = sum of block objectives + constant.
-__global__ void k_final_obj(Ctl* C, const double* __restrict__ objp, int nblocks, int pgd) {
-  __shared__ double sh[32];
-  double v[1] = {0.0};
-  for (int b = threadIdx.x; b < nblocks; b += blockDim.x) v[0] += objp[b];
-  block_sum_d<1>(v, sh);
+__global__ void k_final_obj(DevPlan P, Ctl* C) {
   if (threadIdx.x == 0) {
-    C->f_cur = v[0] + C->const_term;
+    C->f_cur = objective_sum(P) + C->const_term;
     C->passes += 1;
   }
 }
@@ -463,17 +462,16 @@ __global__ void k_pgd_init(DevPlan P, const double* __restrict__ x0, int has_x0,
 // grid (nchunk).  g = 2 sum_s A~_s^T (A~_s x - p~) (Eq. 4 summed over s) from a kResid
 // pass over all scenarios; f(x); start the Armijo trials at t = alpha.
 __global__ void k_pgd_grad(DevPlan P, Ctl* C, const float* __restrict__ partial,
-                           const double* __restrict__ objp, double* g, unsigned long long htrial,
-                           int use_cond) {
-  __shared__ double sh[32];
+                           double* g, unsigned long long htrial, int use_cond) {
   const int j = blockIdx.x * VT + threadIdx.x;
-  if (j < P.n) g[j] = 2.0 * sum_partials(partial, P.n_pad, 0, P.nblocks, j);
+  if (j < P.n) {
+    double gj = 0.0;
+    for (int s = 0; s < P.N; ++s) gj += sum_partials(P, partial, s, j);
+    g[j] = 2.0 * gj;
+  }
   if (!last_block(&C->cnt_pg, gridDim.x)) return;
-  double v[1] = {0.0};
-  for (int b = threadIdx.x; b < P.nblocks; b += blockDim.x) v[0] += __ldcg(&objp[b]);
-  block_sum_d<1>(v, sh);
   if (threadIdx.x == 0) {
-    C->fx = v[0] + C->const_term;
+    C->fx = objective_sum(P) + C->const_term;
     C->t = C->alpha;
     C->trial = 0;
     C->accepted = 0;
@@ -510,14 +508,9 @@ __global__ void k_pgd_trial(DevPlan P, Ctl* C, const double* __restrict__ x,
 }
 
 // <<<1, 256>>>.  Sufficient-decrease test (Eq. 3 read as f(x_t) <= f(x) + beta g'(x_t - x)).
-__global__ void k_pgd_accept(Ctl* C, const double* __restrict__ objp, int nblocks,
-                             unsigned long long htrial, int use_cond) {
-  __shared__ double sh[32];
-  double v[1] = {0.0};
-  for (int b = threadIdx.x; b < nblocks; b += blockDim.x) v[0] += objp[b];
-  block_sum_d<1>(v, sh);
+__global__ void k_pgd_accept(DevPlan P, Ctl* C, unsigned long long htrial, int use_cond) {
   if (threadIdx.x == 0) {
-    const double ft = v[0] + C->const_term;
+    const double ft = objective_sum(P) + C->const_term;
     C->ft = ft;
     C->trials_total += 1;
     C->passes += 1;
@@ -578,14 +571,16 @@ __global__ void k_reduce_scen(DevPlan P, const float* __restrict__ partial,
   const int s = blockIdx.y, j = blockIdx.x * VT + threadIdx.x;
   if (j >= P.n) return;
   const size_t o = (size_t)s * P.n + j;
-  out[o] = sum_partials(partial, P.n_pad, P.blk_first[s], P.blk_first[s + 1], j) + half_rho * v[o];
+  out[o] = sum_partials(P, partial, s, j) + half_rho * v[o];
 }
 
 // grid (nchunk): out = scale * sum over all blocks.
 __global__ void k_reduce_all(DevPlan P, const float* __restrict__ partial, double scale, double* out) {
   const int j = blockIdx.x * VT + threadIdx.x;
   if (j >= P.n) return;
-  out[j] = scale * sum_partials(partial, P.n_pad, 0, P.nblocks, j);
+  double v = 0.0;
+  for (int s = 0; s < P.N; ++s) v += sum_partials(P, partial, s, j);
+  out[j] = scale * v;
 }
 
 // ---------------------------------------------------------------------------
@@ -695,13 +690,13 @@ void admm_iteration_tail(Exec& e, Plan* P, int use_obj, unsigned long long hadmm
          hadmm, use_obj ? 0 : uc);
   if (use_obj) {
     rowpass(e, P, kObj, P->vz32, 0, nullptr);
-    launch(e, k_admm_obj, dim3(1), dim3(256), 0, P->ctl, (const double*)P->objp, dp.nblocks, hadmm, uc);
+    launch(e, k_admm_obj, dim3(1), dim3(32), 0, dp, P->ctl, hadmm, uc);
   }
 }
 
 void admm_tail_final(Exec& e, Plan* P) {
   rowpass(e, P, kObj, P->vz32, 0, nullptr);
-  launch(e, k_final_obj, dim3(1), dim3(256), 0, P->ctl, (const double*)P->objp, P->dp.nblocks, 0);
+  launch(e, k_final_obj, dim3(1), dim3(32), 0, P->dp, P->ctl);
 }
 
 cudaError_t build_admm_graph(Plan* P, int use_obj, double* z0d, double* y0d) {
@@ -742,7 +737,7 @@ void pgd_head(Exec& e, Plan* P, unsigned long long htrial, int uc) {
   const DevPlan& dp = P->dp;
   rowpass(e, P, kResid, P->vz32, 0, nullptr);
   launch(e, k_pgd_grad, dim3(P->nchunk), dim3(VT), 0, dp, P->ctl, (const float*)P->partial,
-         (const double*)P->objp, P->g, htrial, uc);
+         P->g, htrial, uc);
 }
 
 void pgd_trial(Exec& e, Plan* P, unsigned long long htrial, int uc) {
@@ -750,7 +745,7 @@ void pgd_trial(Exec& e, Plan* P, unsigned long long htrial, int uc) {
   launch(e, k_pgd_trial, dim3(P->nchunk), dim3(VT), 0, dp, P->ctl, (const double*)P->xp,
          (const double*)P->g, (const double*)P->lb, (const double*)P->ub, P->xt, P->v32, P->vpart);
   rowpass(e, P, kObj, P->v32, 0, nullptr);
-  launch(e, k_pgd_accept, dim3(1), dim3(256), 0, P->ctl, (const double*)P->objp, dp.nblocks, htrial, uc);
+  launch(e, k_pgd_accept, dim3(1), dim3(32), 0, dp, P->ctl, htrial, uc);
 }
 
 void pgd_tail(Exec& e, Plan* P, unsigned long long houter, int uc) {
@@ -1111,10 +1106,10 @@ int op_gradient(Plan* P, const double* x, double* g_out, double* f_out) {
   rowpass(ex, P, kResid, P->vz32, 0, nullptr);
   launch(ex, k_reduce_all, dim3(P->nchunk), dim3(VT), 0, dp, (const float*)P->partial, 2.0, P->g);
   if (ex.err) return cuda_fail(ex.err, "launch");
-  std::vector<double> objp(dp.nblocks);
+  std::vector<double> objp(dp.N);
   if ((e = cudaMemcpyAsync(g_out, P->g, sizeof(double) * dp.n, cudaMemcpyDeviceToHost, P->stream)))
     return cuda_fail(e, "copy out");
-  if ((e = cudaMemcpyAsync(objp.data(), P->objp, sizeof(double) * dp.nblocks, cudaMemcpyDeviceToHost, P->stream)))
+  if ((e = cudaMemcpyAsync(objp.data(), dp.objs, sizeof(double) * dp.N, cudaMemcpyDeviceToHost, P->stream)))
     return cuda_fail(e, "copy out");
   if ((e = cudaStreamSynchronize(P->stream))) return cuda_fail(e, "sync");
   if (int rc = check_err(P)) return rc;
@@ -1143,12 +1138,15 @@ int op_objective(Plan* P, const double* x, double* f_out, double* dose_out) {
     P->allocs.push_back(P->dose);
   }
   if ((e = stage_host_vector(P, P->vz32, x, 1))) return cuda_fail(e, "stage");
+  // rows that are empty in a scenario are not visited: their dose is zero
+  if (dose_out && (e = cudaMemsetAsync(P->dose, 0, sizeof(float) * (size_t)dp.N * dp.m_act, P->stream)))
+    return cuda_fail(e, "memset");
   Exec ex;
   ex.st = P->stream;
   rowpass(ex, P, dose_out ? kDose : kObj, P->vz32, 0, nullptr, P->dose);
   if (ex.err) return cuda_fail(ex.err, "launch");
-  std::vector<double> objp(dp.nblocks);
-  if ((e = cudaMemcpyAsync(objp.data(), P->objp, sizeof(double) * dp.nblocks, cudaMemcpyDeviceToHost, P->stream)))
+  std::vector<double> objp(dp.N);
+  if ((e = cudaMemcpyAsync(objp.data(), dp.objs, sizeof(double) * dp.N, cudaMemcpyDeviceToHost, P->stream)))
     return cuda_fail(e, "copy out");
   std::vector<float> dose;
   if (dose_out) {

@@ -1,0 +1,57 @@
+"""Write tests/golden/realistic_seed0_oracle.json from the CPU oracle only.
+
+Workload: synthetic.config_realistic(seed=0) (128x128x96 grid, ~299k voxels,
+5000 spots, 13 scenarios).  Records
+  * the paper's ADMM-BB with cached Cholesky subproblems (App. A) run to
+    eps = 1e-8: its objective is the reference optimum f* of the plan;
+  * ADMM-BB with CG subproblems and the library's default parameters
+    (rho = default rule, eps = 1e-4, theta 0.3, eta0 1e-2, floor 1e-6, Jacobi):
+    iterations and CG passes to tolerance, used to extrapolate the CPU timing;
+  * a checksum of the generated matrices so a differing platform is noticed.
+Run: python tests/golden/make_realistic_golden.py   (takes hours, CPU only)
+"""
+import json
+import math
+import os
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+sys.path.insert(0, ROOT)
+
+
+def main():
+    from synthetic import config_realistic
+    from oracle import Weighted, admm_bb, default_rho, certificates
+    out_path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "realistic_seed0_oracle.json")
+    t0 = time.time()
+    prob = config_realistic(0, workers=8)
+    nnz = [int(v.size) for v in prob.val]
+    checksum = float(sum(float(np.sum(v.astype(np.float64))) for v in prob.val))
+    W = Weighted(prob)
+    rho0 = default_rho(W)
+    res = dict(workload="config_realistic(seed=0)", m=prob.m, n=prob.n, N=prob.N, nnz=nnz,
+               value_sum=checksum, default_rho=rho0, made_by="tests/golden/make_realistic_golden.py")
+    # the paper's solver: cached Cholesky factors, tight tolerance
+    r = admm_bb(W, rho=rho0, eps_abs=1e-8, eps_rel=1e-8, max_iter=20000, subproblem="chol")
+    c = certificates(W, r["z"])
+    res["admm_chol_tight"] = dict(eps=1e-8, iterations=r["iterations"], status=r["status"], f=r["f"],
+                                  pg=c["pg"], kkt=c["kkt"], seconds=r["seconds"])
+    res["f_star"] = r["f"]
+    json.dump(res, open(out_path, "w"), indent=1)
+    r4 = admm_bb(W, rho=rho0, eps_abs=1e-4, eps_rel=1e-4, max_iter=20000, subproblem="chol")
+    res["admm_chol"] = dict(eps=1e-4, iterations=r4["iterations"], status=r4["status"], f=r4["f"],
+                            seconds=r4["seconds"])
+    json.dump(res, open(out_path, "w"), indent=1)
+    rc = admm_bb(W, rho=rho0, eps_abs=1e-4, eps_rel=1e-4, max_iter=20000, subproblem="cg",
+                 cg_theta=0.3, cg_eta0=1e-2, cg_floor_rel=1e-6, cg_max=50, cg_precond="jacobi")
+    res["admm_cg"] = dict(eps=1e-4, iterations=rc["iterations"], cg_iterations=rc["cg_iterations"],
+                          status=rc["status"], f=rc["f"], seconds=rc["seconds"])
+    res["total_seconds"] = time.time() - t0
+    json.dump(res, open(out_path, "w"), indent=1)
+
+
+if __name__ == "__main__":
+    main()

@@ -133,18 +133,21 @@ def test_default_rho_matches_oracle_rule(rpt):
     with plan_of(rpt, prob) as P:
         st = P.stats()
     assert st["default_rho"] == pytest.approx(default_rho(Weighted(prob)), rel=1e-12)
-    # rows empty in every scenario are dropped; their w p^2 goes to the constant
-    W = Weighted(prob)
-    empty = np.ones(prob.m, bool)
-    for rp in prob.row_ptr:
-        empty &= np.diff(rp) == 0
-    c = 1.0 if prob.scen_weight is None else prob.scen_weight
-    const = float(np.sum(np.sum(c) * prob.voxel_w[empty] * prob.presc[empty] ** 2))
+    # a row that is empty in scenario s contributes the constant c_s w_i p_i^2 to f
+    # (Eq. 1); rows empty in every scenario are not stored at all
+    c = np.ones(prob.N) if prob.scen_weight is None else prob.scen_weight
+    const = 0.0
+    empty_all = np.ones(prob.m, bool)
+    for s, rp in enumerate(prob.row_ptr):
+        e = np.diff(rp) == 0
+        empty_all &= e
+        const += float(c[s] * np.sum(prob.voxel_w[e] * prob.presc[e] ** 2))
     assert st["const_term"] == pytest.approx(const, rel=1e-12, abs=1e-9)
-    assert st["m_active"] == int((~empty).sum())
+    assert st["m_active"] == int((~empty_all).sum())
 
 
 def test_row_path_selection(rpt, monkeypatch):
+    monkeypatch.delenv("RPT_ROW_PATH", raising=False)
     prob = random_problem(**CASES["long_rows"])          # rows of 300 entries
     with plan_of(rpt, prob) as P:
         assert P.stats()["row_blocks"] >= 1
@@ -152,7 +155,7 @@ def test_row_path_selection(rpt, monkeypatch):
     with pytest.raises(rpt.RptError) as e:
         plan_of(rpt, prob, row_path=2)
     assert e.value.status == rpt.EUNSUPPORTED
-    with plan_of(rpt, prob) as P:                        # auto falls back to the register path
+    with plan_of(rpt, prob) as P:                        # the default is the register path
         U = P.apply_normal(np.ones((prob.N, prob.n)), 1.0)
     W = Weighted(prob)
     np.testing.assert_allclose(U[0], W.normal_apply(0, np.ones(prob.n), 1.0), rtol=1e-4)
