@@ -181,6 +181,8 @@ def main():
     ap.add_argument("--max-iter", type=int, default=0,
                     help="cap ADMM iterations (short profiling runs; not a benchmark setting)")
     ap.add_argument("--row-path", type=int, default=0, help="0 default, 1 register, 2 bulk-copy ring")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="host-driven loop instead of one CUDA graph (profilers then see every launch)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -210,6 +212,8 @@ def main():
     params = rpt.admm_params()          # eps_abs = eps_rel = 1e-4, defaults of the library
     if args.max_iter > 0:
         params.max_iter = args.max_iter
+    if args.no_graph:
+        params.use_graph = 0
 
     def barrier():
         if world > 1:
@@ -274,7 +278,8 @@ def main():
                  "solve_seconds_info": statistics.mean(i["seconds"] for i in infos)},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
-                     "kernel": "k_rowpass<kNormal,f32,int32> (CG operator pass, all scenarios)",
+                     "kernel": ("k_rowpass_tma" if st["row_path"] == 2 else "k_rowpass") +
+                               "<kNormal,f32,int32> (CG operator pass, all scenarios)",
                      "ms_per_launch": ms_pass, "bytes_per_launch": bytes_pass,
                      "peak_source": f"{peak_src} hbm_gbs (burst; kernel timed alone)",
                      "resid_pass_gbs": bytes_resid / (ms_resid * 1e-3) / 1e9},

@@ -156,10 +156,14 @@ void free_plan(Plan* P) {
   delete P;
 }
 
-// Lanes per row: the smallest power of two G with G * kKeep >= len (1..32).
+// Lanes per row: the smallest power of two G >= g_min with G * kKeep >= len
+// (at most 32).  g_min > 1 keeps the rows that share one warp instruction few:
+// lanes of different rows can hit the same spot column in the same shared-memory
+// atomic, which serialises; short rows (the dose periphery) often do.
 constexpr int kKeep = 8;   // entries per lane held in registers by the row-pass kernels
+int g_min_lanes = 8;
 int lanes_for(int len) {
-  int g = 1;
+  int g = g_min_lanes;
   while (g < 32 && g * kKeep < len) g <<= 1;
   return g;
 }
@@ -361,6 +365,8 @@ int create_plan(const rpt_problem* pr, const rpt_device_opts* opts, rpt_plan** o
   const int bi = pr->index_width == 16 ? 2 : 4;
   const int bv = pr->value_format == RPT_F32 ? 4 : (pr->value_format == RPT_BF16 ? 2 : 1);
 
+  g_min_lanes = std::min(32, std::max(1, env_int("RPT_MIN_LANES", 8)));
+  g_min_lanes = 1 << (31 - __builtin_clz((unsigned)g_min_lanes));   // power of two
   // ---- per-scenario row lists, sorted by decreasing length; entries permuted to match ----
   RowLists R;
   R.rec_base.assign(N + 1, 0);
@@ -416,7 +422,8 @@ int create_plan(const rpt_problem* pr, const rpt_device_opts* opts, rpt_plan** o
   }
   // ---- work decomposition: register-direct row blocks (default) or bulk-copy ring ----
   const double per_lane = std::max(0, env_int("RPT_ROW_COST_LANE", 4));   // per-row overhead per lane, in entries
-  // row path: the caller's choice, else RPT_ROW_PATH from the environment, else 1
+  // row path: the caller's choice, else RPT_ROW_PATH from the environment, else
+  // the bulk-copy ring when the plan fits it and the register path otherwise
   const int want_path = (opts && opts->row_path) ? opts->row_path : env_int("RPT_ROW_PATH", 0);
   std::vector<int4> blocks;
   std::vector<int> blk_first(N + 1, 0);
@@ -424,21 +431,23 @@ int create_plan(const rpt_problem* pr, const rpt_device_opts* opts, rpt_plan** o
   std::vector<int> scen_chunk;
   bool use_tma = false;
   int ctas = 0;
-  if (want_path == 2) {
+  if (want_path != 1) {
     int smem_optin = 0;
     cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, P->device);
-    dp.cmax = std::max(64, env_int("RPT_TMA_CMAX", 4096)) & ~15;
+    dp.cmax = std::max(64, env_int("RPT_TMA_CMAX", 6144)) & ~15;
     dp.rmax = std::max(8, env_int("RPT_TMA_RMAX", 512));
-    dp.stages = std::min(8, std::max(2, env_int("RPT_TMA_STAGES", 4)));
+    dp.stages = std::min(8, std::max(2, env_int("RPT_TMA_STAGES", 3)));
     ctas = (opts && opts->ctas_per_sm > 0) ? opts->ctas_per_sm : 1;
     const size_t need = tma_smem_bytes(n_pad, dp.cmax, dp.rmax, dp.stages, bv, bi, true);
     if (need + 1024 <= (size_t)smem_optin)
       use_tma = build_chunks(R, base, N, dp.cmax, dp.rmax, &chunks, &scen_chunk);
-    if (!use_tma) {
+    if (!use_tma && want_path == 2) {
       free_plan(P);
       set_error("bulk-copy row path not possible for this plan (shared memory, or a row longer than RPT_TMA_CMAX)");
       return RPT_EUNSUPPORTED;
     }
+  }
+  if (use_tma) {
     dp.path = 1;
     dp.grid = P->sm_count * ctas;
     dp.nblocks = dp.grid * N;          // one slot per (CTA, scenario)
@@ -710,6 +719,8 @@ int create_plan(const rpt_problem* pr, const rpt_device_opts* opts, rpt_plan** o
   S.sm_count = P->sm_count;
   S.default_rho = 2.0 * (tr / N) / n;
   S.const_term = const_term;
+  S.row_path = dp.path == 1 ? 2 : 1;
+  S.min_lanes = g_min_lanes;
   *out = reinterpret_cast<rpt_plan*>(P);
   return RPT_OK;
 }

@@ -33,7 +33,7 @@
 namespace rpt {
 
 constexpr int kRowThreads = 512;      // threads of a register-path row-pass CTA
-constexpr int kTmaThreads = 512;      // threads of a TMA-path CTA (1 producer + 15 consumer warps)
+constexpr int kTmaThreads = 1024;     // threads of a TMA-path CTA (1 producer + 31 consumer warps)
 constexpr int kVecThreads = 256;      // threads of a vector CTA (one column each)
 
 struct ChunkDesc {

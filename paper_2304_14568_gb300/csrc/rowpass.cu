@@ -19,9 +19,9 @@
 //    bulk asynchronous copies (cp.async.bulk, completion counted on an
 //    mbarrier) of row-aligned chunks: the row records, the values and the
 //    indices; it publishes each chunk's descriptor in shared memory and
-//    prefetches the next one.  Fifteen consumer warps split the rows of a
-//    resident chunk statically (warp w takes rows w, w+15, ...), one warp per
-//    row, and release the stage through a second mbarrier.  Every wait is bounded; a wait that runs out sets the plan's
+//    prefetches the next one.  The other 31 warps consume: they split the rows of a
+//    resident chunk statically in groups of lanes (one group per row), and
+//    release the stage through a second mbarrier.  Every wait is bounded; a wait that runs out sets the plan's
 //    error word and the kernel drains its copies and returns.
 //  * k_rowpass (register path): nnz-balanced row blocks, one CTA each; warps
 //    load row entries straight into registers with a one-row prefetch.
@@ -236,7 +236,7 @@ __device__ __forceinline__ void finish_pass(const DevPlan& P) {
 // ---------------------------------------------------------------------------
 // TMA-ring row pass
 // ---------------------------------------------------------------------------
-constexpr int kHdr = 1024;  // mbarriers (2 x 8 x 8 B), chunk descriptors (8 x 32 B), per-warp objective (16 doubles)
+constexpr int kHdr = 1024;  // mbarriers (2 x 8 x 8 B), chunk descriptors (8 x 32 B), per-warp objective (up to 64 doubles)
 constexpr int kBatch = 4;   // chunks per queue pull
 
 template <int MODE, typename VT, typename IT>
@@ -244,7 +244,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
 k_rowpass_tma(DevPlan P, const float* __restrict__ vin, int v_stride, const int* __restrict__ active,
               float* __restrict__ partial, double* __restrict__ objp, float* __restrict__ dose) {
   constexpr bool kScatter = (MODE == kNormal || MODE == kResid);
-  constexpr int NCW = kTmaThreads / 32 - 1;     // consumer warps
+  constexpr int NCW = kTmaThreads / 32 - 1;     // consumer warps (wobj below holds up to 64)
   constexpr int KR = 8;                         // entries per lane kept in registers
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t* full = reinterpret_cast<uint64_t*>(smem);

@@ -78,7 +78,8 @@ class _Stats(C.Structure):
     _fields_ = [("m", C.c_int32), ("n", C.c_int32), ("N", C.c_int32), ("m_active", C.c_int32),
                 ("nnz", C.c_int64), ("matrix_bytes", C.c_int64), ("value_format", C.c_int32),
                 ("index_width", C.c_int32), ("row_blocks", C.c_int32), ("sm_count", C.c_int32),
-                ("default_rho", C.c_double), ("const_term", C.c_double)]
+                ("default_rho", C.c_double), ("const_term", C.c_double),
+                ("row_path", C.c_int32), ("min_lanes", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

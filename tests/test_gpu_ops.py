@@ -155,7 +155,7 @@ def test_row_path_selection(rpt, monkeypatch):
     with pytest.raises(rpt.RptError) as e:
         plan_of(rpt, prob, row_path=2)
     assert e.value.status == rpt.EUNSUPPORTED
-    with plan_of(rpt, prob) as P:                        # the default is the register path
+    with plan_of(rpt, prob) as P:                        # the default falls back to the register path
         U = P.apply_normal(np.ones((prob.N, prob.n)), 1.0)
     W = Weighted(prob)
     np.testing.assert_allclose(U[0], W.normal_apply(0, np.ones(prob.n), 1.0), rtol=1e-4)
