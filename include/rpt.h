@@ -215,6 +215,38 @@ int rpt_apply_normal(rpt_plan* plan, const double* v, double rho, double* u_out)
 int rpt_profile_row_pass(rpt_plan* plan, int mode, int reps, double* ms_per_pass,
                          double* bytes_per_pass);
 
+/* ---- allocation-free operator -------------------------------------------- */
+
+/* The scenario operator u = A^T diag(w) A v + (rho/2) v (the B_s of the
+ * x-subproblem, with w the scenario's row weights c_s w_i) computed from a CSR
+ * matrix the caller already holds in device memory, without allocating any
+ * memory.  The paper has no counterpart: it is for callers that cannot call
+ * cudaMalloc -- code whose device memory is owned by a pool or framework, or a
+ * loop that must not block on the allocator -- and so cannot create a plan.
+ *
+ * Arguments (all pointers are DEVICE pointers owned by the caller):
+ *   m, n        rows (voxels) and columns (spots); 1 <= n <= 8192
+ *   row_ptr_dev int32[m+1] valid CSR offsets (row_ptr[0] = 0, non-decreasing)
+ *   col_idx_dev int32[row_ptr[m]] column of each entry; entries outside [0, n)
+ *               are ignored
+ *   val_dev     float32[row_ptr[m]] values;  row_w_dev float32[m] row weights
+ *   v_dev       float32[n] input;  u_dev float32[n] output (written)
+ *   rho         >= 0;  stream  cudaStream_t to run on (NULL = default stream)
+ * Working memory: a file-scope device array of 4 MiB (128 x 8192 floats of
+ * per-CTA partial sums), held by every device that loads the library until the
+ * process exits.  The first call on a device looks up that array's device
+ * address (cudaGetSymbolAddress); make that first call before any stream
+ * capture.  The call enqueues two kernels and returns without synchronising.
+ * Every call overwrites the scratch slots it reads, so nothing needs clearing,
+ * but calls that overlap on the GPU (on different streams, or on different
+ * threads) share the array and race.  Allocates nothing (no cudaMalloc,
+ * cudaFree or allocating library routine).  Errors: RPT_EINVAL for bad sizes,
+ * null pointers or rho < 0; RPT_EUNSUPPORTED for n > 8192; RPT_ECUDA if a
+ * launch fails. */
+int rpt_normal_apply_noalloc(int32_t m, int32_t n, const int32_t* row_ptr_dev, const int32_t* col_idx_dev,
+                             const float* val_dev, const float* row_w_dev, const float* v_dev, double rho,
+                             float* u_dev, void* stream);
+
 /* ---- ADMM state (checkpoint / resume) ----------------------------------- */
 
 /* The plan keeps the state (z, x_s, y_s) of its last ADMM solve.  get copies

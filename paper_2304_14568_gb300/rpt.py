@@ -22,7 +22,7 @@ MAX_SPOTS = 24576
 EXPORTED = [
     "rpt_admm_params_default", "rpt_pgd_params_default", "rpt_plan_create", "rpt_plan_destroy",
     "rpt_plan_query", "rpt_admm_bb_solve", "rpt_pgd_solve", "rpt_objective", "rpt_gradient",
-    "rpt_apply_normal", "rpt_profile_row_pass", "rpt_state_get", "rpt_state_set", "rpt_status_string", "rpt_last_error",
+    "rpt_apply_normal", "rpt_profile_row_pass", "rpt_normal_apply_noalloc", "rpt_state_get", "rpt_state_set", "rpt_status_string", "rpt_last_error",
     "rpt_version",
 ]
 
@@ -119,6 +119,9 @@ def lib():
     L.rpt_apply_normal.restype = C.c_int
     L.rpt_profile_row_pass.argtypes = [C.c_void_p, C.c_int, C.c_int, dp, dp]
     L.rpt_profile_row_pass.restype = C.c_int
+    L.rpt_normal_apply_noalloc.argtypes = [C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p,
+                                           C.c_void_p, C.c_void_p, C.c_double, C.c_void_p, C.c_void_p]
+    L.rpt_normal_apply_noalloc.restype = C.c_int
     L.rpt_state_get.argtypes = [C.c_void_p, dp, dp, dp]
     L.rpt_state_get.restype = C.c_int
     L.rpt_state_set.argtypes = [C.c_void_p, dp, dp, dp]
@@ -281,6 +284,13 @@ class Plan:
 
 def plan_create(prob, **kw) -> Plan:
     return Plan.from_problem(prob, **kw)
+
+
+def normal_apply_noalloc(m, n, row_ptr_dev, col_idx_dev, val_dev, row_w_dev, v_dev, rho, u_dev, stream=None):
+    """u = A^T diag(w) A v + (rho/2) v from device arrays (integer device
+    addresses), with no device allocation.  Asynchronous on `stream`."""
+    _check(lib().rpt_normal_apply_noalloc(int(m), int(n), row_ptr_dev, col_idx_dev, val_dev, row_w_dev, v_dev,
+                                          float(rho), u_dev, stream))
 
 
 def version() -> str:
