@@ -115,7 +115,7 @@ def cpu_baseline(prob, budget_s=20.0):
     t0 = time.perf_counter()
     W = Weighted(prob)
     t_setup = time.perf_counter() - t0
-    rho = 0.3 * default_rho(W)
+    rho = default_rho(W)               # the library default (rho_scale 1)
     # one sample iteration at a time until the budget is used
     t1 = time.perf_counter()
     k = 0
@@ -123,7 +123,7 @@ def cpu_baseline(prob, budget_s=20.0):
     while time.perf_counter() - t1 < budget_s and k < 50:
         k += 1
         res = admm_bb(W, rho=rho, eps_abs=1e-4, eps_rel=1e-4, max_iter=k, subproblem="cg",
-                      cg_theta=0.3, cg_eta0=1e-2, cg_floor_rel=1e-6)
+                      cg_theta=0.3, cg_eta0=1e-2, cg_floor_rel=1e-6, cg_max=50, cg_precond="jacobi")
         if time.perf_counter() - t1 > budget_s / 2:
             break
     t_sample = res["seconds"]

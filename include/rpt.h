@@ -84,8 +84,9 @@ typedef struct {
   int32_t device;                   /* CUDA device ordinal */
   void*   stream;                   /* cudaStream_t to run on, or NULL for a stream owned by the plan */
   int32_t ctas_per_sm;              /* row-pass CTAs per SM (0 = library choice) */
-  int32_t row_path;                 /* 1 register-direct loads, 2 bulk-copy (TMA) ring; 0: RPT_ROW_PATH from
-                                       the environment, else 2 when the plan fits it and 1 otherwise */
+  int32_t row_path;                 /* 1 register-direct loads, 2 bulk-copy (TMA) ring, 3 streaming (warps
+                                       claim chunks, entries go straight to registers); 0: RPT_ROW_PATH
+                                       from the environment, else 2 when the plan fits it and 1 otherwise */
 } rpt_device_opts;
 
 /* ADMM-BB parameters (Sec. 2.2).  Fill with rpt_admm_params_default(). */
@@ -145,7 +146,7 @@ typedef struct {
   int32_t sm_count;
   double  default_rho;    /* 2 mean_s(trace(A~_s^T A~_s))/n (without rho_scale) */
   double  const_term;     /* sum over rows not stored for a scenario of c_s w_i p_i^2 (part of every f) */
-  int32_t row_path;       /* row-pass implementation in use: 1 register-direct, 2 bulk-copy ring */
+  int32_t row_path;       /* row-pass implementation in use: 1 register-direct, 2 bulk-copy ring, 3 streaming */
   int32_t min_lanes;      /* smallest lanes-per-row group */
 } rpt_plan_stats;
 

@@ -1,6 +1,6 @@
 """Build librpt.so in-tree with nvcc for sm_103a (no cmake, no torch extension).
 
-The three translation units compile in parallel; the shared library links the
+The translation units compile in parallel; the shared library links the
 CUDA runtime statically.  Run `python -m paper_2304_14568_gb300.build`.
 """
 from __future__ import annotations
@@ -14,8 +14,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "librpt.so")
-SOURCES = ["rowpass.cu", "solver.cu", "api.cu", "noalloc.cu"]
-HEADERS = ["common.cuh", "plan.h", os.path.join("..", "..", "include", "rpt.h")]
+SOURCES = ["rowpass.cu", "rowstream.cu", "solver.cu", "api.cu", "noalloc.cu"]
+HEADERS = ["common.cuh", "rowcommon.cuh", "plan.h", os.path.join("..", "..", "include", "rpt.h")]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
          "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]

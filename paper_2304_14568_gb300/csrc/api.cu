@@ -179,34 +179,48 @@ struct RowLists {
 
 double row_cost(int len, double per_lane) { return (double)len + per_lane * lanes_for(len); }
 
-// Cut every scenario's row list into chunks of rows with the same lanes-per-row
-// class, at most cmax copied entries (16-entry aligned span) and rmax rows.
-// scen_chunk[s]..scen_chunk[s+1] are scenario s's chunks.  Returns false if a
-// single row does not fit a stage.
-bool build_chunks(const RowLists& R, const std::vector<int64_t>& base, int N, int cmax, int rmax,
+// Row-length classes of the streaming path (see k_rowpass_stream): lanes per row
+// 8/16/32/32/32 for padded rows of at most 32/64/128/256/any entries.
+int stream_class(int len) {
+  const int q = (len + 3) >> 2;   // quads of the padded row
+  return q <= 8 ? 0 : q <= 16 ? 1 : q <= 32 ? 2 : q <= 64 ? 3 : 4;
+}
+constexpr int kStreamLanes[5] = {8, 16, 32, 32, 32};
+int stream_lanes(int len) { return kStreamLanes[stream_class(len)]; }
+
+// Cut every scenario's row list into chunks of rows of one class (lanes per row
+// for the ring, the streaming class otherwise), at most cmax entries in the
+// 16-entry aligned span and rmax rows.  scen_chunk[s]..scen_chunk[s+1] are
+// scenario s's chunks.  For the ring, returns false if a single row does not fit
+// a stage; the streaming path takes such a row as a chunk of its own.
+bool build_chunks(const RowLists& R, const std::vector<int64_t>& base, int N, int cmax, int rmax, bool stream,
                   std::vector<ChunkDesc>* chunks, std::vector<int>* scen_chunk) {
   scen_chunk->assign(N + 1, 0);
+  auto cls = [&](int len) { return stream ? stream_class(len) : lanes_for(len); };
   for (int s = 0; s < N; ++s) {
     (*scen_chunk)[s] = (int)chunks->size();
     const int4* r = &R.rec[R.rec_base[s]];
     int q = 0;
     while (q < R.nrows[s]) {
-      const int g0 = lanes_for(r[q + 1].x - r[q].x);
+      const int g0 = cls(r[q + 1].x - r[q].x);
       const int64_t g_al = (base[s] + r[q].x) & ~(int64_t)15;
       int qe = q;
-      while (qe < R.nrows[s] && qe - q < rmax && lanes_for(r[qe + 1].x - r[qe].x) == g0) {
+      while (qe < R.nrows[s] && qe - q < rmax && cls(r[qe + 1].x - r[qe].x) == g0) {
         const int64_t g_end = (base[s] + r[qe + 1].x + 15) & ~(int64_t)15;
-        if (g_end - g_al > cmax) break;
+        if (g_end - g_al > cmax && !(stream && qe == q)) break;
         ++qe;
       }
       if (qe == q) return false;
+      const int64_t n_ent = std::max<int64_t>(16, ((base[s] + r[qe].x + 15) & ~(int64_t)15) - g_al);
+      if (n_ent > (int64_t)1 << 28) return false;
       ChunkDesc ch{};
       ch.g_al = g_al;
       ch.row_begin = q;
       ch.n_rows = qe - q;
-      ch.n_ent = (int)std::max<int64_t>(16, ((base[s] + r[qe].x + 15) & ~(int64_t)15) - g_al);
-      ch.group = g0;
+      ch.n_ent = (int)n_ent;
+      ch.group = stream ? kStreamLanes[g0] : g0;
       ch.s = s;
+      ch.pad = stream ? g0 : 0;
       chunks->push_back(ch);
       q = qe;
     }
@@ -322,12 +336,20 @@ int create_plan(const rpt_problem* pr, const rpt_device_opts* opts, rpt_plan** o
     for (int s = 0; s < N; ++s) const_term -= cs[s] * pr->voxel_w[0] * pr->presc[0] * pr->presc[0];
   }
   const int m_act = (int)kept.size();
-  std::vector<int64_t> nnz(N), base(N);
-  int64_t NNZ = 0;
+  // On the device every row is padded with zero entries (column 0, value 0) to a
+  // multiple of 4 entries, so rows start on 16-byte boundaries and lanes can load
+  // 4 entries at once; pnnz[s] counts scenario s's stored (padded) entries.
+  std::vector<int64_t> nnz(N), pnnz(N), base(N);
+  int64_t NNZ = 0, NNZp = 0;
   for (int s = 0; s < N; ++s) {
-    nnz[s] = pr->row_ptr[s][m];
-    base[s] = NNZ;
+    const int32_t* rp = pr->row_ptr[s];
+    nnz[s] = rp[m];
+    int64_t pn = 0;
+    for (int i = 0; i < m; ++i) pn += (rp[i + 1] - rp[i] + 3) & ~3;
+    pnnz[s] = pn;
+    base[s] = NNZp;
     NNZ += nnz[s];
+    NNZp += pn;
   }
 
   Plan* P = new (std::nothrow) Plan();
@@ -367,6 +389,9 @@ int create_plan(const rpt_problem* pr, const rpt_device_opts* opts, rpt_plan** o
 
   g_min_lanes = std::min(32, std::max(1, env_int("RPT_MIN_LANES", 8)));
   g_min_lanes = 1 << (31 - __builtin_clz((unsigned)g_min_lanes));   // power of two
+  // row path: the caller's choice, else RPT_ROW_PATH from the environment, else
+  // the bulk-copy ring when the plan fits it and the register path otherwise
+  const int want_path = (opts && opts->row_path) ? opts->row_path : env_int("RPT_ROW_PATH", 0);
   // ---- per-scenario row lists, sorted by decreasing length; entries permuted to match ----
   RowLists R;
   R.rec_base.assign(N + 1, 0);
@@ -386,13 +411,24 @@ int create_plan(const rpt_problem* pr, const rpt_device_opts* opts, rpt_plan** o
     R.rec_base[s + 1] = R.rec_base[s] + R.nrows[s] + 1;
   }
   R.rec.resize(R.rec_base[N]);
-  std::vector<int32_t> col_h((size_t)NNZ);
-  std::vector<float> val_h((size_t)NNZ);
+  std::vector<int32_t> col_h((size_t)NNZp, 0);
+  std::vector<float> val_h((size_t)NNZp, 0.f);
   {
+    // The streaming path reads a row as quads (4 stored entries) with lane sl of
+    // the row's G lanes taking quads sl, sl + G, ...; its rows are stored
+    // lane-interleaved so that, for each quad block b (g_b <= G lanes) and each
+    // component k, the lanes hold consecutive entries of the row:
+    //   stored[4 (b G + sl) + k] = row[4 b G + k g_b + sl].
+    // (Row order is free: the pass sums over the row's entries.)  Consecutive
+    // entries have nearby spot columns, which then fall in different
+    // shared-memory banks for the gather and the scatter.
+    const bool interleave = (want_path == 3);
     auto fill = [&](int s) {
       const int32_t* rp = pr->row_ptr[s];
       int4* out = &R.rec[R.rec_base[s]];
       int32_t pos = 0;
+      std::vector<int32_t> lc;
+      std::vector<float> lv;
       for (int q = 0; q < R.nrows[s]; ++q) {
         const int k = order[s][q];
         const int32_t a = rp[kept[k]], len = rp[kept[k] + 1] - a;
@@ -404,9 +440,28 @@ int create_plan(const rpt_problem* pr, const rpt_device_opts* opts, rpt_plan** o
         std::memcpy(&r4.z, &pp, 4);
         r4.w = k;
         out[q] = r4;
-        std::memcpy(&col_h[base[s] + pos], pr->col_idx[s] + a, sizeof(int32_t) * len);
-        std::memcpy(&val_h[base[s] + pos], pr->val[s] + a, sizeof(float) * len);
-        pos += len;
+        const int32_t plen = (len + 3) & ~3;
+        if (!interleave) {
+          std::memcpy(&col_h[base[s] + pos], pr->col_idx[s] + a, sizeof(int32_t) * len);
+          std::memcpy(&val_h[base[s] + pos], pr->val[s] + a, sizeof(float) * len);
+        } else {
+          lc.assign(plen, 0);
+          lv.assign(plen, 0.f);
+          std::memcpy(lc.data(), pr->col_idx[s] + a, sizeof(int32_t) * len);
+          std::memcpy(lv.data(), pr->val[s] + a, sizeof(float) * len);
+          const int G = stream_lanes(plen), nq = plen / 4;
+          for (int b = 0; b * G < nq; ++b) {
+            const int gb = std::min(G, nq - b * G);
+            for (int sl = 0; sl < gb; ++sl)
+              for (int k = 0; k < 4; ++k) {
+                const size_t dst = (size_t)base[s] + pos + 4 * (b * G + sl) + k;
+                const int src = 4 * b * G + k * gb + sl;
+                col_h[dst] = lc[src];
+                val_h[dst] = lv[src];
+              }
+          }
+        }
+        pos += plen;
       }
       out[R.nrows[s]] = make_int4(pos, 0, 0, 0);
     };
@@ -422,16 +477,27 @@ int create_plan(const rpt_problem* pr, const rpt_device_opts* opts, rpt_plan** o
   }
   // ---- work decomposition: register-direct row blocks (default) or bulk-copy ring ----
   const double per_lane = std::max(0, env_int("RPT_ROW_COST_LANE", 4));   // per-row overhead per lane, in entries
-  // row path: the caller's choice, else RPT_ROW_PATH from the environment, else
-  // the bulk-copy ring when the plan fits it and the register path otherwise
-  const int want_path = (opts && opts->row_path) ? opts->row_path : env_int("RPT_ROW_PATH", 0);
   std::vector<int4> blocks;
   std::vector<int> blk_first(N + 1, 0);
   std::vector<ChunkDesc> chunks;
   std::vector<int> scen_chunk;
-  bool use_tma = false;
+  bool use_tma = false, use_stream = false;
   int ctas = 0;
-  if (want_path != 1) {
+  if (want_path == 3) {
+    int smem_optin = 0;
+    cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, P->device);
+    dp.cmax = std::max(16, env_int("RPT_STR_CMAX", 1536)) & ~15;
+    dp.rmax = std::max(1, env_int("RPT_STR_RMAX", 128));
+    dp.stages = 0;
+    ctas = 1;
+    if (stream_smem_bytes(n_pad, dp.rmax, true) + 1024 <= (size_t)smem_optin)
+      use_stream = build_chunks(R, base, N, dp.cmax, dp.rmax, true, &chunks, &scen_chunk);
+    if (!use_stream) {
+      free_plan(P);
+      set_error("streaming row path not possible for this plan (shared memory)");
+      return RPT_EUNSUPPORTED;
+    }
+  } else if (want_path != 1) {
     int smem_optin = 0;
     cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, P->device);
     dp.cmax = std::max(64, env_int("RPT_TMA_CMAX", 6144)) & ~15;
@@ -440,15 +506,16 @@ int create_plan(const rpt_problem* pr, const rpt_device_opts* opts, rpt_plan** o
     ctas = (opts && opts->ctas_per_sm > 0) ? opts->ctas_per_sm : 1;
     const size_t need = tma_smem_bytes(n_pad, dp.cmax, dp.rmax, dp.stages, bv, bi, true);
     if (need + 1024 <= (size_t)smem_optin)
-      use_tma = build_chunks(R, base, N, dp.cmax, dp.rmax, &chunks, &scen_chunk);
+      use_tma = build_chunks(R, base, N, dp.cmax, dp.rmax, false, &chunks, &scen_chunk);
     if (!use_tma && want_path == 2) {
       free_plan(P);
       set_error("bulk-copy row path not possible for this plan (shared memory, or a row longer than RPT_TMA_CMAX)");
       return RPT_EUNSUPPORTED;
     }
   }
-  if (use_tma) {
-    dp.path = 1;
+  const bool dyn = use_tma || use_stream;   // chunk queues
+  if (dyn) {
+    dp.path = use_tma ? 1 : 2;
     dp.grid = P->sm_count * ctas;
     dp.nblocks = dp.grid * N;          // one slot per (CTA, scenario)
     dp.slot_cap = dp.grid;
@@ -499,7 +566,7 @@ int create_plan(const rpt_problem* pr, const rpt_device_opts* opts, rpt_plan** o
   // slot lists: static for the register path (block b of scenario s), written
   // by the kernel for the bulk-copy path
   std::vector<int> slot_count(N, 0), slot_list((size_t)N * dp.slot_cap, 0);
-  if (!use_tma)
+  if (!dyn)
     for (int s = 0; s < N; ++s) {
       slot_count[s] = blk_first[s + 1] - blk_first[s];
       for (int k = 0; k < slot_count[s]; ++k) slot_list[(size_t)s * dp.slot_cap + k] = blk_first[s] + k;
@@ -513,21 +580,21 @@ int create_plan(const rpt_problem* pr, const rpt_device_opts* opts, rpt_plan** o
   constexpr int64_t kPad = 64;
   Alloc A{P};
   int64_t* d_base = A.get<int64_t>(N);
-  int32_t* d_col32 = A.get<int32_t>(NNZ + kPad);   // replaced by 16-bit indices if requested
-  float* d_val32 = A.get<float>(NNZ + kPad);       // replaced by quantised values if requested
+  int32_t* d_col32 = A.get<int32_t>(NNZp + kPad);   // replaced by 16-bit indices if requested
+  float* d_val32 = A.get<float>(NNZp + kPad);       // replaced by quantised values if requested
   int4* d_rec = A.get<int4>(R.rec.size());
   int* d_recbase = A.get<int>(N + 1);
-  ChunkDesc* d_chunks = use_tma ? A.get<ChunkDesc>(chunks.size()) : nullptr;
-  int* d_scen_chunk = use_tma ? A.get<int>(N + 1) : nullptr;
-  int* d_qnext = use_tma ? A.get<int>(N) : nullptr;
-  unsigned char* d_visited = use_tma ? A.get<unsigned char>((size_t)N * dp.grid) : nullptr;
+  ChunkDesc* d_chunks = dyn ? A.get<ChunkDesc>(chunks.size()) : nullptr;
+  int* d_scen_chunk = dyn ? A.get<int>(N + 1) : nullptr;
+  int* d_qnext = dyn ? A.get<int>(N) : nullptr;
+  unsigned char* d_visited = dyn ? A.get<unsigned char>((size_t)N * dp.grid) : nullptr;
   int* d_slot_count = A.get<int>(N);
   int* d_slot_list = A.get<int>(slot_list.size());
   double* d_objs = A.get<double>(N);
   unsigned int* d_done = A.get<unsigned int>(1);
   P->err = A.get<int>(1);
   P->diag = A.get<float>(diag_h.size());
-  int4* d_blocks = use_tma ? nullptr : A.get<int4>(blocks.size());
+  int4* d_blocks = dyn ? nullptr : A.get<int4>(blocks.size());
   P->lb = A.get<double>(n);
   P->ub = A.get<double>(n);
   const size_t Nn = (size_t)N * n;
@@ -586,13 +653,13 @@ int create_plan(const rpt_problem* pr, const rpt_device_opts* opts, rpt_plan** o
     }                                                                                      \
   } while (0)
   RPT_CP(d_base, base.data(), N * sizeof(int64_t));
-  RPT_CP(d_col32, col_h.data(), (size_t)NNZ * sizeof(int32_t));
-  RPT_CP(d_val32, val_h.data(), (size_t)NNZ * sizeof(float));
+  RPT_CP(d_col32, col_h.data(), (size_t)NNZp * sizeof(int32_t));
+  RPT_CP(d_val32, val_h.data(), (size_t)NNZp * sizeof(float));
   RPT_CP(d_rec, R.rec.data(), R.rec.size() * sizeof(int4));
   RPT_CP(d_recbase, R.rec_base.data(), (N + 1) * sizeof(int));
-  if (!use_tma) RPT_CP(d_blocks, blocks.data(), blocks.size() * sizeof(int4));
+  if (!dyn) RPT_CP(d_blocks, blocks.data(), blocks.size() * sizeof(int4));
   RPT_CP(P->diag, diag_h.data(), diag_h.size() * sizeof(float));
-  if (use_tma) {
+  if (dyn) {
     RPT_CP(d_chunks, chunks.data(), chunks.size() * sizeof(ChunkDesc));
     RPT_CP(d_scen_chunk, scen_chunk.data(), (N + 1) * sizeof(int));
   }
@@ -605,10 +672,10 @@ int create_plan(const rpt_problem* pr, const rpt_device_opts* opts, rpt_plan** o
       (e = cudaMemsetAsync(P->err, 0, sizeof(int), st)) ||
       (e = cudaMemsetAsync(d_done, 0, sizeof(unsigned int), st)) ||
       (e = cudaMemsetAsync(d_objs, 0, sizeof(double) * N, st)) ||
-      (use_tma && (e = cudaMemsetAsync(d_qnext, 0, sizeof(int) * N, st))) ||
-      (use_tma && (e = cudaMemsetAsync(d_visited, 0, (size_t)N * dp.grid, st))) ||
-      (e = cudaMemsetAsync(d_col32 + NNZ, 0, sizeof(int32_t) * kPad, st)) ||
-      (e = cudaMemsetAsync(d_val32 + NNZ, 0, sizeof(float) * kPad, st)) ||
+      (dyn && (e = cudaMemsetAsync(d_qnext, 0, sizeof(int) * N, st))) ||
+      (dyn && (e = cudaMemsetAsync(d_visited, 0, (size_t)N * dp.grid, st))) ||
+      (e = cudaMemsetAsync(d_col32 + NNZp, 0, sizeof(int32_t) * kPad, st)) ||
+      (e = cudaMemsetAsync(d_val32 + NNZp, 0, sizeof(float) * kPad, st)) ||
       (e = cudaMemsetAsync(P->ctl, 0, sizeof(Ctl), st)) ||
       (e = cudaMemsetAsync(P->v32, 0, sizeof(float) * (size_t)N * n_pad, st)) ||
       (e = cudaMemsetAsync(P->vz32, 0, sizeof(float) * n_pad, st))) {
@@ -636,8 +703,8 @@ int create_plan(const rpt_problem* pr, const rpt_device_opts* opts, rpt_plan** o
   if (pr->value_format != RPT_F32) {
     float* scale = A.get<float>((size_t)N * n_pad);
     unsigned int* mx = A.get<unsigned int>(n_pad);
-    void* q = pr->value_format == RPT_BF16 ? (void*)A.get<__nv_bfloat16>(NNZ + kPad)
-                                           : (void*)A.get<__nv_fp8_e4m3>(NNZ + kPad);
+    void* q = pr->value_format == RPT_BF16 ? (void*)A.get<__nv_bfloat16>(NNZp + kPad)
+                                           : (void*)A.get<__nv_fp8_e4m3>(NNZp + kPad);
     if (A.err != cudaSuccess) {
       free_plan(P);
       return cuda_fail(A.err, "device allocation");
@@ -646,15 +713,15 @@ int create_plan(const rpt_problem* pr, const rpt_device_opts* opts, rpt_plan** o
     for (int s = 0; s < N && e == cudaSuccess; ++s) {
       e = cudaMemsetAsync(mx, 0, sizeof(unsigned int) * n_pad, st);
       if (e) break;
-      if (nnz[s] > 0) k_colmax<<<qgrid, qblock, 0, st>>>(d_val32 + base[s], d_col32 + base[s], nnz[s], mx);
+      if (pnnz[s] > 0) k_colmax<<<qgrid, qblock, 0, st>>>(d_val32 + base[s], d_col32 + base[s], pnnz[s], mx);
       k_scales<<<(n_pad + 255) / 256, 256, 0, st>>>(mx, n, n_pad, fmt_max, scale + (size_t)s * n_pad);
-      if (nnz[s] > 0) {
+      if (pnnz[s] > 0) {
         if (pr->value_format == RPT_BF16)
-          k_quantise<__nv_bfloat16><<<qgrid, qblock, 0, st>>>(d_val32 + base[s], d_col32 + base[s], nnz[s],
+          k_quantise<__nv_bfloat16><<<qgrid, qblock, 0, st>>>(d_val32 + base[s], d_col32 + base[s], pnnz[s],
                                                               scale + (size_t)s * n_pad,
                                                               (__nv_bfloat16*)q + base[s]);
         else
-          k_quantise<__nv_fp8_e4m3><<<qgrid, qblock, 0, st>>>(d_val32 + base[s], d_col32 + base[s], nnz[s],
+          k_quantise<__nv_fp8_e4m3><<<qgrid, qblock, 0, st>>>(d_val32 + base[s], d_col32 + base[s], pnnz[s],
                                                               scale + (size_t)s * n_pad,
                                                               (__nv_fp8_e4m3*)q + base[s]);
       }
@@ -670,12 +737,12 @@ int create_plan(const rpt_problem* pr, const rpt_device_opts* opts, rpt_plan** o
     dp.val32 = nullptr;
   }
   if (pr->index_width == 16) {
-    uint16_t* c16 = A.get<uint16_t>(NNZ + kPad);
+    uint16_t* c16 = A.get<uint16_t>(NNZp + kPad);
     if (A.err != cudaSuccess) {
       free_plan(P);
       return cuda_fail(A.err, "device allocation");
     }
-    k_to_u16<<<qgrid, qblock, 0, st>>>(d_col32, NNZ + kPad, c16);
+    k_to_u16<<<qgrid, qblock, 0, st>>>(d_col32, NNZp + kPad, c16);
     if ((e = cudaGetLastError())) {
       free_plan(P);
       return cuda_fail(e, "index conversion");
@@ -719,7 +786,7 @@ int create_plan(const rpt_problem* pr, const rpt_device_opts* opts, rpt_plan** o
   S.sm_count = P->sm_count;
   S.default_rho = 2.0 * (tr / N) / n;
   S.const_term = const_term;
-  S.row_path = dp.path == 1 ? 2 : 1;
+  S.row_path = dp.path == 2 ? 3 : (dp.path == 1 ? 2 : 1);
   S.min_lanes = g_min_lanes;
   *out = reinterpret_cast<rpt_plan*>(P);
   return RPT_OK;

@@ -22,6 +22,8 @@
 //               CTA per SM pulls chunks from per-scenario queues (starting at a
 //               home scenario, moving on when it is exhausted), and keeps one
 //               partial slot per scenario it visited (slot = cta * N + s).
+//   path 2 (streaming): the same chunk queues (chunks cut by row-length class),
+//               but every warp of the persistent CTA claims chunks on its own.
 //   The CTA that finishes last compacts the slots of every scenario into an
 //   ordered list, sums the objective per scenario and resets the queues.
 #pragma once
@@ -34,6 +36,7 @@ namespace rpt {
 
 constexpr int kRowThreads = 512;      // threads of a register-path row-pass CTA
 constexpr int kTmaThreads = 1024;     // threads of a TMA-path CTA (1 producer + 31 consumer warps)
+constexpr int kStrThreads = 512;      // threads of a streaming-path CTA (16 independent warps)
 constexpr int kVecThreads = 256;      // threads of a vector CTA (one column each)
 
 struct ChunkDesc {
@@ -43,14 +46,14 @@ struct ChunkDesc {
   int n_ent;                          // copied entries (multiple of 16)
   int group;                          // lanes per row (1..32), the same for every row of the chunk
   int s;                              // scenario
-  int pad;
+  int pad;                            // streaming path: row-length class of the chunk's rows
 };
 
 struct DevPlan {
   int m, n, N, m_act, n_pad, nblocks;  // nblocks = partial slots
   int value_format;                   // RPT_F32 / RPT_BF16 / RPT_FP8E4M3
   int index_width;                    // 32 or 16
-  int path;                           // 0 register, 1 TMA ring
+  int path;                           // 0 register, 1 TMA ring, 2 streaming
   int grid;                           // CTAs of one row pass
   int cmax, rmax, stages;             // TMA path: entries / rows per stage, ring depth
   int slot_cap;                       // capacity of each scenario's slot list
@@ -132,7 +135,7 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
 
 }  // namespace rpt
 
-// ---- launchers implemented in rowpass.cu -----------------------------------------
+// ---- launchers implemented in rowpass.cu / rowstream.cu ---------------------------
 namespace rpt {
 // v:      staged spot vectors, float32 [N][n_pad] (v_stride = n_pad) or one shared
 //         vector (v_stride = 0)
@@ -146,4 +149,6 @@ int rowpass_threads(const DevPlan& P);
 cudaError_t rowpass_prepare(const DevPlan& P);
 size_t tma_smem_bytes(int n_pad, int cmax, int rmax, int stages, int value_bytes, int index_bytes,
                       bool scatter);
+size_t stream_smem_bytes(int n_pad, int rmax, bool scatter);
+void* stream_rowpass_kernel(const DevPlan& P, int mode);   // rowstream.cu
 }  // namespace rpt

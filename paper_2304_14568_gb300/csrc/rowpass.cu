@@ -25,33 +25,17 @@
 //    error word and the kernel drains its copies and returns.
 //  * k_rowpass (register path): nnz-balanced row blocks, one CTA each; warps
 //    load row entries straight into registers with a one-row prefetch.
-#include "common.cuh"
+//  * k_rowpass_stream (rowstream.cu): persistent CTAs whose warps claim chunks
+//    on their own and stream the entries straight into registers.
+#include "rowcommon.cuh"
 
 namespace rpt {
 namespace {
 
-template <typename VT> __device__ __forceinline__ float to_f(VT x);
-template <> __device__ __forceinline__ float to_f<float>(float x) { return x; }
-template <> __device__ __forceinline__ float to_f<__nv_bfloat16>(__nv_bfloat16 x) { return __bfloat162float(x); }
-template <> __device__ __forceinline__ float to_f<__nv_fp8_e4m3>(__nv_fp8_e4m3 x) { return float(x); }
-
-template <typename VT> __device__ __forceinline__ const VT* vals(const DevPlan& P);
-template <> __device__ __forceinline__ const float* vals<float>(const DevPlan& P) { return P.val32; }
-template <> __device__ __forceinline__ const __nv_bfloat16* vals<__nv_bfloat16>(const DevPlan& P) { return P.valbf; }
-template <> __device__ __forceinline__ const __nv_fp8_e4m3* vals<__nv_fp8_e4m3>(const DevPlan& P) { return P.val8; }
-
-template <typename IT> __device__ __forceinline__ const IT* cols(const DevPlan& P);
-template <> __device__ __forceinline__ const int32_t* cols<int32_t>(const DevPlan& P) { return P.col32; }
-template <> __device__ __forceinline__ const uint16_t* cols<uint16_t>(const DevPlan& P) { return P.col16; }
-
-__host__ __device__ __forceinline__ size_t round128(size_t x) { return (x + 127) & ~(size_t)127; }
 
 // ---------------------------------------------------------------------------
 // mbarrier / bulk-copy primitives (inline PTX)
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
 __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
 }
@@ -101,49 +85,14 @@ __device__ __forceinline__ void named_sync(int id, int count) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
 }
 
-// Stage v_s (scaled by the column scales of quantised values) into sv, zero acc.
-template <bool kScatter>
-__device__ __forceinline__ void stage_vector(const DevPlan& P, const float* __restrict__ vin, int v_stride,
-                                             int s, float* sv, float* acc, int t0, int nt) {
-  const float4* v4 = reinterpret_cast<const float4*>(vin + (size_t)s * v_stride);
-  const float4* cs4 =
-      P.colscale ? reinterpret_cast<const float4*>(P.colscale + (size_t)s * P.n_pad) : nullptr;
-  float4* sv4 = reinterpret_cast<float4*>(sv);
-  float4* acc4 = reinterpret_cast<float4*>(acc);
-  for (int k = t0; k < P.n_pad / 4; k += nt) {
-    float4 x = v4[k];
-    if (cs4) {
-      const float4 q = cs4[k];
-      x.x *= q.x; x.y *= q.y; x.z *= q.z; x.w *= q.w;
-    }
-    sv4[k] = x;
-    if (kScatter) acc4[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-  }
-}
-
-template <bool kScatter>
-__device__ __forceinline__ void flush_acc(const DevPlan& P, int s, const float* acc, float* __restrict__ out,
-                                          int t0, int nt) {
-  if (!kScatter) return;
-  float4* out4 = reinterpret_cast<float4*>(out);
-  const float4* acc4 = reinterpret_cast<const float4*>(acc);
-  const float4* cs4 =
-      P.colscale ? reinterpret_cast<const float4*>(P.colscale + (size_t)s * P.n_pad) : nullptr;
-  for (int k = t0; k < P.n_pad / 4; k += nt) {
-    float4 x = acc4[k];
-    if (cs4) {
-      const float4 q = cs4[k];
-      x.x *= q.x; x.y *= q.y; x.z *= q.z; x.w *= q.w;
-    }
-    out4[k] = x;
-  }
-}
-
 // One group of G lanes processes one row (G in {1, 2, ..., 32}); a warp covers
-// 32/G rows at once.  Each lane keeps up to KR of its row's entries in
-// registers between the dot and the scatter; longer rows (only with G = 32)
-// re-read the rest.  Returns nothing; accumulates into acc / obj / dose.
-template <int MODE, typename VT, typename IT, int KR, bool kSmem>
+// 32/G rows at once.  Lane sl of the group takes entries sl, sl + G, ... so that
+// the lanes of one instruction touch consecutive entries (consecutive spot
+// columns fall in different shared-memory banks for the gather and the scatter).
+// Each lane keeps up to KR of its row's entries in registers between the dot and
+// the scatter; longer rows (only with G = 32) re-read the rest.  Padding entries
+// have value 0: they add nothing to the dot and the scatter skips them.
+template <int MODE, typename VT, typename IT, int KR>
 __device__ __forceinline__ void process_rows(const int4* __restrict__ rec, int r, bool valid, int G, int sl,
                                              const VT* __restrict__ val, const IT* __restrict__ col,
                                              long long off, const float* sv, float* acc, double& obj,
@@ -188,49 +137,12 @@ __device__ __forceinline__ void process_rows(const int4* __restrict__ rec, int r
   if (kScatter) {
 #pragma unroll
     for (int k = 0; k < KR; ++k)
-      if (lo + sl + G * k < hi) atomicAdd(&acc[cr[k]], coef * vr[k]);
-    for (int idx = lo + G * KR + sl; idx < hi; idx += G)
-      atomicAdd(&acc[(int)col[idx]], coef * to_f<VT>(val[idx]));
-  }
-}
-
-// The CTA that finishes last publishes the pass's bookkeeping: per scenario,
-// the ordered list of partial slots that were written (path 1; static for
-// path 0) and the objective summed in slot order; it also resets the chunk
-// queues and the finishing counter for the next pass.  Every CTA must call it.
-template <bool kObjective>
-__device__ __forceinline__ void finish_pass(const DevPlan& P) {
-  __shared__ bool last_cta;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    last_cta = (atomicAdd(P.done_ctr, 1u) + 1u == gridDim.x);
-  }
-  __syncthreads();
-  if (!last_cta) return;
-  __threadfence();
-  for (int s = threadIdx.x; s < P.N; s += blockDim.x) {
-    double o = 0.0;
-    if (P.path == 1) {
-      int cnt = 0;
-      for (int c = 0; c < P.grid; ++c) {
-        volatile unsigned char* vis = P.visited + (size_t)s * P.grid + c;
-        if (*vis) {
-          const int slot = c * P.N + s;
-          P.slot_list[(size_t)s * P.slot_cap + cnt++] = slot;
-          if (kObjective) o += __ldcg(&P.objp[slot]);
-          *vis = 0;
-        }
-      }
-      P.slot_count[s] = cnt;
-      P.qnext[s] = 0;
-    } else if (kObjective) {
-      const int cnt = P.slot_count[s];
-      for (int k = 0; k < cnt; ++k) o += __ldcg(&P.objp[P.slot_list[(size_t)s * P.slot_cap + k]]);
+      if (vr[k] != 0.f) atomicAdd(&acc[cr[k]], coef * vr[k]);
+    for (int idx = lo + G * KR + sl; idx < hi; idx += G) {
+      const float a = to_f<VT>(val[idx]);
+      if (a != 0.f) atomicAdd(&acc[(int)col[idx]], coef * a);
     }
-    if (kObjective) P.objs[s] = o;
   }
-  if (threadIdx.x == 0) *P.done_ctr = 0u;
 }
 
 // ---------------------------------------------------------------------------
@@ -396,7 +308,7 @@ k_rowpass_tma(DevPlan P, const float* __restrict__ vin, int v_stride, const int*
       const size_t dose_base = (size_t)s * P.m_act;
       for (int r0 = cw * rpw; r0 < ch.n_rows; r0 += NCW * rpw) {
         const int r = r0 + sub;
-        process_rows<MODE, VT, IT, KR, true>(rec, r, r < ch.n_rows, G, sl, val, col, off, sv, acc, obj,
+        process_rows<MODE, VT, IT, KR>(rec, r, r < ch.n_rows, G, sl, val, col, off, sv, acc, obj,
                                               dose, dose_base);
       }
       __syncwarp();
@@ -461,7 +373,7 @@ k_rowpass(DevPlan P, const float* __restrict__ vin, int v_stride, const int* __r
       r0 = __shfl_sync(0xffffffffu, r0, 0);
       if (r0 >= blk.z) break;
       const int r = r0 + sub;
-      process_rows<MODE, VT, IT, KR, false>(rec, r, r < blk.z, G, sl, val, col, 0, sv, acc, obj, dose,
+      process_rows<MODE, VT, IT, KR>(rec, r, r < blk.z, G, sl, val, col, 0, sv, acc, obj, dose,
                                             dose_base);
     }
     if (kObjective) {
@@ -483,6 +395,7 @@ constexpr int kKR = 8;
 
 template <int MODE>
 void* pick(const DevPlan& P) {
+  if (P.path == 2) return stream_rowpass_kernel(P, MODE);
   if (P.path == 1) {
     if (P.index_width == 16) {
       switch (P.value_format) {
@@ -536,10 +449,13 @@ size_t rowpass_smem(const DevPlan& P, int mode) {
     const int ib = P.index_width == 16 ? 2 : 4;
     return tma_smem_bytes(P.n_pad, P.cmax, P.rmax, P.stages, vb, ib, scatter);
   }
+  if (P.path == 2) return stream_smem_bytes(P.n_pad, P.rmax, scatter);
   return (size_t)P.n_pad * sizeof(float) * (scatter ? 2 : 1);
 }
 
-int rowpass_threads(const DevPlan& P) { return P.path == 1 ? kTmaThreads : kRowThreads; }
+int rowpass_threads(const DevPlan& P) {
+  return P.path == 1 ? kTmaThreads : (P.path == 2 ? kStrThreads : kRowThreads);
+}
 
 // The dynamic shared-memory cap is a per-function, process-wide attribute, so
 // it is raised to the device's opt-in maximum (never lowered): plans with

@@ -98,11 +98,13 @@ def test_iterates_match_oracle(rpt, bb, zm):
             assert info["r_prim"] == pytest.approx(ref["r_prim"], rel=1e-3, abs=1e-5 * sz)
 
 
-def test_converges_to_exact_optimum_tiny_plain(rpt, tiny_plain):
+@pytest.mark.parametrize("row_path", [0, 3])
+def test_converges_to_exact_optimum_tiny_plain(rpt, tiny_plain, row_path):
     """Default parameters, tight tolerances: objective within 1e-6 of the exact
-    box-constrained optimum (lsq_linear), certificates near zero."""
+    box-constrained optimum (lsq_linear), certificates near zero; default row
+    path and the streaming row path."""
     prob, W, xs, fstar = tiny_plain
-    with plan_of(rpt, prob) as P:
+    with plan_of(rpt, prob, row_path=row_path) as P:
         z, info = P.admm_bb_solve(eps_abs=1e-7, eps_rel=1e-7, max_iter=20000)
     f_gpu = W.f(z)
     assert np.all(z >= prob.lb) and np.all(z <= prob.ub)
@@ -206,11 +208,12 @@ def test_warm_start_and_dual_start(rpt):
     assert abs(W.f(z) - W.f(xs)) / W.f(xs) < 1e-6
 
 
-def test_pgd_matches_oracle(rpt, tiny_plain):
+@pytest.mark.parametrize("row_path", [0, 3])
+def test_pgd_matches_oracle(rpt, tiny_plain, row_path):
     prob, W, xs, fstar = tiny_plain
     L = lipschitz(W)
     ref = pgd(W, alpha=4.0 / L, tol_rel_df=1e-6, max_iter=300, record=True)
-    with plan_of(rpt, prob) as P:
+    with plan_of(rpt, prob, row_path=row_path) as P:
         x, info = P.pgd_solve(alpha=4.0 / L, tol_rel_df=1e-6, max_iter=300)
         _, info_auto = P.pgd_solve(tol_rel_df=1e-6, max_iter=5)
     assert info_auto["rho"] == pytest.approx(L, rel=1e-4)          # the library's own estimate

@@ -20,6 +20,7 @@ CASES = {
     "one_spot": dict(seed=3, m=200, n=1, N=2, mean_row=1.0),
     "n33_N1": dict(seed=4, m=257, n=33, N=1, mean_row=9.0, empty_frac=0.4),
     "many_empty": dict(seed=5, m=2000, n=130, N=4, mean_row=6.0, empty_frac=0.9, zero_w_frac=0.2),
+    "dense_1200": dict(seed=6, m=150, n=1200, N=2, mean_row=25.0, long_rows=3),   # rows past 512 entries
 }
 
 
@@ -28,12 +29,16 @@ def rpt():
     return gpu_lib()
 
 
-# row-pass implementations: register-direct loads, the bulk-copy ring, and the
-# ring with tiny stages (many chunks per segment, stage wrap-around, segment switches)
+# row-pass implementations: register-direct loads, the bulk-copy ring, the ring
+# with tiny stages (many chunks per segment, stage wrap-around, segment
+# switches), the streaming path, and the streaming path with tiny chunks (many
+# chunk hand-overs, class changes inside a warp's run, one-row chunks)
 PATHS = {
     "reg": (1, {}),
     "tma": (2, {}),
-    "tma_small": (2, {"RPT_TMA_CMAX": "512", "RPT_TMA_RMAX": "8", "RPT_TMA_STAGES": "2"}),
+    "tma_small": (2, {"RPT_TMA_CMAX": "1280", "RPT_TMA_RMAX": "8", "RPT_TMA_STAGES": "2"}),
+    "stream": (3, {}),
+    "stream_small": (3, {"RPT_STR_CMAX": "64", "RPT_STR_RMAX": "3"}),
 }
 
 
@@ -159,6 +164,19 @@ def test_row_path_selection(rpt, monkeypatch):
         U = P.apply_normal(np.ones((prob.N, prob.n)), 1.0)
     W = Weighted(prob)
     np.testing.assert_allclose(U[0], W.normal_apply(0, np.ones(prob.n), 1.0), rtol=1e-4)
+
+
+def test_stream_path_takes_rows_longer_than_a_chunk(rpt, monkeypatch):
+    monkeypatch.setenv("RPT_STR_CMAX", "128")           # rows of 300 entries: one-row chunks
+    prob = random_problem(**CASES["long_rows"])
+    with plan_of(rpt, prob, row_path=3) as P:
+        assert P.stats()["row_path"] == 3
+        V = np.random.default_rng(3).uniform(-1, 1, size=(prob.N, prob.n))
+        U = P.apply_normal(V, 0.5)
+    W = Weighted(prob)
+    for s in range(prob.N):
+        ref = W.normal_apply(s, V[s], 0.5)
+        np.testing.assert_allclose(U[s], ref, rtol=2e-4, atol=2e-4 * np.abs(ref).max())
 
 
 def test_profile_row_pass(rpt):
