@@ -176,6 +176,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-pgd", action="store_true")
+    ap.add_argument("--no-forms", action="store_true", help="skip the reduced-precision storage forms")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--ref-budget", type=float, default=15.0)
     ap.add_argument("--max-iter", type=int, default=0,
@@ -301,6 +302,31 @@ def main():
                       "trials": pinfo["inner"], "row_passes": pinfo["row_passes"], "f": pinfo["f"],
                       "target_f": fa * (1 + 1e-6), "status": pinfo["status"],
                       "speedup_admm_over_pgd": (pe0.elapsed_time(pe1) / 1e3) / (ms_step / 1e3)}
+
+    if not args.no_forms:
+        # reduced-precision storage forms on the same workload: row-pass bandwidth
+        # and time to the same tolerance; objective of their optimum on the float32 plan
+        forms = {}
+        for name, vf, iw in (("f32+u16", rpt.F32, 16), ("bf16+u16", rpt.BF16, 16), ("fp8+u16", rpt.FP8E4M3, 16)):
+            pf = rpt.Plan.from_problem(prob, device=dev, stream=stream.cuda_stream, value_format=vf,
+                                       index_width=iw, row_path=args.row_path)
+            pf.apply_normal(rng.uniform(0.0, 5.0, size=(prob.N, prob.n)), 0.0)
+            ms_f, by_f = pf.profile_row_pass(0, reps=20)
+            pf.admm_bb_solve(params)                     # warm-up solve
+            fe0 = torch.cuda.Event(enable_timing=True)
+            fe1 = torch.cuda.Event(enable_timing=True)
+            fe0.record(stream)
+            zf, fi = pf.admm_bb_solve(params)
+            fe1.record(stream)
+            torch.cuda.synchronize(dev)
+            f_on_f32 = plan.objective(zf)
+            forms[name] = {"ms_per_pass": ms_f, "bytes_per_pass": by_f, "gbs": by_f / ms_f / 1e6,
+                           "frac_of_peak": by_f / ms_f / 1e6 / peak,
+                           "solve_s": fe0.elapsed_time(fe1) / 1e3, "iterations": fi["iterations"],
+                           "row_passes": fi["row_passes"],
+                           "f_rel_vs_f32_optimum": (f_on_f32 - infos[-1]["f"]) / infos[-1]["f"]}
+            pf.close()
+        out["forms"] = forms
 
     if not args.no_e2e:
         # end to end through the C ABI with host buffers: upload + solve + result read-back

@@ -18,6 +18,8 @@ against the paper by eye:
                 and a library bounded least-squares solve, plus certificates
   boyd.py       textbook scaled-form consensus ADMM, written separately, which
                 ADMM-BB must reproduce when the BB step is switched off
+  quantize.py   the reduced-precision storage form (per-column FP32 scale,
+                bfloat16 or FP8-e4m3 codes) as a plain definition
 
 Readings where the paper is silent or garbled (each one is a parameter):
   * z-update: z = P(mean_s(x_s + y_s/rho)) by default ("std"); the paper's
@@ -32,3 +34,4 @@ from .admm_bb import admm_bb  # noqa: F401
 from .pgd import pgd  # noqa: F401
 from .exact import kkt_bruteforce, lsq_box, certificates  # noqa: F401
 from .boyd import consensus_admm_scaled  # noqa: F401
+from .quantize import quantised_problem, quantise_values, bf16_round, e4m3_round  # noqa: F401

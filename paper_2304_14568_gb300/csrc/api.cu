@@ -32,7 +32,7 @@ __global__ void k_colmax(const float* __restrict__ val, const int32_t* __restric
                          unsigned int* __restrict__ mx) {
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nnz;
        k += (int64_t)gridDim.x * blockDim.x)
-    atomicMax(&mx[col[k]], __float_as_uint(val[k]));   // values are >= 0
+    atomicMax(&mx[col[k]], __float_as_uint(fabsf(val[k])));   // |a| >= 0 orders like its bits
 }
 
 __global__ void k_scales(const unsigned int* __restrict__ mx, int n, int n_pad, float fmt_max,
