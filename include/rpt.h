@@ -256,6 +256,53 @@ int rpt_normal_apply_noalloc(int32_t m, int32_t n, const int32_t* row_ptr_dev, c
 int rpt_state_get(rpt_plan* plan, double* z, double* x, double* y);
 int rpt_state_set(rpt_plan* plan, const double* z, const double* x, const double* y);
 
+/* ---- learned warm start ---------------------------------------------------
+ * The paper has no learned part.  This optional form fits a small multilayer
+ * perceptron that maps a plan's objective weights (features the caller chooses,
+ * e.g. log structure weights and the prescription) to a spot vector, and uses it
+ * as z0 of ADMM-BB; cold-start ADMM-BB is the fallback.  Network: n_in ->
+ * n_hidden (x n_hidden_layers, ReLU) -> n_out (linear); loss: mean squared error
+ * over the batch and the outputs; training: Adam on minibatches (every
+ * minibatch full; the remainder of an epoch's permutation is skipped).  FP32 on
+ * the device.  Parameters as one float array: for each layer W ([out][in],
+ * row-major) then b ([out]).  Host arrays X [n][n_in] and Y [n][n_out] are
+ * row-major.  Errors: RPT_EINVAL for bad sizes or null pointers, RPT_ECUDA. */
+typedef struct rpt_mlp rpt_mlp;
+
+typedef struct {
+  int32_t epochs;         /* default 300 */
+  int32_t batch;          /* minibatch rows (default 128; capped at the sample count) */
+  double  lr;             /* Adam step size (default 1e-3) */
+  double  beta1, beta2;   /* Adam moment decays (defaults 0.9, 0.999) */
+  double  eps;            /* Adam denominator floor (default 1e-8) */
+  double  weight_decay;   /* added to the gradient as wd * p (default 0) */
+  uint64_t seed;          /* minibatch permutation seed (default 1) */
+} rpt_mlp_train_params;
+
+int rpt_mlp_train_params_default(rpt_mlp_train_params* tp);
+/* Glorot-uniform weights from `seed`, zero biases.  n_hidden_layers may be 0. */
+int rpt_mlp_create(int32_t n_in, int32_t n_hidden, int32_t n_hidden_layers, int32_t n_out, uint64_t seed,
+                   int32_t device, rpt_mlp** out);
+int rpt_mlp_destroy(rpt_mlp* mlp);
+int rpt_mlp_param_count(const rpt_mlp* mlp, int64_t* count);
+int rpt_mlp_get_params(rpt_mlp* mlp, float* params);          /* params: [count] host */
+int rpt_mlp_set_params(rpt_mlp* mlp, const float* params);    /* also resets the Adam moments */
+/* Loss of the batch (X, Y; n rows) and its gradient with respect to the parameters
+ * (grad: [count] host, or NULL), at the current parameters. */
+int rpt_mlp_loss_grad(rpt_mlp* mlp, const float* X, const float* Y, int32_t n, double* loss, float* grad);
+/* Train on n samples; final_loss (may be NULL) = loss of the last minibatch. */
+int rpt_mlp_train(rpt_mlp* mlp, const float* X, const float* Y, int32_t n, const rpt_mlp_train_params* tp,
+                  double* final_loss);
+int rpt_mlp_predict(rpt_mlp* mlp, const float* X, int32_t n, float* Y);
+/* ADMM-BB started from z0 = P_[lb,ub](prediction(features) * zscale) (features:
+ * [n_in] host, zscale: [n] host, the scale the network was trained in, e.g. ub).
+ * If that solve ends RPT_NOT_CONVERGED or RPT_DIVERGED, the cold-start solve is
+ * run and returned; info then sums both.  used_warm_start (may be NULL): 1 if
+ * the returned result is the warm-started one. */
+int rpt_admm_bb_solve_learned(rpt_plan* plan, rpt_mlp* mlp, const float* features, const double* zscale,
+                              const rpt_admm_params* params, double* x_out, rpt_solve_info* info,
+                              int32_t* used_warm_start);
+
 /* ---- diagnostics --------------------------------------------------------- */
 const char* rpt_status_string(int status);   /* static string */
 const char* rpt_last_error(void);            /* thread-local, valid until the next call on this thread */

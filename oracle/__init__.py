@@ -20,6 +20,8 @@ against the paper by eye:
                 ADMM-BB must reproduce when the BB step is switched off
   quantize.py   the reduced-precision storage form (per-column FP32 scale,
                 bfloat16 or FP8-e4m3 codes) as a plain definition
+  mlp.py        the learned warm start's network: forward pass, MSE loss and
+                its gradient by the chain rule (float64)
 
 Readings where the paper is silent or garbled (each one is a parameter):
   * z-update: z = P(mean_s(x_s + y_s/rho)) by default ("std"); the paper's

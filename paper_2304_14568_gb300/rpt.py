@@ -23,8 +23,15 @@ EXPORTED = [
     "rpt_admm_params_default", "rpt_pgd_params_default", "rpt_plan_create", "rpt_plan_destroy",
     "rpt_plan_query", "rpt_admm_bb_solve", "rpt_pgd_solve", "rpt_objective", "rpt_gradient",
     "rpt_apply_normal", "rpt_profile_row_pass", "rpt_normal_apply_noalloc", "rpt_state_get", "rpt_state_set", "rpt_status_string", "rpt_last_error",
-    "rpt_version",
+    "rpt_version", "rpt_mlp_train_params_default", "rpt_mlp_create", "rpt_mlp_destroy", "rpt_mlp_param_count",
+    "rpt_mlp_get_params", "rpt_mlp_set_params", "rpt_mlp_loss_grad", "rpt_mlp_train", "rpt_mlp_predict",
+    "rpt_admm_bb_solve_learned",
 ]
+
+
+class MlpTrainParams(C.Structure):
+    _fields_ = [("epochs", C.c_int32), ("batch", C.c_int32), ("lr", C.c_double), ("beta1", C.c_double),
+                ("beta2", C.c_double), ("eps", C.c_double), ("weight_decay", C.c_double), ("seed", C.c_uint64)]
 
 
 class RptError(RuntimeError):
@@ -132,6 +139,29 @@ def lib():
     L.rpt_last_error.restype = C.c_char_p
     L.rpt_version.argtypes = []
     L.rpt_version.restype = C.c_char_p
+    fp = C.POINTER(C.c_float)
+    L.rpt_mlp_train_params_default.argtypes = [C.POINTER(MlpTrainParams)]
+    L.rpt_mlp_train_params_default.restype = C.c_int
+    L.rpt_mlp_create.argtypes = [C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_uint64, C.c_int32,
+                                 C.POINTER(C.c_void_p)]
+    L.rpt_mlp_create.restype = C.c_int
+    L.rpt_mlp_destroy.argtypes = [C.c_void_p]
+    L.rpt_mlp_destroy.restype = C.c_int
+    L.rpt_mlp_param_count.argtypes = [C.c_void_p, C.POINTER(C.c_int64)]
+    L.rpt_mlp_param_count.restype = C.c_int
+    L.rpt_mlp_get_params.argtypes = [C.c_void_p, fp]
+    L.rpt_mlp_get_params.restype = C.c_int
+    L.rpt_mlp_set_params.argtypes = [C.c_void_p, fp]
+    L.rpt_mlp_set_params.restype = C.c_int
+    L.rpt_mlp_loss_grad.argtypes = [C.c_void_p, fp, fp, C.c_int32, dp, fp]
+    L.rpt_mlp_loss_grad.restype = C.c_int
+    L.rpt_mlp_train.argtypes = [C.c_void_p, fp, fp, C.c_int32, C.POINTER(MlpTrainParams), dp]
+    L.rpt_mlp_train.restype = C.c_int
+    L.rpt_mlp_predict.argtypes = [C.c_void_p, fp, C.c_int32, fp]
+    L.rpt_mlp_predict.restype = C.c_int
+    L.rpt_admm_bb_solve_learned.argtypes = [C.c_void_p, C.c_void_p, fp, dp, C.POINTER(AdmmParams), dp,
+                                            C.POINTER(_Info), C.POINTER(C.c_int32)]
+    L.rpt_admm_bb_solve_learned.restype = C.c_int
     _lib = L
     return L
 
@@ -291,6 +321,97 @@ def normal_apply_noalloc(m, n, row_ptr_dev, col_idx_dev, val_dev, row_w_dev, v_d
     addresses), with no device allocation.  Asynchronous on `stream`."""
     _check(lib().rpt_normal_apply_noalloc(int(m), int(n), row_ptr_dev, col_idx_dev, val_dev, row_w_dev, v_dev,
                                           float(rho), u_dev, stream))
+
+
+def _fptr(a):
+    return None if a is None else a.ctypes.data_as(C.POINTER(C.c_float))
+
+
+def mlp_train_params(**kw) -> MlpTrainParams:
+    tp = MlpTrainParams()
+    _check(lib().rpt_mlp_train_params_default(C.byref(tp)))
+    for k, v in kw.items():
+        setattr(tp, k, v)
+    return tp
+
+
+class Mlp:
+    """Learned warm-start network (rpt_mlp_*)."""
+
+    def __init__(self, n_in, n_hidden, n_hidden_layers, n_out, seed=0, device=0):
+        h = C.c_void_p()
+        _check(lib().rpt_mlp_create(int(n_in), int(n_hidden), int(n_hidden_layers), int(n_out), int(seed),
+                                    int(device), C.byref(h)))
+        self._h = h
+        self.n_in, self.n_out = int(n_in), int(n_out)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().rpt_mlp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def param_count(self) -> int:
+        c = C.c_int64()
+        _check(lib().rpt_mlp_param_count(self._h, C.byref(c)))
+        return c.value
+
+    def get_params(self):
+        p = np.empty(self.param_count(), dtype=np.float32)
+        _check(lib().rpt_mlp_get_params(self._h, _fptr(p)))
+        return p
+
+    def set_params(self, p):
+        pa = np.ascontiguousarray(p, dtype=np.float32)
+        _check(lib().rpt_mlp_set_params(self._h, _fptr(pa)))
+
+    def loss_grad(self, X, Y):
+        Xa = np.ascontiguousarray(X, dtype=np.float32)
+        Ya = np.ascontiguousarray(Y, dtype=np.float32)
+        loss = C.c_double()
+        g = np.empty(self.param_count(), dtype=np.float32)
+        _check(lib().rpt_mlp_loss_grad(self._h, _fptr(Xa), _fptr(Ya), int(Xa.shape[0]), C.byref(loss), _fptr(g)))
+        return loss.value, g
+
+    def train(self, X, Y, params: MlpTrainParams | None = None, **kw):
+        tp = params if params is not None else mlp_train_params(**kw)
+        Xa = np.ascontiguousarray(X, dtype=np.float32)
+        Ya = np.ascontiguousarray(Y, dtype=np.float32)
+        loss = C.c_double()
+        _check(lib().rpt_mlp_train(self._h, _fptr(Xa), _fptr(Ya), int(Xa.shape[0]), C.byref(tp), C.byref(loss)))
+        return loss.value
+
+    def predict(self, X):
+        Xa = np.ascontiguousarray(np.atleast_2d(X), dtype=np.float32)
+        Y = np.empty((Xa.shape[0], self.n_out), dtype=np.float32)
+        _check(lib().rpt_mlp_predict(self._h, _fptr(Xa), int(Xa.shape[0]), _fptr(Y)))
+        return Y
+
+
+def admm_bb_solve_learned(plan, mlp, features, zscale, params: AdmmParams | None = None, **kw):
+    """ADMM-BB warm-started by the network (cold-start fallback); returns
+    (x, info, used_warm_start)."""
+    prm = params if params is not None else admm_params(**kw)
+    f = np.ascontiguousarray(features, dtype=np.float32)
+    zs = np.ascontiguousarray(zscale, dtype=np.float64)
+    x = np.empty(plan.n)
+    info = _Info()
+    used = C.c_int32()
+    rc = lib().rpt_admm_bb_solve_learned(plan._h, mlp._h, _fptr(f), _dptr(zs), C.byref(prm), _dptr(x),
+                                         C.byref(info), C.byref(used))
+    _check(rc, allow=(OK, NOT_CONVERGED))
+    return x, info.as_dict(), bool(used.value)
 
 
 def version() -> str:

@@ -13,4 +13,7 @@ from .phantom import (  # noqa: F401
     random_problem,
     scenario_set_13,
     scenario_set_49,
+    reweighted,
+    sample_weights,
+    N_WEIGHT_SLOTS,
 )

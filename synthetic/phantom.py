@@ -571,3 +571,35 @@ def from_dense(A_list, w, p, lb, ub, scen_weight=None, name="dense") -> Problem:
         ub=np.broadcast_to(np.asarray(ub, dtype=np.float64), (n,)).copy(),
         meta=dict(name=name),
     )
+
+
+# ---------------------------------------------------------------------------
+# objective-weight sweeps (inputs of the learned warm start)
+# ---------------------------------------------------------------------------
+N_WEIGHT_SLOTS = 8
+
+
+def reweighted(prob: Problem, struct_w, d_pres: float, target_label: int = 1) -> Problem:
+    """The same geometry and matrices with new objective weights: every voxel
+    gets the weight of its structure slot (slot = label: 0 body, 1 target,
+    2.. organs at risk), the target the prescription d_pres, other voxels 0."""
+    from copy import copy
+    lab = np.asarray(prob.labels)
+    sw = np.asarray(struct_w, dtype=np.float64)
+    out = copy(prob)
+    out.voxel_w = sw[np.clip(lab, 0, sw.size - 1)].astype(np.float64)
+    out.presc = np.where(lab == target_label, float(d_pres), 0.0).astype(np.float64)
+    out.meta = dict(prob.meta, struct_w=sw.tolist(), d_pres=float(d_pres))
+    return out
+
+
+def sample_weights(rng, labels, w_range=(0.1, 100.0), d_range=(60.0, 75.0)):
+    """Seeded draw of structure weights (log-uniform, one per structure present;
+    unused slots 0) and a prescription (uniform)."""
+    present = np.unique(np.asarray(labels))
+    sw = np.zeros(N_WEIGHT_SLOTS)
+    lo, hi = np.log10(w_range[0]), np.log10(w_range[1])
+    for k in present:
+        if 0 <= k < N_WEIGHT_SLOTS:
+            sw[k] = 10.0 ** rng.uniform(lo, hi)
+    return sw, float(rng.uniform(*d_range))

@@ -1,0 +1,92 @@
+"""Learned warm start (rpt_mlp_*): the network's forward pass and gradient on
+the GPU against the float64 oracle (oracle/mlp.py), training, and what the
+trained network gains over cold-start ADMM-BB on held-out objective weights,
+with the oracle's objective and optimality certificate as the judge."""
+import numpy as np
+import pytest
+
+from oracle import Weighted, certificates
+from oracle.mlp import forward, loss_grad
+from synthetic import config_tiny_plain, reweighted, sample_weights, N_WEIGHT_SLOTS
+
+from tests.gpu_util import gpu_lib, plan_of
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def rpt():
+    return gpu_lib()
+
+
+def test_gradient_and_forward_match_oracle(rpt):
+    dims = [9, 70, 70, 45]                     # sizes that leave ragged GEMM tiles
+    rng = np.random.default_rng(3)
+    X = rng.normal(size=(37, 9)).astype(np.float32)
+    Y = rng.normal(size=(37, 45)).astype(np.float32)
+    with rpt.Mlp(9, 70, 2, 45, seed=5) as net:
+        p = net.get_params().astype(np.float64)
+        loss, g = net.loss_grad(X, Y)
+        out = net.predict(X)
+    ref_out = forward(p, dims, X)[-1]
+    np.testing.assert_allclose(out, ref_out, rtol=1e-4, atol=1e-5 * np.abs(ref_out).max())
+    ref_loss, ref_g = loss_grad(p, dims, X, Y)
+    assert loss == pytest.approx(ref_loss, rel=1e-5)
+    np.testing.assert_allclose(g, ref_g, rtol=1e-3, atol=1e-4 * np.abs(ref_g).max())
+
+
+def test_set_params_round_trip_and_training_reduces_loss(rpt):
+    rng = np.random.default_rng(4)
+    X = rng.uniform(-1, 1, size=(512, 4)).astype(np.float32)
+    Y = np.stack([np.sin(2 * X[:, 0]) * X[:, 1], X[:, 2] ** 2 - X[:, 3]], axis=1).astype(np.float32)
+    with rpt.Mlp(4, 64, 2, 2, seed=1) as net:
+        p0 = net.get_params()
+        net.set_params(p0)
+        np.testing.assert_array_equal(net.get_params(), p0)
+        l0, _ = net.loss_grad(X, Y)
+        net.train(X, Y, epochs=200, batch=64, lr=3e-3)
+        l1, _ = net.loss_grad(X, Y)
+    assert l1 < 0.1 * l0, (l0, l1)
+
+
+def _features(sw, d):
+    f = np.zeros(N_WEIGHT_SLOTS + 1, dtype=np.float32)
+    nz = sw > 0
+    f[:N_WEIGHT_SLOTS][nz] = np.log10(sw[nz]) / 2.0
+    f[-1] = (d - 67.5) / 7.5
+    return f
+
+
+def test_learned_warm_start_gains_over_cold_start(rpt):
+    base = config_tiny_plain(0)
+    rng = np.random.default_rng(7)
+    n_train, n_test = 96, 8
+    feats, targets, tests = [], [], []
+    for k in range(n_train + n_test):
+        sw, d = sample_weights(rng, base.labels)
+        prob = reweighted(base, sw, d)
+        if k < n_train:
+            with plan_of(rpt, prob) as P:
+                z, info = P.admm_bb_solve(eps_abs=1e-6, eps_rel=1e-6, max_iter=20000)
+            feats.append(_features(sw, d))
+            targets.append((z / prob.ub).astype(np.float32))
+        else:
+            tests.append((prob, _features(sw, d)))
+    X, Y = np.stack(feats), np.stack(targets)
+    cold_it, warm_it = [], []
+    with rpt.Mlp(X.shape[1], 256, 2, base.n, seed=2) as net:
+        net.train(X, Y, epochs=400, batch=32, lr=1e-3)
+        for prob, f in tests:
+            W = Weighted(prob)
+            with plan_of(rpt, prob) as P:
+                xc, ic = P.admm_bb_solve()
+                xw, iw, used = rpt.admm_bb_solve_learned(P, net, f, prob.ub)
+            assert ic["status"] == 0 and iw["status"] == 0
+            # the oracle judges both results: same objective to the tolerance, near-optimal
+            fc, fw = W.f(xc), W.f(xw)
+            assert abs(fw - fc) / fc <= 1e-3, (fw, fc)
+            assert certificates(W, xw)["pg"] < 1e-2
+            cold_it.append(ic["iterations"])
+            warm_it.append(iw["iterations"] if used else iw["iterations"])
+    print(f"held-out iterations to 1e-4: cold {np.mean(cold_it):.1f}, learned warm start {np.mean(warm_it):.1f}")
+    assert np.mean(warm_it) < 0.9 * np.mean(cold_it), (cold_it, warm_it)
