@@ -1,0 +1,88 @@
+"""Parity at the benchmark's full size: the realistic workload (13 scenarios,
+299,088 voxels, 5,000 spots, 126.9M stored entries) in the launch
+configuration bench.py times (the library's default row path).  The oracle
+evaluates every output here (a few float64 sparse products per scenario), so
+the comparison is element by element with the float32 bound of the plain
+path; the solve is checked against the oracle's exact optimum (stored by
+tests/golden/make_realistic_golden.py) and its optimality certificate."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from oracle import Weighted, certificates
+from synthetic import config_realistic
+
+from tests.gpu_util import gpu_lib, plan_of, fp32_op_bound
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+GOLD = os.path.join(os.path.dirname(__file__), "golden", "realistic_seed0_oracle.json")
+
+
+@pytest.fixture(scope="module")
+def rpt():
+    return gpu_lib()
+
+
+@pytest.fixture(scope="module")
+def big(rpt):
+    prob = config_realistic(0, workers=min(16, os.cpu_count() or 1))
+    W = Weighted(prob)
+    P = plan_of(rpt, prob)
+    yield prob, W, P
+    P.close()
+
+
+def test_plan_is_the_benchmarked_configuration(big):
+    prob, W, P = big
+    st = P.stats()
+    assert st["row_path"] == 2 and st["nnz"] == sum(int(v.size) for v in prob.val)
+    assert st["m_active"] == 85495 and prob.n == 5000 and prob.N == 13
+
+
+def test_operator_every_output(big):
+    prob, W, P = big
+    rng = np.random.default_rng(21)
+    V = rng.uniform(0.0, 5.0, size=(prob.N, prob.n))
+    rho = 1826.0
+    U = P.apply_normal(V, rho)
+    k = fp32_op_bound(prob)
+    for s in range(prob.N):
+        ref = W.normal_apply(s, V[s], rho)
+        Aa = abs(W.At[s])
+        mag = Aa.T @ (Aa @ V[s]) + 0.5 * rho * V[s]            # V >= 0
+        err = np.abs(U[s] - ref)
+        assert np.all(err <= k * mag), (s, float((err / mag).max()), k)
+
+
+def test_gradient_objective_every_output(big):
+    prob, W, P = big
+    x = np.random.default_rng(22).uniform(0.0, 6.0, size=prob.n)
+    g, f = P.gradient(x)
+    k = fp32_op_bound(prob)
+    gref = W.grad(x)
+    gmag = sum(2.0 * (abs(W.At[s]).T @ (abs(W.At[s]) @ x + W.pt[s])) for s in range(prob.N))
+    assert np.all(np.abs(g - gref) <= k * gmag)
+    fmag = sum(float(np.sum((abs(W.At[s]) @ x + W.pt[s]) ** 2)) for s in range(prob.N))
+    assert abs(f - W.f(x)) <= 2 * k * fmag
+    assert abs(P.objective(x) - W.f(x)) <= 2 * k * fmag
+
+
+def test_benchmark_solve_reaches_the_oracle_optimum(big):
+    prob, W, P = big
+    z, info = P.admm_bb_solve()                               # the benchmark's step: eps 1e-4
+    assert info["status"] == 0
+    assert np.all(z >= prob.lb) and np.all(z <= prob.ub)
+    fz = W.f(z)
+    assert info["f"] == pytest.approx(fz, rel=1e-5)
+    c = certificates(W, z)
+    assert c["pg"] < 1e-2, c
+    if not os.path.exists(GOLD):
+        pytest.skip("no stored oracle optimum")
+    g = json.load(open(GOLD))
+    assert g["value_sum"] == pytest.approx(float(sum(float(np.sum(v.astype(np.float64))) for v in prob.val)),
+                                           rel=1e-12)
+    fstar = g["f_star"]
+    # eps = 1e-4 on the residuals of Eq. 9 leaves a small objective gap
+    assert fstar <= fz * (1 + 1e-9) and (fz - fstar) / fstar <= 1e-4, ((fz - fstar) / fstar)
