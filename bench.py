@@ -143,6 +143,56 @@ def cpu_baseline(prob, budget_s=20.0):
             "setup_s": round(t_setup, 2)}
 
 
+def run_batch(args, rpt, dev, stream, peak):
+    """Batched form: four plans of uneven size over 49 scenarios solved one by
+    one, then as one block-diagonal plan (one persistent row pass over all of
+    them, ring configuration picked by the autotuner)."""
+    import numpy as np
+    import torch
+    from synthetic import config_batch, block_diagonal
+    t0 = time.perf_counter()
+    probs = config_batch(args.seed, workers=args.workers)
+    gen_s = time.perf_counter() - t0
+    params = rpt.admm_params()
+
+    def timed_solve(P):
+        P.admm_bb_solve(params)                              # warm-up
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        z, info = P.admm_bb_solve(params)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        return z, info, e0.elapsed_time(e1) / 1e3
+
+    seq = []
+    for p in probs:
+        P = rpt.Plan.from_problem(p, device=dev, stream=stream.cuda_stream)
+        z, info, t = timed_solve(P)
+        ms, by = P.profile_row_pass(0, reps=10)
+        seq.append({"m": p.m, "n": p.n, "nnz": int(P.stats()["nnz"]), "solve_s": t, "iterations": info["iterations"],
+                    "f": info["f"], "pass_ms": ms, "pass_gbs": by / ms / 1e6})
+        P.close()
+    big = block_diagonal(probs)
+    del probs
+    t1 = time.perf_counter()
+    P = rpt.Plan.from_problem(big, device=dev, stream=stream.cuda_stream, autotune=1)
+    create_s = time.perf_counter() - t1
+    st = P.stats()
+    z, info, t = timed_solve(P)
+    ms, by = P.profile_row_pass(0, reps=10)
+    P.close()
+    return {"workload": "4 plans (voxels, spots) = 100k/2k, 170k/3k, 230k/4k, 300k/5k; 49 scenarios each; "
+                        "~1700 nnz/spot", "generate_s": round(gen_s, 1),
+            "one_by_one": seq, "one_by_one_solve_s": sum(q["solve_s"] for q in seq),
+            "stacked": {"nnz": int(st["nnz"]), "create_s": create_s, "solve_s": t, "iterations": info["iterations"],
+                        "row_passes": info["row_passes"], "f": info["f"],
+                        "f_sum_alone": sum(q["f"] for q in seq),
+                        "pass_ms": ms, "pass_gbs": by / ms / 1e6, "frac_of_peak": by / ms / 1e6 / peak,
+                        "ring": {"chunk_entries": st["chunk_entries"], "chunk_rows": st["chunk_rows"],
+                                 "stages": st["stages"], "configs_timed": st["autotuned"]}}}
+
+
 def run_reference(args):
     rank = _env_int("RANK", 0)
     if rank != 0:
@@ -177,6 +227,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-pgd", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the reduced-precision storage forms")
+    ap.add_argument("--batch", action="store_true",
+                    help="also run the batched form: 4 plans x 49 scenarios (~9 GB), one stacked plan vs one by one")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--ref-budget", type=float, default=15.0)
     ap.add_argument("--max-iter", type=int, default=0,
@@ -208,7 +260,7 @@ def main():
     prob = _workload(args.seed, args.workers)
     t_gen = time.perf_counter() - t_gen
     stream = torch.cuda.Stream(device=dev)
-    plan = rpt.Plan.from_problem(prob, device=dev, stream=stream.cuda_stream, row_path=args.row_path)
+    plan = rpt.Plan.from_problem(prob, device=dev, stream=stream.cuda_stream, row_path=args.row_path, autotune=1)
     st = plan.stats()
     params = rpt.admm_params()          # eps_abs = eps_rel = 1e-4, defaults of the library
     if args.max_iter > 0:
@@ -272,7 +324,9 @@ def main():
                    "N": prob.N, "nnz": st["nnz"], "matrix_bytes": st["matrix_bytes"],
                    "eps_abs": params.eps_abs, "eps_rel": params.eps_rel,
                    "rho": infos[-1]["rho"], "l2": "inputs 1.02 GB > 129 MB L2, no flush",
-                   "parallelism": "replicas" if world > 1 else "single GPU", "seed": args.seed},
+                   "parallelism": "replicas" if world > 1 else "single GPU", "seed": args.seed,
+                   "ring": {"chunk_entries": st["chunk_entries"], "chunk_rows": st["chunk_rows"],
+                            "stages": st["stages"], "configs_timed": st["autotuned"]}},
         "admm": {"iterations": iters, "cg_iterations": statistics.mean(i["inner"] for i in infos),
                  "row_passes": passes_per_solve, "f": infos[-1]["f"], "status": infos[-1]["status"],
                  "iterations_per_s": iters / (ms_step / 1e3),
@@ -328,6 +382,9 @@ def main():
             pf.close()
         out["forms"] = forms
 
+    if args.batch:
+        out["batch"] = run_batch(args, rpt, dev, stream, peak)
+
     if not args.no_e2e:
         # end to end through the C ABI with host buffers: upload + solve + result read-back
         h2d = st["matrix_bytes"] + prob.m * 16 + prob.n * 16
@@ -335,7 +392,8 @@ def main():
         for _ in range(max(2, args.steps)):
             torch.cuda.synchronize(dev)
             t0 = time.perf_counter()
-            p2 = rpt.Plan.from_problem(prob, device=dev, stream=stream.cuda_stream, row_path=args.row_path)
+            p2 = rpt.Plan.from_problem(prob, device=dev, stream=stream.cuda_stream, row_path=args.row_path,
+                                       autotune=1)
             x2, i2 = p2.admm_bb_solve(params)
             torch.cuda.synchronize(dev)
             e2e.append(time.perf_counter() - t0)

@@ -87,6 +87,9 @@ typedef struct {
   int32_t row_path;                 /* 1 register-direct loads, 2 bulk-copy (TMA) ring, 3 streaming (warps
                                        claim chunks, entries go straight to registers); 0: RPT_ROW_PATH
                                        from the environment, else 2 when the plan fits it and 1 otherwise */
+  int32_t autotune;                 /* 1: time every ring configuration that fits this plan (entries and
+                                       rows per stage, stages) on its own row pass and keep the fastest;
+                                       0: RPT_AUTOTUNE from the environment, else the first that fits */
 } rpt_device_opts;
 
 /* ADMM-BB parameters (Sec. 2.2).  Fill with rpt_admm_params_default(). */
@@ -148,6 +151,11 @@ typedef struct {
   double  const_term;     /* sum over rows not stored for a scenario of c_s w_i p_i^2 (part of every f) */
   int32_t row_path;       /* row-pass implementation in use: 1 register-direct, 2 bulk-copy ring, 3 streaming */
   int32_t min_lanes;      /* smallest lanes-per-row group */
+  int32_t chunk_entries;  /* ring / streaming: entries per chunk (0 for the register path) */
+  int32_t chunk_rows;     /* ring / streaming: rows per chunk */
+  int32_t stages;         /* ring: stages */
+  int32_t autotuned;      /* ring configurations timed at plan creation (0: none) */
+  double  autotune_ms;    /* the chosen configuration's pass time in that timing */
 } rpt_plan_stats;
 
 /* ---- defaults ----------------------------------------------------------- */

@@ -229,6 +229,13 @@ bool build_chunks(const RowLists& R, const std::vector<int64_t>& base, int N, in
   return true;
 }
 
+// One bulk-copy ring configuration and its chunk lists.
+struct RingCfg {
+  int cmax = 0, rmax = 0, stages = 0;
+  std::vector<ChunkDesc> chunks;
+  std::vector<int> scen_chunk;
+};
+
 int env_int(const char* name, int dflt) {
   const char* v = std::getenv(name);
   if (!v || !*v) return dflt;
@@ -483,6 +490,8 @@ int create_plan(const rpt_problem* pr, const rpt_device_opts* opts, rpt_plan** o
   std::vector<int> scen_chunk;
   bool use_tma = false, use_stream = false;
   int ctas = 0;
+  const bool autotune = (opts && opts->autotune) || env_int("RPT_AUTOTUNE", 0) != 0;
+  std::vector<RingCfg> ring_cfgs;   // ring configurations that fit (all of them when autotuning)
   if (want_path == 3) {
     int smem_optin = 0;
     cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, P->device);
@@ -500,13 +509,37 @@ int create_plan(const rpt_problem* pr, const rpt_device_opts* opts, rpt_plan** o
   } else if (want_path != 1) {
     int smem_optin = 0;
     cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, P->device);
-    dp.cmax = std::max(64, env_int("RPT_TMA_CMAX", 6144)) & ~15;
-    dp.rmax = std::max(8, env_int("RPT_TMA_RMAX", 512));
-    dp.stages = std::min(8, std::max(2, env_int("RPT_TMA_STAGES", 3)));
     ctas = (opts && opts->ctas_per_sm > 0) ? opts->ctas_per_sm : 1;
-    const size_t need = tma_smem_bytes(n_pad, dp.cmax, dp.rmax, dp.stages, bv, bi, true);
-    if (need + 1024 <= (size_t)smem_optin)
-      use_tma = build_chunks(R, base, N, dp.cmax, dp.rmax, false, &chunks, &scen_chunk);
+    // ring configurations {entries per stage, rows per stage, stages}: the
+    // environment's, else the default followed by smaller ones for wide plans
+    // (the spot vector and the accumulator share the shared memory with the ring)
+    std::vector<int3> cands;
+    if (std::getenv("RPT_TMA_CMAX") || std::getenv("RPT_TMA_STAGES") || std::getenv("RPT_TMA_RMAX"))
+      cands.push_back(make_int3(std::max(64, env_int("RPT_TMA_CMAX", 6144)) & ~15,
+                                std::max(8, env_int("RPT_TMA_RMAX", 512)),
+                                std::min(8, std::max(2, env_int("RPT_TMA_STAGES", 3)))));
+    else
+      cands = {make_int3(6144, 512, 3), make_int3(8192, 512, 2), make_int3(4096, 512, 4),
+               make_int3(4096, 512, 3), make_int3(4096, 512, 2), make_int3(3072, 256, 3),
+               make_int3(3072, 256, 2), make_int3(2048, 256, 4), make_int3(2048, 256, 2)};
+    for (const int3& c : cands) {
+      if (tma_smem_bytes(n_pad, c.x, c.y, c.z, bv, bi, true) + 1024 > (size_t)smem_optin) continue;
+      RingCfg rc;
+      rc.cmax = c.x;
+      rc.rmax = c.y;
+      rc.stages = c.z;
+      if (!build_chunks(R, base, N, rc.cmax, rc.rmax, false, &rc.chunks, &rc.scen_chunk)) continue;
+      ring_cfgs.push_back(std::move(rc));
+      if (!autotune) break;   // first that fits
+    }
+    if (!ring_cfgs.empty()) {
+      use_tma = true;
+      dp.cmax = ring_cfgs[0].cmax;
+      dp.rmax = ring_cfgs[0].rmax;
+      dp.stages = ring_cfgs[0].stages;
+      chunks = ring_cfgs[0].chunks;
+      scen_chunk = ring_cfgs[0].scen_chunk;
+    }
     if (!use_tma && want_path == 2) {
       free_plan(P);
       set_error("bulk-copy row path not possible for this plan (shared memory, or a row longer than RPT_TMA_CMAX)");
@@ -584,7 +617,9 @@ int create_plan(const rpt_problem* pr, const rpt_device_opts* opts, rpt_plan** o
   float* d_val32 = A.get<float>(NNZp + kPad);       // replaced by quantised values if requested
   int4* d_rec = A.get<int4>(R.rec.size());
   int* d_recbase = A.get<int>(N + 1);
-  ChunkDesc* d_chunks = dyn ? A.get<ChunkDesc>(chunks.size()) : nullptr;
+  size_t chunk_cap = chunks.size();
+  for (const RingCfg& rc : ring_cfgs) chunk_cap = std::max(chunk_cap, rc.chunks.size());
+  ChunkDesc* d_chunks = dyn ? A.get<ChunkDesc>(chunk_cap) : nullptr;
   int* d_scen_chunk = dyn ? A.get<int>(N + 1) : nullptr;
   int* d_qnext = dyn ? A.get<int>(N) : nullptr;
   unsigned char* d_visited = dyn ? A.get<unsigned char>((size_t)N * dp.grid) : nullptr;
@@ -788,6 +823,53 @@ int create_plan(const rpt_problem* pr, const rpt_device_opts* opts, rpt_plan** o
   S.const_term = const_term;
   S.row_path = dp.path == 2 ? 3 : (dp.path == 1 ? 2 : 1);
   S.min_lanes = g_min_lanes;
+  S.chunk_entries = dp.path >= 1 ? dp.cmax : 0;
+  S.chunk_rows = dp.path >= 1 ? dp.rmax : 0;
+  S.stages = dp.path == 1 ? dp.stages : 0;
+  S.autotuned = 0;
+  S.autotune_ms = 0.0;
+  // ---- autotuning: time every fitting ring configuration on this plan, keep the fastest ----
+  if (use_tma && ring_cfgs.size() > 1) {
+    std::vector<double> ms(ring_cfgs.size(), 1e30);
+    auto apply = [&](const RingCfg& rc) -> cudaError_t {
+      cudaError_t ee = cudaMemcpyAsync(d_chunks, rc.chunks.data(), rc.chunks.size() * sizeof(ChunkDesc),
+                                       cudaMemcpyHostToDevice, st);
+      if (ee == cudaSuccess)
+        ee = cudaMemcpyAsync(d_scen_chunk, rc.scen_chunk.data(), (N + 1) * sizeof(int), cudaMemcpyHostToDevice, st);
+      if (ee == cudaSuccess) ee = cudaStreamSynchronize(st);
+      P->dp.cmax = rc.cmax;
+      P->dp.rmax = rc.rmax;
+      P->dp.stages = rc.stages;
+      if (ee == cudaSuccess) ee = rowpass_prepare(P->dp);
+      return ee;
+    };
+    if ((e = cudaMemsetAsync(P->v32, 0, sizeof(float) * (size_t)N * n_pad, st))) {
+      free_plan(P);
+      return cuda_fail(e, "autotune");
+    }
+    for (size_t c = 0; c < ring_cfgs.size(); ++c) {
+      if ((e = apply(ring_cfgs[c]))) {
+        free_plan(P);
+        return cuda_fail(e, "autotune");
+      }
+      double t = 0.0, by = 0.0;
+      if (int rc = profile_row_pass(P, kNormal, 3, &t, &by)) {
+        free_plan(P);
+        return rc;
+      }
+      ms[c] = t;
+    }
+    const size_t best = (size_t)(std::min_element(ms.begin(), ms.end()) - ms.begin());
+    if ((e = apply(ring_cfgs[best]))) {
+      free_plan(P);
+      return cuda_fail(e, "autotune");
+    }
+    S.chunk_entries = ring_cfgs[best].cmax;
+    S.chunk_rows = ring_cfgs[best].rmax;
+    S.stages = ring_cfgs[best].stages;
+    S.autotuned = (int32_t)ring_cfgs.size();
+    S.autotune_ms = ms[best];
+  }
   *out = reinterpret_cast<rpt_plan*>(P);
   return RPT_OK;
 }

@@ -53,7 +53,7 @@ class _Problem(C.Structure):
 
 class _DeviceOpts(C.Structure):
     _fields_ = [("device", C.c_int32), ("stream", C.c_void_p), ("ctas_per_sm", C.c_int32),
-                ("row_path", C.c_int32)]
+                ("row_path", C.c_int32), ("autotune", C.c_int32)]
 
 
 class AdmmParams(C.Structure):
@@ -86,7 +86,9 @@ class _Stats(C.Structure):
                 ("nnz", C.c_int64), ("matrix_bytes", C.c_int64), ("value_format", C.c_int32),
                 ("index_width", C.c_int32), ("row_blocks", C.c_int32), ("sm_count", C.c_int32),
                 ("default_rho", C.c_double), ("const_term", C.c_double),
-                ("row_path", C.c_int32), ("min_lanes", C.c_int32)]
+                ("row_path", C.c_int32), ("min_lanes", C.c_int32), ("chunk_entries", C.c_int32),
+                ("chunk_rows", C.c_int32), ("stages", C.c_int32), ("autotuned", C.c_int32),
+                ("autotune_ms", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -201,7 +203,7 @@ class Plan:
 
     def __init__(self, m, n, N, row_ptr, col_idx, val, voxel_w, presc, scen_weight=None,
                  lb=None, ub=None, value_format=F32, index_width=32, device=0, stream=None,
-                 ctas_per_sm=0, row_path=0):
+                 ctas_per_sm=0, row_path=0, autotune=0):
         L = lib()
         rp = [np.ascontiguousarray(a, dtype=np.int32) for a in row_ptr]
         ci = [np.ascontiguousarray(a, dtype=np.int32) for a in col_idx]
@@ -216,7 +218,7 @@ class Plan:
         VA = (C.POINTER(C.c_float) * N)(*[a.ctypes.data_as(C.POINTER(C.c_float)) for a in va])
         pr = _Problem(m, n, N, RP, CI, VA, _dptr(w), _dptr(p), _dptr(sw), _dptr(lbv), _dptr(ubv),
                       value_format, index_width)
-        opts = _DeviceOpts(device, stream, ctas_per_sm, row_path)
+        opts = _DeviceOpts(device, stream, ctas_per_sm, row_path, autotune)
         h = C.c_void_p()
         _check(L.rpt_plan_create(C.byref(pr), C.byref(opts), C.byref(h)))
         self._h = h

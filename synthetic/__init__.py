@@ -14,6 +14,8 @@ from .phantom import (  # noqa: F401
     scenario_set_13,
     scenario_set_49,
     reweighted,
+    block_diagonal,
+    config_batch,
     sample_weights,
     N_WEIGHT_SLOTS,
 )

@@ -465,21 +465,25 @@ def _beam_spots_for_target(body, target, ang, spacing, n_spots, margin, rng):
 
 def config_realistic(seed: int = 0, n_spots: int = 5000, nnz_per_col: float = 2000.0,
                      scenarios=None, workers: int = 8, grid=(128, 128, 96), h: float = 2.5,
-                     beams_deg=(0.0, 120.0, 240.0)) -> Problem:
+                     beams_deg=(0.0, 120.0, 240.0), scale: float = 1.0) -> Problem:
     """128x128x96 grid at 2.5 mm; body ellipsoid of ~300k voxels; ellipsoidal
     target (70 Gy, w 100) and three OAR ellipsoids (0 Gy, w 10); body (0 Gy,
     w 1); n_spots from 3 beams on a 5 mm lateral grid; 13 scenarios; the
     truncation factor is tuned on the nominal scenario to nnz_per_col entries
-    per spot column; bounds [0, 10].
+    per spot column; bounds [0, 10].  `scale` multiplies every length of the
+    geometry and the grid extent (voxel size fixed): about 300k * scale^3 voxels.
     """
     rng = np.random.default_rng(seed)
+    if scale != 1.0:
+        grid = tuple(max(8, int(round(g * scale))) for g in grid)
     Pall = _grid_centers(grid, h)
-    body = _Ellipsoid([0.0, 0.0, 0.0], [90.0, 105.0, 118.0])
-    target = _Ellipsoid([10.0, 5.0, 0.0], [30.0, 28.0, 32.0])
+    sc = float(scale)
+    body = _Ellipsoid([0.0, 0.0, 0.0], [90.0 * sc, 105.0 * sc, 118.0 * sc])
+    target = _Ellipsoid([10.0 * sc, 5.0 * sc, 0.0], [30.0 * sc, 28.0 * sc, 32.0 * sc])
     oars = [
-        _Ellipsoid([-42.0, 0.0, 10.0], [12.0, 15.0, 20.0]),
-        _Ellipsoid([35.0, 45.0, -10.0], [10.0, 12.0, 15.0]),
-        _Ellipsoid([0.0, -55.0, 0.0], [8.0, 8.0, 60.0]),
+        _Ellipsoid([-42.0 * sc, 0.0, 10.0 * sc], [12.0 * sc, 15.0 * sc, 20.0 * sc]),
+        _Ellipsoid([35.0 * sc, 45.0 * sc, -10.0 * sc], [10.0 * sc, 12.0 * sc, 15.0 * sc]),
+        _Ellipsoid([0.0, -55.0 * sc, 0.0], [8.0 * sc, 8.0 * sc, 60.0 * sc]),
     ]
     lab_all = _label_voxels(Pall, body, target, oars)
     keep = lab_all >= 0
@@ -603,3 +607,61 @@ def sample_weights(rng, labels, w_range=(0.1, 100.0), d_range=(60.0, 75.0)):
         if 0 <= k < N_WEIGHT_SLOTS:
             sw[k] = 10.0 ** rng.uniform(lo, hi)
     return sw, float(rng.uniform(*d_range))
+
+
+# ---------------------------------------------------------------------------
+# several plans at once (the batched form)
+# ---------------------------------------------------------------------------
+def block_diagonal(problems) -> Problem:
+    """Several independent problems with the same number of scenarios as one:
+    rows (voxels) and columns (spots) are stacked, scenario s of the result is
+    blockdiag(A_s of each problem).  The objective is the sum of the problems'
+    objectives and the box is the product of their boxes, so the optimum is
+    the problems' optima side by side.  meta["blocks"] = [(row0, m, col0, n)]."""
+    N = problems[0].N
+    assert all(p.N == N for p in problems)
+    rps, cis, vas = [], [], []
+    for s in range(N):
+        rp_parts, ci_parts, va_parts = [], [], []
+        nnz0, col0 = 0, 0
+        for p in problems:
+            rp = np.asarray(p.row_ptr[s], dtype=np.int64)
+            rp_parts.append(rp[:-1] + nnz0)
+            ci_parts.append(np.asarray(p.col_idx[s], dtype=np.int64) + col0)
+            va_parts.append(np.asarray(p.val[s], dtype=np.float32))
+            nnz0 += int(rp[-1])
+            col0 += p.n
+        rp_all = np.concatenate(rp_parts + [np.array([nnz0], dtype=np.int64)])
+        assert nnz0 < 2 ** 31
+        rps.append(rp_all.astype(np.int32))
+        cis.append(np.concatenate(ci_parts).astype(np.int32))
+        vas.append(np.concatenate(va_parts))
+    blocks, r0, c0 = [], 0, 0
+    for p in problems:
+        blocks.append((r0, p.m, c0, p.n))
+        r0 += p.m
+        c0 += p.n
+    sw = problems[0].scen_weight
+    labels = None if any(p.labels is None for p in problems) else np.concatenate([p.labels for p in problems])
+    return Problem(
+        m=r0, n=c0, N=N, row_ptr=rps, col_idx=cis, val=vas,
+        voxel_w=np.concatenate([p.voxel_w for p in problems]),
+        presc=np.concatenate([p.presc for p in problems]), scen_weight=sw,
+        lb=np.concatenate([p.lb for p in problems]), ub=np.concatenate([p.ub for p in problems]),
+        labels=labels, meta=dict(name=f"{len(problems)} plans block-diagonal", blocks=blocks))
+
+
+BATCH_SIZES = ((100_000, 2000), (170_000, 3000), (230_000, 4000), (300_000, 5000))
+
+
+def config_batch(seed: int = 0, workers: int = 8, nnz_per_col: float = 1700.0, scenarios=None,
+                 sizes=BATCH_SIZES):
+    """Four plans of uneven size (voxels, spots) = 100k/2k, 170k/3k, 230k/4k,
+    300k/5k, each over the 49-scenario set, realistic geometry scaled to the
+    voxel count, about nnz_per_col entries per spot column.  Returns the list."""
+    scen = scenarios if scenarios is not None else scenario_set_49()
+    out = []
+    for k, (m, n) in enumerate(sizes):
+        out.append(config_realistic(seed + 101 * k, n_spots=n, nnz_per_col=nnz_per_col, scenarios=scen,
+                                    workers=workers, scale=(m / 299_088.0) ** (1.0 / 3.0)))
+    return out
