@@ -34,6 +34,6 @@ Readings where the paper is silent or garbled (each one is a parameter):
 from .problem import Weighted, default_rho, lipschitz  # noqa: F401
 from .admm_bb import admm_bb  # noqa: F401
 from .pgd import pgd  # noqa: F401
-from .exact import kkt_bruteforce, lsq_box, certificates  # noqa: F401
+from .exact import kkt_bruteforce, lsq_box, box_qp_newton, normal_equations, certificates  # noqa: F401
 from .boyd import consensus_admm_scaled  # noqa: F401
 from .quantize import quantised_problem, quantise_values, bf16_round, e4m3_round  # noqa: F401

@@ -2,9 +2,8 @@
 
 Workload: synthetic.config_realistic(seed=0) (128x128x96 grid, ~299k voxels,
 5000 spots, 13 scenarios).  Records
-  * the exact box-constrained optimum f* of the plan (oracle.exact.lsq_box,
-    trust-region reflective least squares on the stacked weighted system) with
-    its optimality certificates;
+  * the exact box-constrained optimum f* of the plan (oracle.exact.box_qp_newton
+    on the dense normal equations) with its optimality certificates;
   * ADMM-BB with CG subproblems and the library's default parameters
     (rho = default rule, eps = 1e-4, theta 0.3, eta0 1e-2, floor 1e-6, at most
     50 steps, Jacobi): iterations and CG steps to tolerance and the objective,
@@ -28,7 +27,7 @@ sys.path.insert(0, ROOT)
 
 def main():
     from synthetic import config_realistic
-    from oracle import Weighted, admm_bb, default_rho, certificates, lsq_box
+    from oracle import Weighted, admm_bb, default_rho, certificates, box_qp_newton
     out_path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "realistic_seed0_oracle.json")
     t0 = time.time()
     prob = config_realistic(0, workers=8)
@@ -44,9 +43,10 @@ def main():
         json.dump(res, open(out_path, "w"), indent=1)
 
     t1 = time.time()
-    xs = lsq_box(W)
+    xs = box_qp_newton(W)
     c = certificates(W, xs)
-    res["exact"] = dict(method="lsq_box trf", f=W.f(xs), pg=c["pg"], kkt=c["kkt"], seconds=time.time() - t1)
+    res["exact"] = dict(method="box_qp_newton", f=W.f(xs), pg=c["pg"], kkt=c["kkt"], seconds=time.time() - t1,
+                        at_lb=int((xs <= W.lb).sum()), at_ub=int((xs >= W.ub).sum()))
     res["f_star"] = W.f(xs)
     save()
     rc = admm_bb(W, rho=rho0, eps_abs=1e-4, eps_rel=1e-4, max_iter=20000, subproblem="cg",

@@ -258,3 +258,20 @@ def test_pgd_monotone_and_armijo_holds():
     t = r1["history"][0]["step"] if r1["history"] else None
     r1 = pgd(W, max_iter=1, tol_rel_df=0.0, record=True)
     assert r1["history"][0]["step"] >= 0.5 / L
+
+
+@pytest.mark.parametrize("seed,ub", [(41, 3.0), (42, 3.0), (60, 20.0), (61, 100.0)])
+def test_projected_newton_matches_bruteforce_and_library_bvls(seed, ub):
+    """box_qp_newton (used for the full-size optimum) against KKT enumeration
+    (n = 8) and against the library's BVLS on a case with free variables and
+    both kinds of active bounds."""
+    from oracle import box_qp_newton
+    small = random_problem(seed, m=300, n=8, N=2, mean_row=4.0, ub=ub)
+    Ws = Weighted(small)
+    a, b = kkt_bruteforce(Ws), box_qp_newton(Ws)
+    assert abs(Ws.f(a) - Ws.f(b)) <= 1e-12 * Ws.f(a) and np.abs(a - b).max() <= 1e-9
+    prob = random_problem(seed, m=2000, n=120, N=3, mean_row=10.0, ub=ub)
+    W = Weighted(prob)
+    a, b = lsq_box(W), box_qp_newton(W)
+    assert abs(W.f(a) - W.f(b)) <= 1e-12 * W.f(a) and np.abs(a - b).max() <= 1e-8
+    assert certificates(W, b)["pg"] <= 1e-12
