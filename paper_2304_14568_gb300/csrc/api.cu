@@ -229,6 +229,59 @@ bool build_chunks(const RowLists& R, const std::vector<int64_t>& base, int N, in
   return true;
 }
 
+// Reorder a row's entries (the order is free: a pass sums over them) so that
+// every aligned group of G consecutive entries, the entries that the G lanes of
+// the row touch in one instruction, falls in as many distinct shared-memory banks
+// (spot column mod 32) as the row allows: each group takes one entry from each of
+// the banks with the most entries left, largest first.  The gather from v_s and
+// the scatter into the accumulator then conflict less.
+struct BankScratch {
+  std::vector<int> order, idx;
+  std::vector<int32_t> c;
+  std::vector<float> v;
+};
+
+void bank_balance(int32_t* col, float* val, int len, int G, BankScratch& S) {
+  if (len <= 1) return;
+  int cnt[32] = {0}, start[33], cur[32];
+  for (int i = 0; i < len; ++i) ++cnt[col[i] & 31];
+  start[0] = 0;
+  for (int b = 0; b < 32; ++b) start[b + 1] = start[b] + cnt[b];
+  S.idx.resize(len);
+  for (int b = 0; b < 32; ++b) cur[b] = start[b];
+  for (int i = 0; i < len; ++i) S.idx[cur[col[i] & 31]++] = i;   // entries by bank, stable
+  for (int b = 0; b < 32; ++b) cur[b] = start[b];
+  S.order.clear();
+  int banks[32];
+  while ((int)S.order.size() < len) {
+    // banks by entries left, largest first
+    int nb = 0;
+    for (int b = 0; b < 32; ++b)
+      if (cur[b] < start[b + 1]) banks[nb++] = b;
+    std::sort(banks, banks + nb, [&](int x, int y) {
+      const int rx = start[x + 1] - cur[x], ry = start[y + 1] - cur[y];
+      return rx != ry ? rx > ry : x < y;
+    });
+    const int want = std::min(G, len - (int)S.order.size());
+    int taken = 0;
+    for (int k = 0; k < nb && taken < want; ++k, ++taken) S.order.push_back(S.idx[cur[banks[k]]++]);
+    // fewer non-empty banks than lanes: fill the group from the largest banks again
+    for (int k = 0; taken < want; k = (k + 1) % nb) {
+      const int b = banks[k];
+      if (cur[b] < start[b + 1]) {
+        S.order.push_back(S.idx[cur[b]++]);
+        ++taken;
+      }
+    }
+  }
+  S.c.assign(col, col + len);
+  S.v.assign(val, val + len);
+  for (int i = 0; i < len; ++i) {
+    col[i] = S.c[S.order[i]];
+    val[i] = S.v[S.order[i]];
+  }
+}
+
 // One bulk-copy ring configuration and its chunk lists.
 struct RingCfg {
   int cmax = 0, rmax = 0, stages = 0;
@@ -436,6 +489,7 @@ int create_plan(const rpt_problem* pr, const rpt_device_opts* opts, rpt_plan** o
       int32_t pos = 0;
       std::vector<int32_t> lc;
       std::vector<float> lv;
+      BankScratch bb;
       for (int q = 0; q < R.nrows[s]; ++q) {
         const int k = order[s][q];
         const int32_t a = rp[kept[k]], len = rp[kept[k] + 1] - a;
@@ -448,14 +502,15 @@ int create_plan(const rpt_problem* pr, const rpt_device_opts* opts, rpt_plan** o
         r4.w = k;
         out[q] = r4;
         const int32_t plen = (len + 3) & ~3;
+        lc.assign(plen, 0);
+        lv.assign(plen, 0.f);
+        std::memcpy(lc.data(), pr->col_idx[s] + a, sizeof(int32_t) * len);
+        std::memcpy(lv.data(), pr->val[s] + a, sizeof(float) * len);
+        bank_balance(lc.data(), lv.data(), len, interleave ? stream_lanes(plen) : lanes_for(plen), bb);
         if (!interleave) {
-          std::memcpy(&col_h[base[s] + pos], pr->col_idx[s] + a, sizeof(int32_t) * len);
-          std::memcpy(&val_h[base[s] + pos], pr->val[s] + a, sizeof(float) * len);
+          std::memcpy(&col_h[base[s] + pos], lc.data(), sizeof(int32_t) * plen);
+          std::memcpy(&val_h[base[s] + pos], lv.data(), sizeof(float) * plen);
         } else {
-          lc.assign(plen, 0);
-          lv.assign(plen, 0.f);
-          std::memcpy(lc.data(), pr->col_idx[s] + a, sizeof(int32_t) * len);
-          std::memcpy(lv.data(), pr->val[s] + a, sizeof(float) * len);
           const int G = stream_lanes(plen), nq = plen / 4;
           for (int b = 0; b * G < nq; ++b) {
             const int gb = std::min(G, nq - b * G);
@@ -843,9 +898,13 @@ int create_plan(const rpt_problem* pr, const rpt_device_opts* opts, rpt_plan** o
       if (ee == cudaSuccess) ee = rowpass_prepare(P->dp);
       return ee;
     };
-    if ((e = cudaMemsetAsync(P->v32, 0, sizeof(float) * (size_t)N * n_pad, st))) {
-      free_plan(P);
-      return cuda_fail(e, "autotune");
+    // time on a nonzero vector (a zero vector makes every scatter add zeros)
+    {
+      std::vector<float> ones((size_t)N * n_pad, 1.0f);
+      if ((e = cudaMemcpy(P->v32, ones.data(), sizeof(float) * ones.size(), cudaMemcpyHostToDevice))) {
+        free_plan(P);
+        return cuda_fail(e, "autotune");
+      }
     }
     for (size_t c = 0; c < ring_cfgs.size(); ++c) {
       if ((e = apply(ring_cfgs[c]))) {
