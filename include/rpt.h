@@ -111,7 +111,15 @@ typedef struct {
   int32_t check_every;    /* host-driven loop: read the convergence flag every k iterations (default 1) */
   int32_t resume;         /* 1: start from the plan's stored state (rpt_state_set / previous solve) */
   int32_t cg_precond;     /* 0: plain CG; 1: Jacobi-preconditioned CG, M = diag(B_s) (default 1) */
+  int32_t subproblem;     /* x-update (App. A): RPT_SUB_CG (default) conjugate gradients on the sparse
+                             operator; RPT_SUB_CHOL the cached factor: B_s = A~_s^T A~_s + (rho/2) I
+                             formed, factored and inverted once per (plan, rho) in FP32 on the device,
+                             then x_s = B_s^{-1} c_s each iteration (4 n^2 N bytes of device memory,
+                             plus as much again while it is formed) */
 } rpt_admm_params;
+
+#define RPT_SUB_CG   0
+#define RPT_SUB_CHOL 1
 
 /* PGD parameters (Sec. 2.1, Eq. 3 read as sufficient decrease). */
 typedef struct {
@@ -137,6 +145,7 @@ typedef struct {
   double  r_prim, r_dual, eps_prim, eps_dual;   /* Eq. 9 at the last iteration (ADMM) */
   double  step;           /* last dual step (ADMM) or accepted step (PGD) */
   double  rho;            /* penalty used (ADMM) or Lipschitz estimate L (PGD) */
+  double  setup_seconds;  /* RPT_SUB_CHOL: forming and inverting B_s in this call (0 if cached) */
 } rpt_solve_info;
 
 typedef struct {

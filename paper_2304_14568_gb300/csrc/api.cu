@@ -685,6 +685,7 @@ int create_plan(const rpt_problem* pr, const rpt_device_opts* opts, rpt_plan** o
   P->err = A.get<int>(1);
   P->diag = A.get<float>(diag_h.size());
   int4* d_blocks = dyn ? nullptr : A.get<int4>(blocks.size());
+  P->rec_of = A.get<int>((size_t)N * m_act);
   P->lb = A.get<double>(n);
   P->ub = A.get<double>(n);
   const size_t Nn = (size_t)N * n;
@@ -747,6 +748,10 @@ int create_plan(const rpt_problem* pr, const rpt_device_opts* opts, rpt_plan** o
   RPT_CP(d_val32, val_h.data(), (size_t)NNZp * sizeof(float));
   RPT_CP(d_rec, R.rec.data(), R.rec.size() * sizeof(int4));
   RPT_CP(d_recbase, R.rec_base.data(), (N + 1) * sizeof(int));
+  std::vector<int> rec_of((size_t)N * m_act, -1);
+  for (int s = 0; s < N; ++s)
+    for (int q = 0; q < R.nrows[s]; ++q) rec_of[(size_t)s * m_act + R.rec[R.rec_base[s] + q].w] = q;
+  RPT_CP(P->rec_of, rec_of.data(), rec_of.size() * sizeof(int));
   if (!dyn) RPT_CP(d_blocks, blocks.data(), blocks.size() * sizeof(int4));
   RPT_CP(P->diag, diag_h.data(), diag_h.size() * sizeof(float));
   if (dyn) {
@@ -986,6 +991,7 @@ void rpt_admm_params_default(rpt_admm_params* p) {
   p->check_every = 1;
   p->resume = 0;
   p->cg_precond = 1;
+  p->subproblem = RPT_SUB_CG;
 }
 
 void rpt_pgd_params_default(rpt_pgd_params* p) {

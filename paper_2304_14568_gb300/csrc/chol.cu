@@ -1,0 +1,330 @@
+// Cached-factor x-update (App. A; the subproblem solver of the paper): for a
+// fixed rho,
+//     B_s = A~_s^T A~_s + (rho/2) I
+// is formed once per (plan, rho), factored (Cholesky, B_s = L L^T) and inverted
+// (B_s^{-1} = L^{-T} L^{-1}); every ADMM iteration then takes
+//     x_s = B_s^{-1} c_s,   c_s = A~_s^T p~ + (rho/2) z - y_s / 2
+// as one dense matrix-vector product per scenario, without a pass over the
+// sparse matrices.  The paper factors in double precision on the CPU; here the
+// factor, its inverse and the products are FP32 on the device (the solver state
+// stays FP64), which bounds the relative error of an x-update by about
+// cond(B_s) * n * eps32.
+//
+// Forming B_s uses the sparsity: rows are taken kRB at a time in voxel order
+// (neighbouring voxels share most of their spots), their union of columns U is
+// built in shared memory with the dense kRB x |U| block of A~, and every nonzero
+// pair sum over the block goes to the lower triangle of B_s with one global
+// atomic.  Factorisation and inversion are blocked (64) right-looking
+// algorithms: small diagonal-block kernels plus the FP32 GEMM of gemm.cuh for
+// the trailing updates, batched over scenarios.
+#include <cmath>
+#include <vector>
+
+#include "gemm.cuh"
+#include "plan.h"
+#include "rowcommon.cuh"
+
+namespace rpt {
+namespace {
+
+constexpr int kRB = 16;       // rows per outer-product block
+constexpr int kUMax = 1536;   // columns a block may touch (more: the per-row path)
+constexpr int kNB = 64;       // Cholesky / inverse block size
+constexpr unsigned kFull = 0xffffffffu;
+
+// Lower triangle of B_s (row-major n x n, zero on entry) += sum over kept rows k
+// in [blockIdx.x * kRB, +kRB) of c_s w_k a_k a_k^T (A~ = diag(sqrt(c_s w)) A).
+template <typename VT, typename IT>
+__global__ void __launch_bounds__(256)
+k_btb(DevPlan P, int s, const int* __restrict__ rec_of, float* __restrict__ B) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  int* map = reinterpret_cast<int*>(smem);            // [n_pad]: flag, then position in U (-1: absent)
+  int* U = map + P.n_pad;                             // [kUMax] sorted union of columns
+  float* D = reinterpret_cast<float*>(U + kUMax);     // [kRB][kUMax] dense block of A~
+  __shared__ int rlo[kRB], rhi[kRB];
+  __shared__ float rw[kRB];
+  __shared__ int wsum[8];
+  __shared__ int running;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int n = P.n;
+  const int4* rec = P.rowrec + P.rec_base[s];
+  const long long base = P.nnz_base[s];
+  const VT* val = vals<VT>(P) + base;
+  const IT* col = cols<IT>(P) + base;
+  const float* cs = P.colscale ? P.colscale + (size_t)s * P.n_pad : nullptr;
+  if (tid < kRB) {
+    const int k = blockIdx.x * kRB + tid;
+    const int q = k < P.m_act ? rec_of[(size_t)s * P.m_act + k] : -1;
+    rlo[tid] = q >= 0 ? rec[q].x : 0;
+    rhi[tid] = q >= 0 ? rec[q + 1].x : 0;
+    rw[tid] = q >= 0 ? sqrtf(__int_as_float(rec[q].y)) : 0.f;
+  }
+  if (tid == 0) running = 0;
+  for (int j = tid; j < P.n_pad; j += blockDim.x) map[j] = 0;
+  __syncthreads();
+  for (int r = 0; r < kRB; ++r)
+    for (int e = rlo[r] + tid; e < rhi[r]; e += blockDim.x)
+      if (to_f<VT>(val[e]) != 0.f) map[(int)col[e]] = 1;
+  __syncthreads();
+  // ordered compaction of the flags: map[c] = position in U, U[position] = c
+  for (int c0 = 0; c0 < P.n_pad; c0 += blockDim.x) {
+    const int c = c0 + tid;
+    const int f = c < P.n_pad ? map[c] : 0;
+    const unsigned bal = __ballot_sync(kFull, f != 0);
+    if (lane == 0) wsum[w] = __popc(bal);
+    __syncthreads();
+    int off = running;
+    for (int i = 0; i < w; ++i) off += wsum[i];
+    if (c < P.n_pad) {
+      const int pos = off + __popc(bal & ((1u << lane) - 1u));
+      map[c] = f ? pos : -1;
+      if (f && pos < kUMax) U[pos] = c;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      int t = running;
+      for (int i = 0; i < 8; ++i) t += wsum[i];
+      running = t;
+    }
+    __syncthreads();
+  }
+  const int nu = running;
+  if (nu > kUMax) {
+    // rare: rows too spread out for one dense block; add each row's pairs directly
+    for (int r = 0; r < kRB; ++r) {
+      const int lo = rlo[r], len = rhi[r] - rlo[r];
+      const long long pairs = (long long)len * len;
+      for (long long p = tid; p < pairs; p += blockDim.x) {
+        const int e1 = lo + (int)(p / len), e2 = lo + (int)(p % len);
+        const int c1 = (int)col[e1], c2 = (int)col[e2];
+        if (c1 < c2) continue;
+        float a1 = to_f<VT>(val[e1]), a2 = to_f<VT>(val[e2]);
+        if (cs) {
+          a1 *= cs[c1];
+          a2 *= cs[c2];
+        }
+        const float v = rw[r] * rw[r] * a1 * a2;
+        if (v != 0.f) atomicAdd(&B[(size_t)c1 * n + c2], v);
+      }
+    }
+    return;
+  }
+  for (int e = tid; e < kRB * nu; e += blockDim.x) D[(e / nu) * kUMax + (e % nu)] = 0.f;
+  __syncthreads();
+  for (int r = 0; r < kRB; ++r)
+    for (int e = rlo[r] + tid; e < rhi[r]; e += blockDim.x) {
+      const int c = (int)col[e];
+      float a = to_f<VT>(val[e]);
+      if (a != 0.f) {
+        if (cs) a *= cs[c];
+        D[r * kUMax + map[c]] = rw[r] * a;
+      }
+    }
+  __syncthreads();
+  // pairs a >= b of U (row U[a] >= column U[b]: the lower triangle)
+  const long long npairs = (long long)nu * (nu + 1) / 2;
+  for (long long p = tid; p < npairs; p += blockDim.x) {
+    int a = (int)((sqrt(8.0 * (double)p + 1.0) - 1.0) * 0.5);
+    while ((long long)a * (a + 1) / 2 > p) --a;
+    while ((long long)(a + 1) * (a + 2) / 2 <= p) ++a;
+    const int b = (int)(p - (long long)a * (a + 1) / 2);
+    float sum = 0.f;
+#pragma unroll
+    for (int r = 0; r < kRB; ++r) sum = fmaf(D[r * kUMax + a], D[r * kUMax + b], sum);
+    if (sum != 0.f) atomicAdd(&B[(size_t)U[a] * n + U[b]], sum);
+  }
+}
+
+// B_s[j][j] += half_rho for every scenario (grid.y = scenario).
+__global__ void k_add_diag(float* B, int n, float half_rho) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < n) B[(size_t)blockIdx.y * n * n + (size_t)j * n + j] += half_rho;
+}
+
+// Y_s = I (all scenarios; Y zero on entry).
+__global__ void k_set_identity(float* Y, int n) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < n) Y[(size_t)blockIdx.y * n * n + (size_t)j * n + j] = 1.f;
+}
+
+// Cholesky of the diagonal block kb of every scenario (grid.x = scenario), in place
+// (lower).  A pivot <= 0 sets *err and is replaced by 1 so that the factorisation ends.
+__global__ void __launch_bounds__(256) k_potrf_diag(float* B, int n, int kb, int* err) {
+  __shared__ float a[kNB][kNB + 1];
+  float* Bs = B + (size_t)blockIdx.x * n * n;
+  const int r0 = kb * kNB, nb = min(kNB, n - r0);
+  for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
+    const int i = e / nb, k = e % nb;
+    a[i][k] = Bs[(size_t)(r0 + i) * n + r0 + k];
+  }
+  __syncthreads();
+  for (int j = 0; j < nb; ++j) {
+    if (threadIdx.x == 0) {
+      float d = a[j][j];
+      if (!(d > 0.f)) {
+        atomicExch(err, 1);
+        d = 1.f;
+      }
+      a[j][j] = sqrtf(d);
+    }
+    __syncthreads();
+    const float ljj = a[j][j];
+    for (int i = j + 1 + threadIdx.x; i < nb; i += blockDim.x) a[i][j] /= ljj;
+    __syncthreads();
+    const int m = nb - j - 1;
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+      const int i = j + 1 + e / m, k = j + 1 + e % m;
+      if (k <= i) a[i][k] -= a[i][j] * a[k][j];
+    }
+    __syncthreads();
+  }
+  for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
+    const int i = e / nb, k = e % nb;
+    if (k <= i) Bs[(size_t)(r0 + i) * n + r0 + k] = a[i][k];
+  }
+}
+
+// Panel below diagonal block kb: each row x solves x L_kk^T = a (grid (row blocks,
+// scenario), one row per thread).
+__global__ void __launch_bounds__(64) k_trsm_panel(float* B, int n, int kb) {
+  __shared__ float L[kNB][kNB + 1];
+  __shared__ float x[64][kNB + 1];
+  float* Bs = B + (size_t)blockIdx.y * n * n;
+  const int r0 = kb * kNB, nb = min(kNB, n - r0);
+  for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
+    const int i = e / nb, k = e % nb;
+    L[i][k] = Bs[(size_t)(r0 + i) * n + r0 + k];
+  }
+  const int i = r0 + nb + blockIdx.x * 64 + threadIdx.x;
+  if (i < n)
+    for (int k = 0; k < nb; ++k) x[threadIdx.x][k] = Bs[(size_t)i * n + r0 + k];
+  __syncthreads();
+  if (i >= n) return;
+  for (int j = 0; j < nb; ++j) {
+    float t = x[threadIdx.x][j];
+    for (int k = 0; k < j; ++k) t -= x[threadIdx.x][k] * L[j][k];
+    x[threadIdx.x][j] = t / L[j][j];
+  }
+  for (int k = 0; k < nb; ++k) Bs[(size_t)i * n + r0 + k] = x[threadIdx.x][k];
+}
+
+// Rows of block kb of Y: Y[R, 0:cols] = L_kk^{-1} Y[R, 0:cols] (forward
+// substitution down the block's rows; one column per thread; grid (column blocks,
+// scenario)).
+__global__ void __launch_bounds__(64) k_trsm_left(const float* L, float* Y, int n, int kb, int cols) {
+  __shared__ float Lk[kNB][kNB + 1];
+  __shared__ float y[kNB][64 + 1];
+  const float* Ls = L + (size_t)blockIdx.y * n * n;
+  float* Ys = Y + (size_t)blockIdx.y * n * n;
+  const int r0 = kb * kNB, nb = min(kNB, n - r0);
+  for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
+    const int i = e / nb, k = e % nb;
+    Lk[i][k] = Ls[(size_t)(r0 + i) * n + r0 + k];
+  }
+  const int c = blockIdx.x * 64 + threadIdx.x;
+  if (c < cols)
+    for (int j = 0; j < nb; ++j) y[j][threadIdx.x] = Ys[(size_t)(r0 + j) * n + c];
+  __syncthreads();
+  if (c >= cols) return;
+  for (int j = 0; j < nb; ++j) {
+    float t = y[j][threadIdx.x];
+    for (int k = 0; k < j; ++k) t -= Lk[j][k] * y[k][threadIdx.x];
+    y[j][threadIdx.x] = t / Lk[j][j];
+  }
+  for (int j = 0; j < nb; ++j) Ys[(size_t)(r0 + j) * n + c] = y[j][threadIdx.x];
+}
+
+}  // namespace
+
+// Form, factor and invert B_s for every scenario into P->binv (allocating it on
+// first use); also A~_s^T p~ into P->bchol (compute_bconst, solver.cu).
+int chol_prepare(Plan* P, double rho) {
+  if (P->chol_ready && P->chol_rho == rho) return RPT_OK;
+  const DevPlan& dp = P->dp;
+  const int n = dp.n, N = dp.N;
+  const size_t nn = (size_t)n * n;
+  cudaStream_t st = P->stream;
+  cudaError_t e;
+  if (!P->binv) {
+    if ((e = cudaMalloc(&P->binv, sizeof(float) * nn * N))) return cuda_fail(e, "allocate the factor");
+    P->allocs.push_back(P->binv);
+  }
+  if (!P->bchol) {
+    if ((e = cudaMalloc(&P->bchol, sizeof(double) * (size_t)n * N))) return cuda_fail(e, "allocate A~'p~");
+    P->allocs.push_back(P->bchol);
+  }
+  float* Y = nullptr;
+  if ((e = cudaMalloc(&Y, sizeof(float) * nn * N))) return cuda_fail(e, "allocate the inverse workspace");
+  auto done = [&](int rc) {
+    cudaStreamSynchronize(st);
+    cudaFree(Y);
+    return rc;
+  };
+  if ((e = cudaMemsetAsync(P->binv, 0, sizeof(float) * nn * N, st))) return done(cuda_fail(e, "memset"));
+  if ((e = cudaMemsetAsync(Y, 0, sizeof(float) * nn * N, st))) return done(cuda_fail(e, "memset"));
+  if ((e = cudaMemsetAsync(P->err, 0, sizeof(int), st))) return done(cuda_fail(e, "memset"));
+  // 1. B_s = A~_s^T A~_s (lower), + (rho/2) I
+  const size_t smem = sizeof(int) * ((size_t)dp.n_pad + kUMax) + sizeof(float) * kRB * kUMax;
+  void* fn;
+  if (dp.index_width == 16)
+    fn = dp.value_format == 1 ? (void*)k_btb<__nv_bfloat16, uint16_t>
+       : dp.value_format == 2 ? (void*)k_btb<__nv_fp8_e4m3, uint16_t> : (void*)k_btb<float, uint16_t>;
+  else
+    fn = dp.value_format == 1 ? (void*)k_btb<__nv_bfloat16, int32_t>
+       : dp.value_format == 2 ? (void*)k_btb<__nv_fp8_e4m3, int32_t> : (void*)k_btb<float, int32_t>;
+  if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
+    return done(cuda_fail(e, "kernel attribute"));
+  const dim3 gb((dp.m_act + kRB - 1) / kRB);
+  for (int s = 0; s < N; ++s) {
+    DevPlan dpc = dp;
+    float* Bs = P->binv + nn * s;
+    const int* ro = P->rec_of;
+    int ss = s;
+    void* args[] = {(void*)&dpc, (void*)&ss, (void*)&ro, (void*)&Bs};
+    if ((e = cudaLaunchKernel(fn, gb, dim3(256), args, smem, st))) return done(cuda_fail(e, "launch"));
+  }
+  const dim3 gd((n + 255) / 256, N);
+  k_add_diag<<<gd, 256, 0, st>>>(P->binv, n, (float)(0.5 * rho));
+  // 2. Cholesky, lower, in place
+  const int nblk = (n + kNB - 1) / kNB;
+  for (int kb = 0; kb < nblk; ++kb) {
+    k_potrf_diag<<<N, 256, 0, st>>>(P->binv, n, kb, P->err);
+    const int below = n - (kb + 1) * kNB;
+    if (below > 0) {
+      k_trsm_panel<<<dim3((below + 63) / 64, N), 64, 0, st>>>(P->binv, n, kb);
+      float* L21 = P->binv + (size_t)(kb + 1) * kNB * n + (size_t)kb * kNB;
+      float* A22 = P->binv + (size_t)(kb + 1) * kNB * n + (size_t)(kb + 1) * kNB;
+      gemm<false, true>(st, below, below, kNB, L21, n, L21, n, A22, n, nullptr, false, -1.f, 1.f, N, (long long)nn,
+                        (long long)nn, (long long)nn);
+    }
+  }
+  // 3. Y = L^{-1} (forward substitution on I, block row by block row)
+  k_set_identity<<<gd, 256, 0, st>>>(Y, n);
+  for (int kb = 0; kb < nblk; ++kb) {
+    const int r0 = kb * kNB, nb = std::min(kNB, n - r0);
+    if (r0 > 0)
+      gemm<false, false>(st, nb, r0, r0, P->binv + (size_t)r0 * n, n, Y, n, Y + (size_t)r0 * n, n, nullptr, false,
+                         -1.f, 1.f, N, (long long)nn, (long long)nn, (long long)nn);
+    const int cols = r0 + nb;
+    k_trsm_left<<<dim3((cols + 63) / 64, N), 64, 0, st>>>(P->binv, Y, n, kb, cols);
+  }
+  // 4. B^{-1} = Y^T Y into binv (the factor is no longer needed)
+  gemm<true, false>(st, n, n, n, Y, n, Y, n, P->binv, n, nullptr, false, 1.f, 0.f, N, (long long)nn, (long long)nn,
+                    (long long)nn);
+  if ((e = cudaGetLastError())) return done(cuda_fail(e, "launch"));
+  // 5. A~_s^T p~
+  if (int rc = compute_bconst(P)) return done(rc);
+  if ((e = cudaStreamSynchronize(st))) return done(cuda_fail(e, "sync"));
+  int herr = 0;
+  if ((e = cudaMemcpy(&herr, P->err, sizeof(int), cudaMemcpyDeviceToHost))) return done(cuda_fail(e, "copy"));
+  if (herr) {
+    cudaMemset(P->err, 0, sizeof(int));
+    set_error("cached-factor subproblem: B_s is not positive definite in float32");
+    return done(RPT_EINVAL);
+  }
+  P->chol_ready = true;
+  P->chol_rho = rho;
+  return done(RPT_OK);
+}
+
+}  // namespace rpt

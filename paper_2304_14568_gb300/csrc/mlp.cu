@@ -6,8 +6,8 @@
 // Network: n_in -> H -> ... -> H (L hidden layers, ReLU) -> n_out (linear).
 // Loss: mean squared error over the batch and the outputs.  Training: Adam on
 // minibatches drawn from a seeded permutation every epoch.  Everything runs in
-// the kernels below (FP32): a tiled shared-memory GEMM with transpose options
-// and fused bias/ReLU epilogue, the ReLU and bias gradients, the loss gradient
+// the library's kernels (FP32): the tiled shared-memory GEMM of gemm.cuh with its
+// fused bias/ReLU epilogue, the ReLU and bias gradients, the loss gradient
 // and the Adam update.  The network is small (a few hundred thousand weights,
 // batches of a few hundred rows), so the GEMMs are latency- and launch-bound;
 // they use the CUDA cores, not the tensor cores.
@@ -21,70 +21,11 @@
 #include <string>
 #include <vector>
 
+#include "gemm.cuh"
 #include "plan.h"
 
 namespace rpt {
 namespace {
-
-constexpr int kTM = 64, kTN = 64, kTK = 16;   // GEMM tile
-constexpr int kGemmThreads = 256;             // 16 x 16 threads, 4 x 4 outputs each
-
-// C[M][N] = op(A)[M][K] * op(B)[K][N] (+ bias[N]) (ReLU if relu)
-// op(A)(i,k) = TA ? A[k*lda + i] : A[i*lda + k];  op(B)(k,j) = TB ? B[j*ldb + k] : B[k*ldb + j]
-template <bool TA, bool TB>
-__global__ void __launch_bounds__(kGemmThreads)
-k_gemm(int M, int N, int K, const float* __restrict__ A, int lda, const float* __restrict__ B, int ldb,
-       float* __restrict__ C, int ldc, const float* __restrict__ bias, int relu) {
-  __shared__ float As[kTK][kTM + 4];
-  __shared__ float Bs[kTK][kTN + 4];
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  const int i0 = blockIdx.y * kTM, j0 = blockIdx.x * kTN;
-  float acc[4][4] = {};
-  for (int k0 = 0; k0 < K; k0 += kTK) {
-    for (int e = threadIdx.x; e < kTK * kTM; e += kGemmThreads) {
-      const int kk = e / kTM, ii = e % kTM;
-      const int i = i0 + ii, k = k0 + kk;
-      float a = 0.f;
-      if (i < M && k < K) a = TA ? A[(size_t)k * lda + i] : A[(size_t)i * lda + k];
-      As[kk][ii] = a;
-    }
-    for (int e = threadIdx.x; e < kTK * kTN; e += kGemmThreads) {
-      const int kk = e / kTN, jj = e % kTN;
-      const int j = j0 + jj, k = k0 + kk;
-      float b = 0.f;
-      if (j < N && k < K) b = TB ? B[(size_t)j * ldb + k] : B[(size_t)k * ldb + j];
-      Bs[kk][jj] = b;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int kk = 0; kk < kTK; ++kk) {
-      float a[4], b[4];
-#pragma unroll
-      for (int r = 0; r < 4; ++r) a[r] = As[kk][ty * 4 + r];
-#pragma unroll
-      for (int c = 0; c < 4; ++c) b[c] = Bs[kk][tx * 4 + c];
-#pragma unroll
-      for (int r = 0; r < 4; ++r)
-#pragma unroll
-        for (int c = 0; c < 4; ++c) acc[r][c] = fmaf(a[r], b[c], acc[r][c]);
-    }
-    __syncthreads();
-  }
-#pragma unroll
-  for (int r = 0; r < 4; ++r) {
-    const int i = i0 + ty * 4 + r;
-    if (i >= M) continue;
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      const int j = j0 + tx * 4 + c;
-      if (j >= N) continue;
-      float v = acc[r][c];
-      if (bias) v += bias[j];
-      if (relu) v = fmaxf(v, 0.f);
-      C[(size_t)i * ldc + j] = v;
-    }
-  }
-}
 
 // dH *= (H > 0)   (ReLU backward; H is the layer's output after ReLU)
 __global__ void k_relu_bwd(int64_t n, const float* __restrict__ H, float* __restrict__ dH) {
@@ -187,13 +128,6 @@ cudaError_t ensure_cap(Mlp* M, int rows) {
   if (e == cudaSuccess) e = cudaMalloc(&M->idx, sizeof(int) * (size_t)rows);
   if (e == cudaSuccess) M->cap = rows;
   return e;
-}
-
-template <bool TA, bool TB>
-void gemm(cudaStream_t st, int M_, int N, int K, const float* A, int lda, const float* B, int ldb, float* C,
-          int ldc, const float* bias, bool relu) {
-  dim3 grid((N + kTN - 1) / kTN, (M_ + kTM - 1) / kTM);
-  k_gemm<TA, TB><<<grid, kGemmThreads, 0, st>>>(M_, N, K, A, lda, B, ldb, C, ldc, bias, relu ? 1 : 0);
 }
 
 int blocks_for(int64_t n) { return (int)std::min<int64_t>(4096, std::max<int64_t>(1, (n + 255) / 256)); }

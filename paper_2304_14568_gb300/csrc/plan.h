@@ -64,6 +64,16 @@ struct Plan {
   Ctl *ctl = nullptr;             // device control block
   Ctl *ctl_host = nullptr;        // pinned mirror
 
+  // cached-factor subproblem (chol.cu): B_s^{-1} [N][n][n] FP32, A~_s^T p~ [N][n],
+  // record index of kept row k in scenario s's list [N][m_act] (-1: empty there)
+  float *binv = nullptr;
+  double *bchol = nullptr;
+  int *rec_of = nullptr;
+  bool chol_ready = false;
+  double chol_rho = 0.0;
+  cudaGraphExec_t admm_chol_exec = nullptr;
+  int admm_chol_exec_obj = -1;
+
   std::vector<int32_t> kept_rows; // original row index of each device row
   double lipschitz = 0.0;         // cached 2 lambda_max, 0 = not computed
   bool state_valid = false;
@@ -85,6 +95,8 @@ int op_objective(Plan* P, const double* x, double* f_out, double* dose_out);
 int compute_lipschitz(Plan* P, double* L);
 int profile_row_pass(Plan* P, int mode, int reps, double* ms, double* bytes);
 void destroy_graphs(Plan* P);
+int chol_prepare(Plan* P, double rho);   // chol.cu
+int compute_bconst(Plan* P);             // solver.cu: P->bchol = A~_s^T p~
 
 // error reporting (api.cu)
 void set_error(const std::string& msg);

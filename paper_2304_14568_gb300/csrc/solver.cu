@@ -16,6 +16,7 @@
 // Vectors are float64; the row passes see them rounded to float32 (staged in
 // shared memory).  Dot products and norms are float64; the per-CTA partials of
 // a row pass are summed in a fixed order with compensated float32 sums.
+#include <chrono>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -574,6 +575,49 @@ __global__ void k_reduce_scen(DevPlan P, const float* __restrict__ partial,
   out[o] = sum_partials(P, partial, s, j) + half_rho * v[o];
 }
 
+// grid (nchunk, N).  out[s][j] = -(row-pass partials of scenario s)[j]; with the
+// residual pass at v = 0 this is A~_s^T p~.
+__global__ void k_neg_partials(DevPlan P, const float* __restrict__ partial, double* out) {
+  const int s = blockIdx.y, j = blockIdx.x * VT + threadIdx.x;
+  if (j >= P.n) return;
+  out[(size_t)s * P.n + j] = -sum_partials(P, partial, s, j);
+}
+
+// Cached-factor x-update: x_s = B_s^{-1} c_s, c_s = A~_s^T p~ + (rho/2) z - y_s/2
+// (App. A).  grid (ceil(n / 32), N), 256 threads: c_s staged in shared memory as
+// float, one row of B_s^{-1} per warp step, FP64 accumulation.
+__global__ void __launch_bounds__(256)
+k_chol_x(DevPlan P, const Ctl* __restrict__ C, const float* __restrict__ binv, const double* __restrict__ bchol,
+         const double* __restrict__ z, const double* __restrict__ y, double* x) {
+  extern __shared__ float cbuf[];
+  const int s = blockIdx.y, n = P.n;
+  const double hr = 0.5 * C->rho;
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    const size_t o = (size_t)s * n + j;
+    cbuf[j] = (float)(bchol[o] + hr * z[j] - 0.5 * y[o]);
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const float* Bs = binv + (size_t)s * n * n;
+  for (int r = w; r < 32; r += 8) {
+    const int j = blockIdx.x * 32 + r;
+    if (j >= n) break;
+    const float* row = Bs + (size_t)j * n;
+    double acc = 0.0;
+    if ((n & 3) == 0) {
+      const float4* row4 = reinterpret_cast<const float4*>(row);
+      for (int k = lane; k < n / 4; k += 32) {
+        const float4 b = __ldcs(row4 + k);
+        acc += (double)(b.x * cbuf[4 * k] + b.y * cbuf[4 * k + 1]) + (double)(b.z * cbuf[4 * k + 2] + b.w * cbuf[4 * k + 3]);
+      }
+    } else {
+      for (int k = lane; k < n; k += 32) acc += (double)(__ldcs(row + k) * cbuf[k]);
+    }
+    acc = warp_sum_d(acc);
+    if (lane == 0) x[(size_t)s * n + j] = acc;
+  }
+}
+
 // grid (nchunk): out = scale * sum over all blocks.
 __global__ void k_reduce_all(DevPlan P, const float* __restrict__ partial, double scale, double* out) {
   const int j = blockIdx.x * VT + threadIdx.x;
@@ -699,6 +743,38 @@ void admm_tail_final(Exec& e, Plan* P) {
   launch(e, k_final_obj, dim3(1), dim3(32), 0, P->dp, P->ctl);
 }
 
+void chol_iteration_head(Exec& e, Plan* P) {
+  const DevPlan& dp = P->dp;
+  launch(e, k_chol_x, dim3((dp.n + 31) / 32, dp.N), dim3(256), sizeof(float) * (size_t)dp.n, dp,
+         (const Ctl*)P->ctl, (const float*)P->binv, (const double*)P->bchol, (const double*)P->z,
+         (const double*)P->y, P->x);
+}
+
+cudaError_t build_admm_chol_graph(Plan* P, int use_obj) {
+  cudaGraph_t g = nullptr;
+  cudaError_t err = cudaGraphCreate(&g, 0);
+  if (err != cudaSuccess) return err;
+  cudaGraphConditionalHandle hadmm = 0;
+  err = cudaGraphConditionalHandleCreate(&hadmm, g, 1, cudaGraphCondAssignDefault);
+  Exec top;
+  top.g = g;
+  top.err = err;
+  Exec body = top.while_body(hadmm);
+  chol_iteration_head(body, P);
+  admm_iteration_tail(body, P, use_obj, (unsigned long long)hadmm, 1);
+  if (body.err != cudaSuccess) top.err = body.err;
+  admm_tail_final(top, P);
+  err = top.err;
+  if (err == cudaSuccess) {
+    if (P->admm_chol_exec) cudaGraphExecDestroy(P->admm_chol_exec);
+    P->admm_chol_exec = nullptr;
+    err = cudaGraphInstantiate(&P->admm_chol_exec, g, 0);
+    if (err == cudaSuccess) P->admm_chol_exec_obj = use_obj;
+  }
+  cudaGraphDestroy(g);
+  return err;
+}
+
 cudaError_t build_admm_graph(Plan* P, int use_obj, double* z0d, double* y0d) {
   (void)z0d;
   (void)y0d;
@@ -809,8 +885,10 @@ cudaError_t read_ctl(Plan* P) {
 
 void destroy_graphs(Plan* P) {
   if (P->admm_exec) cudaGraphExecDestroy(P->admm_exec);
+  if (P->admm_chol_exec) cudaGraphExecDestroy(P->admm_chol_exec);
   if (P->pgd_exec) cudaGraphExecDestroy(P->pgd_exec);
   P->admm_exec = nullptr;
+  P->admm_chol_exec = nullptr;
   P->pgd_exec = nullptr;
 }
 
@@ -825,7 +903,7 @@ int admm_solve(Plan* P, const rpt_admm_params* prm, const double* z0, const doub
   }
   if (prm->max_iter < 1 || prm->cg_max < 0 || prm->eps_abs < 0 || prm->eps_rel < 0 ||
       prm->bb_mode < 0 || prm->bb_mode > 2 || prm->z_mode < 0 || prm->z_mode > 1 ||
-      prm->cg_precond < 0 || prm->cg_precond > 1 ||
+      prm->cg_precond < 0 || prm->cg_precond > 1 || prm->subproblem < 0 || prm->subproblem > 1 ||
       !(prm->bb_kappa >= 1.0) || !(prm->cg_theta > 0) || !(prm->cg_eta0 > 0) ||
       !(prm->cg_floor_rel >= 0) || std::isnan(prm->tol_obj)) {
     set_error("invalid ADMM parameters");
@@ -846,8 +924,19 @@ int admm_solve(Plan* P, const rpt_admm_params* prm, const double* z0, const doub
         }
   }
   const int use_obj = std::isfinite(prm->tol_obj) ? 1 : 0;
+  const bool chol = prm->subproblem == RPT_SUB_CHOL;
   cudaStream_t st = P->stream;
   cudaError_t e;
+  double setup_s = 0.0;
+  if (chol) {
+    if ((e = cudaFuncSetAttribute(k_chol_x, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)(sizeof(float) * (size_t)n))))
+      return cuda_fail(e, "kernel attribute");
+    const bool cached = P->chol_ready && P->chol_rho == rho;
+    const auto t0 = std::chrono::steady_clock::now();
+    if (int rc = chol_prepare(P, rho)) return rc;
+    if (!cached) setup_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
   // inputs: z0 -> znew (scratch until the first z-update), y0 -> u (scratch until CG)
   if (z0 && (e = cudaMemcpyAsync(P->znew, z0, sizeof(double) * n, cudaMemcpyHostToDevice, st)))
     return cuda_fail(e, "copy z0");
@@ -888,7 +977,29 @@ int admm_solve(Plan* P, const rpt_admm_params* prm, const double* z0, const doub
            P->z, P->dprev, P->v32);
     if (ex.err) return cuda_fail(ex.err, "launch init");
   }
-  if (prm->use_graph) {
+  if (chol && prm->use_graph) {
+    if (!P->admm_chol_exec || P->admm_chol_exec_obj != use_obj) {
+      if ((e = build_admm_chol_graph(P, use_obj))) return cuda_fail(e, "build ADMM graph");
+    }
+    if ((e = cudaGraphLaunch(P->admm_chol_exec, st))) return cuda_fail(e, "launch ADMM graph");
+  } else if (chol) {
+    const int every = prm->check_every > 0 ? prm->check_every : 1;
+    for (int it = 1;; ++it) {
+      Exec ex;
+      ex.st = st;
+      chol_iteration_head(ex, P);
+      admm_iteration_tail(ex, P, use_obj, 0, 0);
+      if (ex.err) return cuda_fail(ex.err, "launch");
+      if (it % every == 0 || it >= prm->max_iter) {
+        if ((e = read_ctl(P))) return cuda_fail(e, "read control");
+        if (P->ctl_host->stop) break;
+      }
+    }
+    Exec ex;
+    ex.st = st;
+    admm_tail_final(ex, P);
+    if (ex.err) return cuda_fail(ex.err, "launch");
+  } else if (prm->use_graph) {
     if (!P->admm_exec || P->admm_exec_obj != use_obj) {
       if ((e = build_admm_graph(P, use_obj, nullptr, nullptr))) return cuda_fail(e, "build ADMM graph");
     }
@@ -940,7 +1051,9 @@ int admm_solve(Plan* P, const rpt_admm_params* prm, const double* z0, const doub
     info->row_passes = h.passes;
     // init + per iteration (residual pass, CG init, 3 per CG step, z/d/y, 2 for the
     // optional objective test) + final objective pass and its reduction
-    info->kernels = 3 + 5LL * h.k + 3LL * h.cg_steps + (use_obj ? 2LL * h.k : 0LL);
+    info->kernels = chol ? 3 + 4LL * h.k + (use_obj ? 2LL * h.k : 0LL)
+                         : 3 + 5LL * h.k + 3LL * h.cg_steps + (use_obj ? 2LL * h.k : 0LL);
+    info->setup_seconds = setup_s;
     info->seconds = ms * 1e-3;
     info->f = h.f_cur;
     info->r_prim = h.r_prim;
@@ -1194,6 +1307,19 @@ int profile_row_pass(Plan* P, int mode, int reps, double* ms, double* bytes) {
     *bytes = (double)P->stats.matrix_bytes + per_row * (double)dp.N * dp.m_act +
              2.0 * 4.0 * (double)dp.N * dp.n;
   }
+  return RPT_OK;
+}
+
+int compute_bconst(Plan* P) {
+  const DevPlan& dp = P->dp;
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(P->v32, 0, sizeof(float) * (size_t)dp.N * dp.n_pad, P->stream)))
+    return cuda_fail(e, "memset");
+  Exec ex;
+  ex.st = P->stream;
+  rowpass(ex, P, kResid, P->v32, dp.n_pad, nullptr);
+  launch(ex, k_neg_partials, dim3(P->nchunk, dp.N), dim3(VT), 0, dp, (const float*)P->partial, P->bchol);
+  if (ex.err) return cuda_fail(ex.err, "launch");
   return RPT_OK;
 }
 

@@ -15,6 +15,7 @@ LIB_PATH = os.path.join(_HERE, "librpt.so")
 
 OK, NOT_CONVERGED, EINVAL, ENOMEM, ECUDA, TIMEOUT, DIVERGED, EUNSUPPORTED = 0, 1, -1, -2, -3, -4, -5, -6
 F32, BF16, FP8E4M3 = 0, 1, 2
+SUB_CG, SUB_CHOL = 0, 1
 BB_PAPER, BB_GUARDED, BB_OFF = 0, 1, 2
 Z_STD, Z_LIT = 0, 1
 MAX_SPOTS = 24576
@@ -62,7 +63,7 @@ class AdmmParams(C.Structure):
                 ("bb_mode", C.c_int32), ("bb_kappa", C.c_double), ("z_mode", C.c_int32),
                 ("cg_max", C.c_int32), ("cg_theta", C.c_double), ("cg_eta0", C.c_double),
                 ("cg_floor_rel", C.c_double), ("use_graph", C.c_int32), ("check_every", C.c_int32),
-                ("resume", C.c_int32), ("cg_precond", C.c_int32)]
+                ("resume", C.c_int32), ("cg_precond", C.c_int32), ("subproblem", C.c_int32)]
 
 
 class PgdParams(C.Structure):
@@ -75,7 +76,8 @@ class _Info(C.Structure):
     _fields_ = [("status", C.c_int32), ("iterations", C.c_int32), ("inner", C.c_int64),
                 ("row_passes", C.c_int64), ("kernels", C.c_int64), ("seconds", C.c_double), ("f", C.c_double),
                 ("r_prim", C.c_double), ("r_dual", C.c_double), ("eps_prim", C.c_double),
-                ("eps_dual", C.c_double), ("step", C.c_double), ("rho", C.c_double)]
+                ("eps_dual", C.c_double), ("step", C.c_double), ("rho", C.c_double),
+                ("setup_seconds", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -86,3 +86,17 @@ def test_benchmark_solve_reaches_the_oracle_optimum(big):
     fstar = g["f_star"]
     # eps = 1e-4 on the residuals of Eq. 9 leaves a small objective gap
     assert fstar <= fz * (1 + 1e-9) and (fz - fstar) / fstar <= 1e-4, ((fz - fstar) / fstar)
+
+
+def test_cached_factor_solve_reaches_the_oracle_optimum(rpt, big):
+    prob, W, P = big
+    z, info = P.admm_bb_solve(subproblem=rpt.SUB_CHOL)
+    assert info["status"] == 0 and info["setup_seconds"] > 0
+    assert np.all(z >= prob.lb) and np.all(z <= prob.ub)
+    fz = W.f(z)
+    assert info["f"] == pytest.approx(fz, rel=1e-5)
+    assert certificates(W, z)["pg"] < 1e-2
+    if not os.path.exists(GOLD):
+        pytest.skip("no stored oracle optimum")
+    fstar = json.load(open(GOLD))["f_star"]
+    assert fstar <= fz * (1 + 1e-9) and (fz - fstar) / fstar <= 1e-4, ((fz - fstar) / fstar)
