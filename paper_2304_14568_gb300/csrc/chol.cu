@@ -141,6 +141,24 @@ __global__ void k_add_diag(float* B, int n, float half_rho) {
   if (j < n) B[(size_t)blockIdx.y * n * n + (size_t)j * n + j] += half_rho;
 }
 
+// Upper triangle of every B_s^{-1} from its lower triangle (32 x 32 tiles through
+// shared memory; grid (tiles, tiles, scenario), only tiles with row block >= column block).
+__global__ void k_mirror_lower(float* X, int n) {
+  __shared__ float t[32][33];
+  const int bi = blockIdx.y, bj = blockIdx.x;
+  if (bj > bi) return;
+  float* Xs = X + (size_t)blockIdx.z * n * n;
+  for (int r = threadIdx.y; r < 32; r += 8) {
+    const int i = bi * 32 + r, j = bj * 32 + threadIdx.x;
+    if (i < n && j < n) t[r][threadIdx.x] = Xs[(size_t)i * n + j];
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += 8) {
+    const int i = bj * 32 + r, j = bi * 32 + threadIdx.x;       // (i, j) = transposed position
+    if (i < n && j < n && j > i) Xs[(size_t)i * n + j] = t[threadIdx.x][r];
+  }
+}
+
 // Y_s = I (all scenarios; Y zero on entry).
 __global__ void k_set_identity(float* Y, int n) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -295,7 +313,7 @@ int chol_prepare(Plan* P, double rho) {
       float* L21 = P->binv + (size_t)(kb + 1) * kNB * n + (size_t)kb * kNB;
       float* A22 = P->binv + (size_t)(kb + 1) * kNB * n + (size_t)(kb + 1) * kNB;
       gemm<false, true>(st, below, below, kNB, L21, n, L21, n, A22, n, nullptr, false, -1.f, 1.f, N, (long long)nn,
-                        (long long)nn, (long long)nn);
+                        (long long)nn, (long long)nn, /*lower=*/true);
     }
   }
   // 3. Y = L^{-1} (forward substitution on I, block row by block row)
@@ -304,13 +322,15 @@ int chol_prepare(Plan* P, double rho) {
     const int r0 = kb * kNB, nb = std::min(kNB, n - r0);
     if (r0 > 0)
       gemm<false, false>(st, nb, r0, r0, P->binv + (size_t)r0 * n, n, Y, n, Y + (size_t)r0 * n, n, nullptr, false,
-                         -1.f, 1.f, N, (long long)nn, (long long)nn, (long long)nn);
+                         -1.f, 1.f, N, (long long)nn, (long long)nn, (long long)nn, false, /*kdiag=*/1);
     const int cols = r0 + nb;
     k_trsm_left<<<dim3((cols + 63) / 64, N), 64, 0, st>>>(P->binv, Y, n, kb, cols);
   }
-  // 4. B^{-1} = Y^T Y into binv (the factor is no longer needed)
+  // 4. B^{-1} = Y^T Y into binv (the factor is no longer needed): lower tiles, the
+  //    sum starting at max(i, j) since Y is lower triangular; then mirrored
   gemm<true, false>(st, n, n, n, Y, n, Y, n, P->binv, n, nullptr, false, 1.f, 0.f, N, (long long)nn, (long long)nn,
-                    (long long)nn);
+                    (long long)nn, /*lower=*/true, /*kdiag=*/2);
+  k_mirror_lower<<<dim3((n + 31) / 32, (n + 31) / 32, N), dim3(32, 8), 0, st>>>(P->binv, n);
   if ((e = cudaGetLastError())) return done(cuda_fail(e, "launch"));
   // 5. A~_s^T p~
   if (int rc = compute_bconst(P)) return done(rc);

@@ -583,32 +583,55 @@ __global__ void k_neg_partials(DevPlan P, const float* __restrict__ partial, dou
   out[(size_t)s * P.n + j] = -sum_partials(P, partial, s, j);
 }
 
-// Cached-factor x-update: x_s = B_s^{-1} c_s, c_s = A~_s^T p~ + (rho/2) z - y_s/2
-// (App. A).  grid (ceil(n / 32), N), 256 threads: c_s staged in shared memory as
-// float, one row of B_s^{-1} per warp step, FP64 accumulation.
+// Cached-factor x-update, part 1: c_s = A~_s^T p~ + (rho/2) z - y_s/2 as float
+// (grid (nchunk, N)).
+__global__ void k_chol_rhs(DevPlan P, const Ctl* __restrict__ C, const double* __restrict__ bchol,
+                           const double* __restrict__ z, const double* __restrict__ y, float* c) {
+  const int s = blockIdx.y, j = blockIdx.x * VT + threadIdx.x;
+  if (j >= P.n) return;
+  const size_t o = (size_t)s * P.n + j;
+  c[(size_t)s * P.n_pad + j] = (float)(bchol[o] + 0.5 * C->rho * z[j] - 0.5 * y[o]);
+}
+
+// Cached-factor x-update, part 2 (App. A): x_s = B_s^{-1} c_s.  grid (ceil(n /
+// kCholRows), N), 256 threads: c_s staged in shared memory, each warp takes rows
+// of B_s^{-1} (streamed once, evict-first) with four 16-byte loads in flight per
+// lane, FP64 accumulation of FP32 products.
+constexpr int kCholRows = 64;
 __global__ void __launch_bounds__(256)
-k_chol_x(DevPlan P, const Ctl* __restrict__ C, const float* __restrict__ binv, const double* __restrict__ bchol,
-         const double* __restrict__ z, const double* __restrict__ y, double* x) {
+k_chol_x(DevPlan P, const float* __restrict__ binv, const float* __restrict__ c, double* x) {
   extern __shared__ float cbuf[];
   const int s = blockIdx.y, n = P.n;
-  const double hr = 0.5 * C->rho;
-  for (int j = threadIdx.x; j < n; j += blockDim.x) {
-    const size_t o = (size_t)s * n + j;
-    cbuf[j] = (float)(bchol[o] + hr * z[j] - 0.5 * y[o]);
-  }
+  for (int j = threadIdx.x; j < n; j += blockDim.x) cbuf[j] = c[(size_t)s * P.n_pad + j];
   __syncthreads();
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const float* Bs = binv + (size_t)s * n * n;
-  for (int r = w; r < 32; r += 8) {
-    const int j = blockIdx.x * 32 + r;
+  const bool vec = (n & 3) == 0;
+  for (int r = w; r < kCholRows; r += 8) {
+    const int j = blockIdx.x * kCholRows + r;
     if (j >= n) break;
     const float* row = Bs + (size_t)j * n;
     double acc = 0.0;
-    if ((n & 3) == 0) {
+    if (vec) {
       const float4* row4 = reinterpret_cast<const float4*>(row);
-      for (int k = lane; k < n / 4; k += 32) {
+      const float4* c4 = reinterpret_cast<const float4*>(cbuf);
+      const int nq = n >> 2;
+      int k = lane;
+      for (; k + 96 < nq; k += 128) {
+        const float4 b0 = __ldcs(row4 + k), b1 = __ldcs(row4 + k + 32), b2 = __ldcs(row4 + k + 64),
+                     b3 = __ldcs(row4 + k + 96);
+        const float4 v0 = c4[k], v1 = c4[k + 32], v2 = c4[k + 64], v3 = c4[k + 96];
+        float t = b0.x * v0.x + b0.y * v0.y + b0.z * v0.z + b0.w * v0.w;
+        t += b1.x * v1.x + b1.y * v1.y + b1.z * v1.z + b1.w * v1.w;
+        acc += (double)t;
+        t = b2.x * v2.x + b2.y * v2.y + b2.z * v2.z + b2.w * v2.w;
+        t += b3.x * v3.x + b3.y * v3.y + b3.z * v3.z + b3.w * v3.w;
+        acc += (double)t;
+      }
+      for (; k < nq; k += 32) {
         const float4 b = __ldcs(row4 + k);
-        acc += (double)(b.x * cbuf[4 * k] + b.y * cbuf[4 * k + 1]) + (double)(b.z * cbuf[4 * k + 2] + b.w * cbuf[4 * k + 3]);
+        const float4 v = c4[k];
+        acc += (double)(b.x * v.x + b.y * v.y + b.z * v.z + b.w * v.w);
       }
     } else {
       for (int k = lane; k < n; k += 32) acc += (double)(__ldcs(row + k) * cbuf[k]);
@@ -745,9 +768,10 @@ void admm_tail_final(Exec& e, Plan* P) {
 
 void chol_iteration_head(Exec& e, Plan* P) {
   const DevPlan& dp = P->dp;
-  launch(e, k_chol_x, dim3((dp.n + 31) / 32, dp.N), dim3(256), sizeof(float) * (size_t)dp.n, dp,
-         (const Ctl*)P->ctl, (const float*)P->binv, (const double*)P->bchol, (const double*)P->z,
-         (const double*)P->y, P->x);
+  launch(e, k_chol_rhs, dim3(P->nchunk, dp.N), dim3(VT), 0, dp, (const Ctl*)P->ctl, (const double*)P->bchol,
+         (const double*)P->z, (const double*)P->y, P->v32);
+  launch(e, k_chol_x, dim3((dp.n + kCholRows - 1) / kCholRows, dp.N), dim3(256), sizeof(float) * (size_t)dp.n_pad,
+         dp, (const float*)P->binv, (const float*)P->v32, P->x);
 }
 
 cudaError_t build_admm_chol_graph(Plan* P, int use_obj) {
@@ -930,7 +954,7 @@ int admm_solve(Plan* P, const rpt_admm_params* prm, const double* z0, const doub
   double setup_s = 0.0;
   if (chol) {
     if ((e = cudaFuncSetAttribute(k_chol_x, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)(sizeof(float) * (size_t)n))))
+                                  (int)(sizeof(float) * (size_t)dp.n_pad))))
       return cuda_fail(e, "kernel attribute");
     const bool cached = P->chol_ready && P->chol_rho == rho;
     const auto t0 = std::chrono::steady_clock::now();
@@ -1051,7 +1075,7 @@ int admm_solve(Plan* P, const rpt_admm_params* prm, const double* z0, const doub
     info->row_passes = h.passes;
     // init + per iteration (residual pass, CG init, 3 per CG step, z/d/y, 2 for the
     // optional objective test) + final objective pass and its reduction
-    info->kernels = chol ? 3 + 4LL * h.k + (use_obj ? 2LL * h.k : 0LL)
+    info->kernels = chol ? 3 + 5LL * h.k + (use_obj ? 2LL * h.k : 0LL)
                          : 3 + 5LL * h.k + 3LL * h.cg_steps + (use_obj ? 2LL * h.k : 0LL);
     info->setup_seconds = setup_s;
     info->seconds = ms * 1e-3;
