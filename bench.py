@@ -397,6 +397,10 @@ def main():
     if not args.no_chol:
         # the paper's subproblem solver (App. A): cached factor of B_s, x_s = B_s^{-1} c_s
         prm_c = rpt.admm_params(subproblem=rpt.SUB_CHOL)
+        if args.max_iter > 0:
+            prm_c.max_iter = args.max_iter
+        if args.no_graph:
+            prm_c.use_graph = 0
         zc, ic0 = plan.admm_bb_solve(prm_c)          # forms and inverts B_s (timed by the library)
         ce0 = torch.cuda.Event(enable_timing=True)
         ce1 = torch.cuda.Event(enable_timing=True)

@@ -71,6 +71,20 @@ __device__ __forceinline__ bool last_block(unsigned int* counter, unsigned int t
   return am_last;
 }
 
+// In the last block: S[k] = sum over b < count of buf[b * stride + off + k], the
+// whole block taking entries b = tid, tid + blockDim, ... then a block reduction
+// (a fixed order for a given launch shape).  Result valid in thread 0.
+template <int K>
+__device__ __forceinline__ void last_block_sums(const double* buf, int count, int stride, int off, double (&S)[K],
+                                                double* sh /* [K*32] */) {
+#pragma unroll
+  for (int k = 0; k < K; ++k) S[k] = 0.0;
+  for (int b = threadIdx.x; b < count; b += blockDim.x)
+#pragma unroll
+    for (int k = 0; k < K; ++k) S[k] += __ldcg(&buf[(size_t)b * stride + off + k]);
+  block_sum_d<K>(S, sh);
+}
+
 __device__ __forceinline__ void set_cond(unsigned long long h, int use, int value) {
   if (use) cudaGraphSetConditional((cudaGraphConditionalHandle)h, value ? 1u : 0u);
 }
@@ -312,12 +326,10 @@ __global__ void k_admm_z(DevPlan P, Ctl* C, const double* __restrict__ x, const 
     vpart[blockIdx.x * 8 + 1] = v[1];
   }
   if (!last_block(&C->cnt_z, gridDim.x)) return;
+  double S2[2];
+  last_block_sums<2>(vpart, gridDim.x, 8, 0, S2, sh);
   if (threadIdx.x == 0) {
-    double a = 0.0, b = 0.0;
-    for (int c = 0; c < (int)gridDim.x; ++c) {
-      a += __ldcg(&vpart[c * 8 + 0]);
-      b += __ldcg(&vpart[c * 8 + 1]);
-    }
+    const double a = S2[0], b = S2[1];
     C->sz2 = a;
     C->dz2 = b;
   }
@@ -349,10 +361,9 @@ __global__ void k_admm_d(DevPlan P, Ctl* C, const double* __restrict__ x,
     for (int k = 0; k < 4; ++k) vpart[(size_t)(nchunk + blk) * 8 + k] = v[k];
   }
   if (!last_block(&C->cnt_d, gridDim.x * gridDim.y)) return;
+  double S[4];
+  last_block_sums<4>(vpart + (size_t)nchunk * 8, gridDim.x * gridDim.y, 8, 0, S, sh);
   if (threadIdx.x == 0) {
-    double S[4] = {0.0, 0.0, 0.0, 0.0};
-    for (int b = 0; b < (int)(gridDim.x * gridDim.y); ++b)
-      for (int k = 0; k < 4; ++k) S[k] += __ldcg(&vpart[(size_t)(nchunk + b) * 8 + k]);
     const double rho = C->rho;
     double step = rho;
     if (C->bb_mode != 2 && C->have_prev && S[1] > 0.0) {
@@ -401,9 +412,10 @@ __global__ void k_admm_y(DevPlan P, Ctl* C, const double* __restrict__ x, double
   const int blk = s * nchunk + blockIdx.x;
   if (threadIdx.x == 0) vpart[(size_t)(nchunk + blk) * 8 + 4] = v[0];
   if (!last_block(&C->cnt_y, gridDim.x * gridDim.y)) return;
+  double SY[1];
+  last_block_sums<1>(vpart + (size_t)nchunk * 8, gridDim.x * gridDim.y, 8, 4, SY, sh);
   if (threadIdx.x == 0) {
-    double Y = 0.0;
-    for (int b = 0; b < (int)(gridDim.x * gridDim.y); ++b) Y += __ldcg(&vpart[(size_t)(nchunk + b) * 8 + 4]);
+    const double Y = SY[0];
     C->eps_dual = C->eps_abs * sqrt((double)P.N * P.n) + C->eps_rel * sqrt(Y);
     const int conv = (C->r_prim <= C->eps_prim) && (C->r_dual <= C->eps_dual);
     C->k += 1;
