@@ -121,17 +121,20 @@ k_btb(DevPlan P, int s, const int* __restrict__ rec_of, float* __restrict__ B) {
       }
     }
   __syncthreads();
-  // pairs a >= b of U (row U[a] >= column U[b]: the lower triangle)
-  const long long npairs = (long long)nu * (nu + 1) / 2;
-  for (long long p = tid; p < npairs; p += blockDim.x) {
-    int a = (int)((sqrt(8.0 * (double)p + 1.0) - 1.0) * 0.5);
-    while ((long long)a * (a + 1) / 2 > p) --a;
-    while ((long long)(a + 1) * (a + 2) / 2 <= p) ++a;
-    const int b = (int)(p - (long long)a * (a + 1) / 2);
-    float sum = 0.f;
+  // pairs a >= b of U (row U[a] >= column U[b]: the lower triangle): a warp takes
+  // a row a (its D column broadcast), its lanes the columns b <= a
+  const int nwarps = blockDim.x >> 5;
+  for (int a = w; a < nu; a += nwarps) {
+    float da[kRB];
 #pragma unroll
-    for (int r = 0; r < kRB; ++r) sum = fmaf(D[r * kUMax + a], D[r * kUMax + b], sum);
-    if (sum != 0.f) atomicAdd(&B[(size_t)U[a] * n + U[b]], sum);
+    for (int r = 0; r < kRB; ++r) da[r] = D[r * kUMax + a];
+    const size_t rowoff = (size_t)U[a] * n;
+    for (int b = lane; b <= a; b += 32) {
+      float sum = 0.f;
+#pragma unroll
+      for (int r = 0; r < kRB; ++r) sum = fmaf(da[r], D[r * kUMax + b], sum);
+      if (sum != 0.f) atomicAdd(&B[rowoff + U[b]], sum);
+    }
   }
 }
 
