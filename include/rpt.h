@@ -116,6 +116,7 @@ typedef struct {
                              formed, factored and inverted once per (plan, rho) in FP32 on the device,
                              then x_s = B_s^{-1} c_s each iteration (4 n^2 N bytes of device memory,
                              plus as much again while it is formed) */
+  int32_t trace;          /* 1: record one entry per iteration (see rpt_trace_get); default 0 */
 } rpt_admm_params;
 
 #define RPT_SUB_CG   0
@@ -319,6 +320,14 @@ int rpt_mlp_predict(rpt_mlp* mlp, const float* X, int32_t n, float* Y);
 int rpt_admm_bb_solve_learned(rpt_plan* plan, rpt_mlp* mlp, const float* features, const double* zscale,
                               const rpt_admm_params* params, double* x_out, rpt_solve_info* info,
                               int32_t* used_warm_start);
+
+/* ---- tracing --------------------------------------------------------------
+ * The per-iteration record of the plan's last solve run with params.trace = 1:
+ * count (<= 65536) entries of 8 doubles {iteration, seconds since the first
+ * iteration ended (device clock), r_prim, r_dual, eps_prim, eps_dual (Eq. 9),
+ * dual step (Eq. 8), CG steps so far summed over scenarios}.  out: [cap][8] host
+ * or NULL (count only).  Solves also appear as NVTX ranges ("rpt: ...") for tools. */
+int rpt_trace_get(rpt_plan* plan, double* out, int32_t cap, int32_t* count);
 
 /* ---- diagnostics --------------------------------------------------------- */
 const char* rpt_status_string(int status);   /* static string */

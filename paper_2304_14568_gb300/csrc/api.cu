@@ -125,14 +125,26 @@ void check_scenario(const rpt_problem* pr, int s, ScenarioCheck* out) {
   out->trace = tr;
 }
 
+// Device allocations of a plan.  RPT_DEVICE_MEM_CAP (bytes, environment) caps the
+// plan's total, so that running out of device memory can be tested without
+// exhausting the device: a request past the cap fails as cudaMalloc would.
 struct Alloc {
   Plan* P;
   cudaError_t err = cudaSuccess;
+  size_t total = 0;
+  size_t cap = (size_t)std::strtoull(std::getenv("RPT_DEVICE_MEM_CAP") ? std::getenv("RPT_DEVICE_MEM_CAP") : "0",
+                                     nullptr, 10);
   template <typename T>
   T* get(size_t count) {
     if (err != cudaSuccess) return nullptr;
     void* p = nullptr;
-    err = cudaMalloc(&p, std::max<size_t>(count, 1) * sizeof(T));
+    const size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+    if (cap && total + bytes > cap) {
+      err = cudaErrorMemoryAllocation;
+      return nullptr;
+    }
+    total += bytes;
+    err = cudaMalloc(&p, bytes);
     if (err != cudaSuccess) return nullptr;
     P->allocs.push_back(p);
     return (T*)p;
@@ -441,6 +453,10 @@ int create_plan(const rpt_problem* pr, const rpt_device_opts* opts, rpt_plan** o
   dp.m_act = m_act;
   dp.n_pad = n_pad;
   dp.value_format = pr->value_format;
+  // RPT_INJECT_TIMEOUT=1 (environment): the bulk-copy ring's producer issues no
+  // copy, so every consumer wait runs out (after its one-second bound) and the
+  // pass reports RPT_TIMEOUT; for testing the bounded waits without a GPU fault
+  dp.inject_timeout = env_int("RPT_INJECT_TIMEOUT", 0) != 0 ? 1 : 0;
   dp.index_width = pr->index_width;
   P->nchunk = (n + kVecThreads - 1) / kVecThreads;
   P->kept_rows = kept;
@@ -992,6 +1008,7 @@ void rpt_admm_params_default(rpt_admm_params* p) {
   p->resume = 0;
   p->cg_precond = 1;
   p->subproblem = RPT_SUB_CG;
+  p->trace = 0;
 }
 
 void rpt_pgd_params_default(rpt_pgd_params* p) {
@@ -1163,3 +1180,20 @@ const char* rpt_last_error(void) { return g_last_error.c_str(); }
 const char* rpt_version(void) { return "librpt 0.1 (sm_103a)"; }
 
 }  // extern "C"
+
+extern "C" int rpt_trace_get(rpt_plan* plan, double* out, int32_t cap, int32_t* count) {
+  if (!plan || !count || cap < 0) {
+    rpt::set_error("rpt_trace_get: bad argument");
+    return RPT_EINVAL;
+  }
+  rpt::Plan* P = reinterpret_cast<rpt::Plan*>(plan);
+  *count = P->trace_count;
+  if (!out || P->trace_count == 0) return RPT_OK;
+  const int k = std::min(cap, P->trace_count);
+  cudaError_t e = cudaSetDevice(P->device);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(out, P->trace, sizeof(double) * rpt::kTraceFields * (size_t)k, cudaMemcpyDeviceToHost,
+                        P->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(P->stream);
+  return e == cudaSuccess ? RPT_OK : rpt::cuda_fail(e, "rpt_trace_get");
+}

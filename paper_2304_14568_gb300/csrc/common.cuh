@@ -81,6 +81,7 @@ struct DevPlan {
   const int* rec_base;                // [N+1] first record of each scenario's row list
   const ChunkDesc* chunks;            // path 1: scenario-major chunk list
   int* err;                           // device error word (bounded waits that ran out)
+  int inject_timeout;                 // testing: the ring's producer issues nothing (waits run out)
 };
 
 // ---- row-pass modes ---------------------------------------------------------

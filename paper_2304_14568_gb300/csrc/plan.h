@@ -28,7 +28,17 @@ struct Ctl {
   // last-block-done counters (every finisher resets its own counter)
   unsigned int cnt_init, cnt_dots_g, cnt_upd, cnt_d, cnt_y, cnt_z, cnt_red, cnt_pg, cnt_pt;
   unsigned int pad3;
+  // optional per-iteration trace (rpt_admm_params.trace): kTraceFields doubles per
+  // iteration, at most trace_cap iterations, written by the dual update's last block
+  double* trace;
+  int trace_cap, trace_on;
+  unsigned long long t_start;      // %globaltimer at the first iteration (trace time base)
 };
+
+// trace entry: iteration, seconds since the solve started, r_prim, r_dual,
+// eps_prim, eps_dual, dual step, CG steps so far (summed over scenarios)
+constexpr int kTraceFields = 8;
+constexpr int kTraceCap = 1 << 16;
 
 struct Plan {
   int device = 0;
@@ -69,6 +79,8 @@ struct Plan {
   float *binv = nullptr;
   double *bchol = nullptr;
   int *rec_of = nullptr;
+  double *trace = nullptr;         // [kTraceCap][kTraceFields] (allocated on first traced solve)
+  int trace_count = 0;             // entries of the last traced solve
   bool chol_ready = false;
   double chol_rho = 0.0;
   cudaGraphExec_t admm_chol_exec = nullptr;

@@ -192,7 +192,7 @@ k_rowpass_tma(DevPlan P, const float* __restrict__ vin, int v_stride, const int*
       // walk the scenarios starting at this CTA's home scenario, taking chunks
       // from each scenario's queue until all queues are empty
       const int home = (int)(((long long)blockIdx.x * P.N) / gridDim.x);
-      for (int k = 0; k < P.N && ok; ++k) {
+      for (int k = 0; k < P.N && ok && !P.inject_timeout; ++k) {
         const int sc = (home + k) % P.N;
         if (active != nullptr && active[sc] == 0) continue;
         const int c0 = P.scen_chunk[sc], c1 = P.scen_chunk[sc + 1];
@@ -234,8 +234,10 @@ k_rowpass_tma(DevPlan P, const float* __restrict__ vin, int v_stride, const int*
           cb = cbn;
         }
       }
-      // end-of-work marker in the next stage
-      if (ok && (issued < S || mbar_wait(smem_u32(&empty[st]), (uint32_t)(ph ^ 1)))) {
+      // end-of-work marker in the next stage (none when a timeout is injected)
+      if (P.inject_timeout) {
+        ok = true;
+      } else if (ok && (issued < S || mbar_wait(smem_u32(&empty[st]), (uint32_t)(ph ^ 1)))) {
         ChunkDesc endm{};
         endm.n_rows = -1;
         sdesc[st] = endm;

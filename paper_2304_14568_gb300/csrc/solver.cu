@@ -21,6 +21,8 @@
 #include <cstring>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "plan.h"
 
 namespace rpt {
@@ -418,6 +420,20 @@ __global__ void k_admm_y(DevPlan P, Ctl* C, const double* __restrict__ x, double
     const double Y = SY[0];
     C->eps_dual = C->eps_abs * sqrt((double)P.N * P.n) + C->eps_rel * sqrt(Y);
     const int conv = (C->r_prim <= C->eps_prim) && (C->r_dual <= C->eps_dual);
+    if (C->trace_on && C->k < C->trace_cap) {
+      unsigned long long t;
+      asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+      if (C->k == 0) C->t_start = t;
+      double* e = C->trace + (size_t)C->k * kTraceFields;
+      e[0] = (double)(C->k + 1);
+      e[1] = 1e-9 * (double)(t - C->t_start);
+      e[2] = C->r_prim;
+      e[3] = C->r_dual;
+      e[4] = C->eps_prim;
+      e[5] = C->eps_dual;
+      e[6] = step;
+      e[7] = (double)C->cg_total;
+    }
     C->k += 1;
     C->have_prev = 1;
     C->step_prev = step;
@@ -928,8 +944,24 @@ void destroy_graphs(Plan* P) {
   P->pgd_exec = nullptr;
 }
 
+namespace {
+struct NvtxRange {            // NVTX range for tools (no cost without one attached)
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
+}  // namespace
+
+int admm_solve_impl(Plan* P, const rpt_admm_params* prm, const double* z0, const double* y0, double* x_out,
+                    rpt_solve_info* info);
+
 int admm_solve(Plan* P, const rpt_admm_params* prm, const double* z0, const double* y0,
                double* x_out, rpt_solve_info* info) {
+  NvtxRange r(prm && prm->subproblem == RPT_SUB_CHOL ? "rpt: ADMM-BB (cached factor)" : "rpt: ADMM-BB (CG)");
+  return admm_solve_impl(P, prm, z0, y0, x_out, info);
+}
+
+int admm_solve_impl(Plan* P, const rpt_admm_params* prm, const double* z0, const double* y0,
+                    double* x_out, rpt_solve_info* info) {
   const DevPlan& dp = P->dp;
   const int n = dp.n, N = dp.N;
   double rho = prm->rho > 0 ? prm->rho : prm->rho_scale * P->stats.default_rho;
@@ -997,6 +1029,15 @@ int admm_solve(Plan* P, const rpt_admm_params* prm, const double* z0, const doub
   c.precond = prm->cg_precond;
   c.use_obj = use_obj;
   c.first = 1;
+  if (prm->trace) {
+    if (!P->trace) {
+      if ((e = cudaMalloc(&P->trace, sizeof(double) * kTraceFields * kTraceCap))) return cuda_fail(e, "trace buffer");
+      P->allocs.push_back(P->trace);
+    }
+    c.trace = P->trace;
+    c.trace_cap = kTraceCap;
+    c.trace_on = 1;
+  }
   c.step_prev = rho;
   c.step = rho;
   c.f_prev = HUGE_VAL;
@@ -1099,12 +1140,14 @@ int admm_solve(Plan* P, const rpt_admm_params* prm, const double* z0, const doub
     info->step = h.step;
     info->rho = rho;
   }
+  P->trace_count = prm->trace ? std::min(h.k, kTraceCap) : 0;
   if (status == RPT_DIVERGED) set_error("ADMM residuals became non-finite");
   return status;
 }
 
 int pgd_solve(Plan* P, const rpt_pgd_params* prm, const double* x0, double* x_out,
               rpt_solve_info* info) {
+  NvtxRange range("rpt: PGD");
   const DevPlan& dp = P->dp;
   const int n = dp.n;
   if (!(prm->beta > 0 && prm->beta < 1) || !(prm->gamma > 0 && prm->gamma < 1) ||

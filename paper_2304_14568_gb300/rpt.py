@@ -26,7 +26,7 @@ EXPORTED = [
     "rpt_apply_normal", "rpt_profile_row_pass", "rpt_normal_apply_noalloc", "rpt_state_get", "rpt_state_set", "rpt_status_string", "rpt_last_error",
     "rpt_version", "rpt_mlp_train_params_default", "rpt_mlp_create", "rpt_mlp_destroy", "rpt_mlp_param_count",
     "rpt_mlp_get_params", "rpt_mlp_set_params", "rpt_mlp_loss_grad", "rpt_mlp_train", "rpt_mlp_predict",
-    "rpt_admm_bb_solve_learned",
+    "rpt_admm_bb_solve_learned", "rpt_trace_get",
 ]
 
 
@@ -63,7 +63,8 @@ class AdmmParams(C.Structure):
                 ("bb_mode", C.c_int32), ("bb_kappa", C.c_double), ("z_mode", C.c_int32),
                 ("cg_max", C.c_int32), ("cg_theta", C.c_double), ("cg_eta0", C.c_double),
                 ("cg_floor_rel", C.c_double), ("use_graph", C.c_int32), ("check_every", C.c_int32),
-                ("resume", C.c_int32), ("cg_precond", C.c_int32), ("subproblem", C.c_int32)]
+                ("resume", C.c_int32), ("cg_precond", C.c_int32), ("subproblem", C.c_int32),
+                ("trace", C.c_int32)]
 
 
 class PgdParams(C.Structure):
@@ -166,6 +167,8 @@ def lib():
     L.rpt_admm_bb_solve_learned.argtypes = [C.c_void_p, C.c_void_p, fp, dp, C.POINTER(AdmmParams), dp,
                                             C.POINTER(_Info), C.POINTER(C.c_int32)]
     L.rpt_admm_bb_solve_learned.restype = C.c_int
+    L.rpt_trace_get.argtypes = [C.c_void_p, dp, C.c_int32, C.POINTER(C.c_int32)]
+    L.rpt_trace_get.restype = C.c_int
     _lib = L
     return L
 
@@ -301,6 +304,18 @@ class Plan:
         by = C.c_double()
         _check(lib().rpt_profile_row_pass(self._h, int(mode), int(reps), C.byref(ms), C.byref(by)))
         return ms.value, by.value
+
+    TRACE_FIELDS = ("iteration", "seconds", "r_prim", "r_dual", "eps_prim", "eps_dual", "step", "cg_steps")
+
+    def trace(self):
+        """Per-iteration record of the last solve run with trace=1, as an array
+        [iterations][8] with columns TRACE_FIELDS."""
+        cnt = C.c_int32()
+        _check(lib().rpt_trace_get(self._h, None, 0, C.byref(cnt)))
+        out = np.empty((cnt.value, 8))
+        if cnt.value:
+            _check(lib().rpt_trace_get(self._h, _dptr(out), cnt.value, C.byref(cnt)))
+        return out
 
     def state_get(self):
         z = np.empty(self.n)

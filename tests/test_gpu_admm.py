@@ -253,3 +253,21 @@ def test_input_errors(rpt):
         # the plan stays usable after errors
         x, info = P.admm_bb_solve()
         assert info["status"] in (0, 1)
+
+
+@pytest.mark.parametrize("use_graph,sub", [(1, 0), (0, 0), (1, 1)])
+def test_trace_records_every_iteration(rpt, use_graph, sub):
+    prob = random_problem(27, m=400, n=40, N=3, mean_row=8.0, ub=6.0)
+    with plan_of(rpt, prob) as P:
+        z, info = P.admm_bb_solve(trace=1, use_graph=use_graph, subproblem=sub)
+        T = P.trace()
+        P.admm_bb_solve()
+        assert P.trace().shape[0] == 0                     # an untraced solve records nothing
+    k = info["iterations"]
+    assert T.shape == (k, 8)
+    np.testing.assert_array_equal(T[:, 0], np.arange(1, k + 1))
+    assert T[0, 1] == 0.0 and np.all(np.diff(T[:, 1]) >= 0)
+    assert T[-1, 2] == pytest.approx(info["r_prim"]) and T[-1, 3] == pytest.approx(info["r_dual"])
+    assert T[-1, 4] == pytest.approx(info["eps_prim"]) and T[-1, 5] == pytest.approx(info["eps_dual"])
+    assert T[-1, 2] <= T[-1, 4] and T[-1, 3] <= T[-1, 5]   # the stopping rule held at the last entry
+    assert np.all(np.diff(T[:, 7]) >= 0) and (T[-1, 7] == info["inner"] or sub == 1)
