@@ -40,7 +40,25 @@ __device__ __forceinline__ double sum_partials(const DevPlan& P, const float* __
   float sum = 0.f, c = 0.f;
   const int cnt = __ldcg(&P.slot_count[s]);
   const int* list = P.slot_list + (size_t)s * P.slot_cap;
-  for (int k = 0; k < cnt; ++k) {
+  // eight slots at a time: all loads of a batch are issued before the
+  // (order-preserving) compensated sums consume them
+  int k = 0;
+  for (; k + 8 <= cnt; k += 8) {
+    int idx[8];
+    float v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) idx[u] = __ldcg(&list[k + u]);
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v[u] = __ldcg(part + (size_t)idx[u] * P.n_pad + j);
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      float t, e;
+      two_sum(sum, v[u], t, e);
+      sum = t;
+      c += e;
+    }
+  }
+  for (; k < cnt; ++k) {
     const float v = __ldcg(part + (size_t)__ldcg(&list[k]) * P.n_pad + j);
     float t, e;
     two_sum(sum, v, t, e);
