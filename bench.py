@@ -132,7 +132,7 @@ def cpu_baseline(prob, budget_s=20.0):
     while time.perf_counter() - t1 < budget_s and k < 50:
         k += 1
         res = admm_bb(W, rho=rho, eps_abs=1e-4, eps_rel=1e-4, max_iter=k, subproblem="cg",
-                      cg_theta=0.3, cg_eta0=1e-2, cg_floor_rel=1e-6, cg_max=50, cg_precond="jacobi")
+                      cg_theta=0.15, cg_eta0=1e-2, cg_floor_rel=1e-6, cg_max=50, cg_precond="jacobi")
         if time.perf_counter() - t1 > budget_s / 2:
             break
     t_sample = res["seconds"]

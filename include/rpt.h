@@ -104,7 +104,7 @@ typedef struct {
   double  bb_kappa;       /* guard factor for RPT_BB_GUARDED (default 10) */
   int32_t z_mode;         /* RPT_Z_STD (default) | RPT_Z_LIT */
   int32_t cg_max;         /* CG iterations per subproblem solve (default 50) */
-  double  cg_theta;       /* CG stops at ||c_s - B_s x|| <= theta (rho/2) max(r_prim, eps_prim)/sqrt(N) (default 0.3) */
+  double  cg_theta;       /* CG stops at ||c_s - B_s x|| <= theta (rho/2) max(r_prim, eps_prim)/sqrt(N) (default 0.15) */
   double  cg_eta0;        /* first ADMM iteration: CG stops at ||r|| <= eta0 ||r_0|| (default 1e-2) */
   double  cg_floor_rel;   /* never ask CG for ||r|| below floor_rel * ||r_0|| of the first solve (default 1e-6) */
   int32_t use_graph;      /* 1 (default): one CUDA graph with device-side loops; 0: host-driven loop */

@@ -71,7 +71,7 @@ def _cg(W, s, rho, c, x, tol_fn, kmax, minv=None):
 
 def admm_bb(prob_or_w, rho=None, eps_abs=1e-4, eps_rel=1e-4, max_iter=1000,
             subproblem="chol", bb="paper", zmode="std", bb_kappa=10.0,
-            z0=None, y0=None, tol_obj=math.inf, cg_theta=0.3, cg_eta0=1e-2,
+            z0=None, y0=None, tol_obj=math.inf, cg_theta=0.15, cg_eta0=1e-2,
             cg_floor_rel=0.0, cg_max=200, cg_precond="jacobi", record=False, record_f=False):
     W = prob_or_w if isinstance(prob_or_w, Weighted) else Weighted(prob_or_w)
     N, n = W.N, W.n

@@ -1000,7 +1000,7 @@ void rpt_admm_params_default(rpt_admm_params* p) {
   p->bb_kappa = 10.0;
   p->z_mode = RPT_Z_STD;
   p->cg_max = 50;
-  p->cg_theta = 0.3;
+  p->cg_theta = 0.15;
   p->cg_eta0 = 1e-2;
   p->cg_floor_rel = 1e-6;
   p->use_graph = 1;

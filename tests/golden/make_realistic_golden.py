@@ -5,7 +5,7 @@ Workload: synthetic.config_realistic(seed=0) (128x128x96 grid, ~299k voxels,
   * the exact box-constrained optimum f* of the plan (oracle.exact.box_qp_newton
     on the dense normal equations) with its optimality certificates;
   * ADMM-BB with CG subproblems and the library's default parameters
-    (rho = default rule, eps = 1e-4, theta 0.3, eta0 1e-2, floor 1e-6, at most
+    (rho = default rule, eps = 1e-4, theta 0.15, eta0 1e-2, floor 1e-6, at most
     50 steps, Jacobi): iterations and CG steps to tolerance and the objective,
     used to extrapolate the CPU timing of a bounded sample;
   * the paper's ADMM-BB with cached Cholesky subproblems (App. A) at eps = 1e-4;
@@ -50,7 +50,7 @@ def main():
     res["f_star"] = W.f(xs)
     save()
     rc = admm_bb(W, rho=rho0, eps_abs=1e-4, eps_rel=1e-4, max_iter=20000, subproblem="cg",
-                 cg_theta=0.3, cg_eta0=1e-2, cg_floor_rel=1e-6, cg_max=50, cg_precond="jacobi")
+                 cg_theta=0.15, cg_eta0=1e-2, cg_floor_rel=1e-6, cg_max=50, cg_precond="jacobi")
     res["admm_cg"] = dict(eps=1e-4, iterations=rc["iterations"], cg_iterations=rc["cg_iterations"],
                           status=rc["status"], f=rc["f"], seconds=rc["seconds"])
     save()

@@ -125,7 +125,7 @@ def test_time_to_tolerance_setting_matches_oracle(rpt, tiny_plain):
     prob, W, xs, fstar = tiny_plain
     rho = 0.3 * default_rho(W)
     ref = admm_bb(W, rho=rho, eps_abs=1e-4, eps_rel=1e-4, max_iter=5000, subproblem="cg",
-                  cg_theta=0.3, cg_eta0=1e-2, cg_floor_rel=1e-6, cg_precond="jacobi")
+                  cg_theta=0.15, cg_eta0=1e-2, cg_floor_rel=1e-6, cg_precond="jacobi")
     with plan_of(rpt, prob) as P:
         z, info = P.admm_bb_solve(rho=rho)
     assert info["status"] == 0
