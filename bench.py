@@ -30,6 +30,19 @@ METRIC = "ADMM-BB time-to-tolerance (s), SpMV GB/s vs HBM peak: plain vs mixed/l
 WORKLOAD = "realistic: 128x128x96 grid, 299k voxels, 5000 spots, 13 scenarios, ~2000 nnz/spot, F32+int32 CSR"
 
 
+def max_over_ranks(value, world, device=None):
+    """The largest of every rank's value (a step time is max-reduced across the
+    job); world 1: the value itself.  device: where the reduction tensor lives
+    (the rank's GPU with NCCL, None for the CPU with gloo)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def _env_int(k, d):
     try:
         return int(os.environ.get(k, d))
@@ -302,10 +315,7 @@ def main():
     clocks = sampler.stop()
     ms_total = e0.elapsed_time(e1)
     ms_step = ms_total / args.steps
-    if world > 1:
-        t = torch.tensor([ms_step], device=f"cuda:{dev}")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
+    ms_step = max_over_ranks(ms_step, world, f"cuda:{dev}")
     iters = statistics.mean(i["iterations"] for i in infos)
     kernels = int(sum(i["kernels"] for i in infos))
 
