@@ -1,7 +1,7 @@
 """Learned warm start (rpt_mlp_*): the network's forward pass and gradient on
 the GPU against the float64 oracle (oracle/mlp.py), training, and what the
 trained network gains over cold-start ADMM-BB on held-out objective weights,
-with the oracle's objective and optimality certificate as the judge."""
+with the oracle's objective and optimality certificate deciding."""
 import numpy as np
 import pytest
 
@@ -82,7 +82,7 @@ def test_learned_warm_start_gains_over_cold_start(rpt):
                 xc, ic = P.admm_bb_solve()
                 xw, iw, used = rpt.admm_bb_solve_learned(P, net, f, prob.ub)
             assert ic["status"] == 0 and iw["status"] == 0
-            # the oracle judges both results: same objective to the tolerance, near-optimal
+            # the oracle checks both results: same objective to the tolerance, near-optimal
             fc, fw = W.f(xc), W.f(xw)
             assert abs(fw - fc) / fc <= 1e-3, (fw, fc)
             assert certificates(W, xw)["pg"] < 1e-2
