@@ -166,14 +166,23 @@ def cpu_baseline(prob, budget_s=20.0):
 
 
 def run_batch(args, rpt, dev, stream, peak):
-    """Batched form: four plans of uneven size over 49 scenarios solved one by
-    one, then as one block-diagonal plan (one persistent row pass over all of
-    them, ring configuration picked by the autotuner)."""
+    """Batched form: plans of uneven size solved one by one, then as one
+    block-diagonal plan (one persistent row pass over all of them, ring
+    configuration picked by the autotuner).  'large': four plans over 49
+    scenarios; 'small': eight plans over 13 scenarios, each too small to fill
+    the GPU alone."""
     import numpy as np
     import torch
-    from synthetic import config_batch, block_diagonal
+    from synthetic import config_batch, block_diagonal, BATCH_SIZES_SMALL, scenario_set_13
     t0 = time.perf_counter()
-    probs = config_batch(args.seed, workers=args.workers)
+    if args.batch == "small":
+        probs = config_batch(args.seed, workers=args.workers, nnz_per_col=1500.0,
+                             scenarios=scenario_set_13(), sizes=BATCH_SIZES_SMALL)
+        label = ("8 plans (voxels, spots) = 12k/250 ... 54k/950 in steps of 6k/100; 13 scenarios each; "
+                 "~1500 nnz/spot")
+    else:
+        probs = config_batch(args.seed, workers=args.workers)
+        label = "4 plans (voxels, spots) = 100k/2k, 170k/3k, 230k/4k, 300k/5k; 49 scenarios each; ~1700 nnz/spot"
     gen_s = time.perf_counter() - t0
     params = rpt.admm_params()
 
@@ -204,8 +213,7 @@ def run_batch(args, rpt, dev, stream, peak):
     z, info, t = timed_solve(P)
     ms, by = P.profile_row_pass(0, reps=10)
     P.close()
-    return {"workload": "4 plans (voxels, spots) = 100k/2k, 170k/3k, 230k/4k, 300k/5k; 49 scenarios each; "
-                        "~1700 nnz/spot", "generate_s": round(gen_s, 1),
+    return {"workload": label, "generate_s": round(gen_s, 1),
             "one_by_one": seq, "one_by_one_solve_s": sum(q["solve_s"] for q in seq),
             "stacked": {"nnz": int(st["nnz"]), "create_s": create_s, "solve_s": t, "iterations": info["iterations"],
                         "row_passes": info["row_passes"], "f": info["f"],
@@ -250,8 +258,9 @@ def main():
     ap.add_argument("--no-pgd", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the reduced-precision storage forms")
     ap.add_argument("--no-chol", action="store_true", help="skip the cached-factor subproblem solver")
-    ap.add_argument("--batch", action="store_true",
-                    help="also run the batched form: 4 plans x 49 scenarios (~9 GB), one stacked plan vs one by one")
+    ap.add_argument("--batch", nargs="?", const="large", default=None, choices=["large", "small"],
+                    help="also run the batched form, one stacked plan vs one by one: 'large' = 4 plans x 49 "
+                         "scenarios (~9 GB), 'small' = 8 small plans x 13 scenarios")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--ref-budget", type=float, default=15.0)
     ap.add_argument("--max-iter", type=int, default=0,

@@ -16,6 +16,7 @@ from .phantom import (  # noqa: F401
     reweighted,
     block_diagonal,
     config_batch,
+    BATCH_SIZES_SMALL,
     sample_weights,
     N_WEIGHT_SLOTS,
 )

@@ -652,13 +652,18 @@ def block_diagonal(problems) -> Problem:
 
 
 BATCH_SIZES = ((100_000, 2000), (170_000, 3000), (230_000, 4000), (300_000, 5000))
+# eight small plans of uneven size over the 13-scenario set: each alone is too
+# small to fill the GPU, so one launch over all of them has room to gain
+BATCH_SIZES_SMALL = ((12_000, 250), (18_000, 350), (24_000, 450), (30_000, 550),
+                     (36_000, 650), (42_000, 750), (48_000, 850), (54_000, 950))
 
 
 def config_batch(seed: int = 0, workers: int = 8, nnz_per_col: float = 1700.0, scenarios=None,
                  sizes=BATCH_SIZES):
-    """Four plans of uneven size (voxels, spots) = 100k/2k, 170k/3k, 230k/4k,
-    300k/5k, each over the 49-scenario set, realistic geometry scaled to the
-    voxel count, about nnz_per_col entries per spot column.  Returns the list."""
+    """Plans of uneven size (voxels, spots), by default four (100k/2k,
+    170k/3k, 230k/4k, 300k/5k) over the 49-scenario set; realistic geometry
+    scaled to each voxel count, about nnz_per_col entries per spot column.
+    Returns the list."""
     scen = scenarios if scenarios is not None else scenario_set_49()
     out = []
     for k, (m, n) in enumerate(sizes):
