@@ -10,6 +10,8 @@ z in the box.  Each iteration k:
   3. y_s^{k+1} = y_s^k + step_k (x_s^{k+1} - z^{k+1})                   (Eq. 7)
      step_k = BB value beta^k = -dd'dy/||dd||^2 if it is > 0, else rho   (Eq. 8)
      dd = d^{k+1} - d^k with d = x - 1(x)z, dy = y^k - y^{k-1}
+     (bb_per_scenario: the same rule applied to each scenario's own blocks
+     dd_s, dy_s, giving one step beta_s^k per scenario)
   4. stop when ||r_prim|| <= eps_prim and ||r_dual|| <= eps_dual          (Eq. 9)
      r_prim = x^{k+1} - 1(x)z^{k+1},  r_dual = 1(x) rho (z^{k+1} - z^k),
      eps_prim = eps_abs sqrt(Nn) + eps_rel max(||x||, sqrt(N)||z||),
@@ -19,7 +21,10 @@ Optionally combined (AND) with a relative objective-change test (Sec. 2.3).
 Readings (the paper is silent): z^0 = P(z0) (default 0), y^0 = y0 (default 0),
 x_s^0 = z^0; the BB step needs y^{k-1}, so the first iteration uses rho; the
 step must be finite and > 0, else rho; bb="guarded" clamps it to
-[rho/kappa, kappa*rho]; bb="off" always uses rho.
+[rho/kappa, kappa*rho]; bb="off" always uses rho.  Eq. 8 is written over the
+concatenated vectors, so one global step is the default; per-scenario steps
+are an option (a reading, not the paper's rule).  The returned "step" is the
+global step, or the mean of the per-scenario steps ("steps" holds them all).
 
 The subproblem is solved either with a Cholesky factor of B_s computed once
 (App. A, the paper's method) or by conjugate gradients warm-started from
@@ -72,7 +77,8 @@ def _cg(W, s, rho, c, x, tol_fn, kmax, minv=None):
 def admm_bb(prob_or_w, rho=None, eps_abs=1e-4, eps_rel=1e-4, max_iter=1000,
             subproblem="chol", bb="paper", zmode="std", bb_kappa=10.0,
             z0=None, y0=None, tol_obj=math.inf, cg_theta=0.15, cg_eta0=1e-2,
-            cg_floor_rel=0.0, cg_max=200, cg_precond="jacobi", record=False, record_f=False):
+            cg_floor_rel=0.0, cg_max=200, cg_precond="jacobi", record=False, record_f=False,
+            bb_per_scenario=False):
     W = prob_or_w if isinstance(prob_or_w, Weighted) else Weighted(prob_or_w)
     N, n = W.N, W.n
     if rho is None:
@@ -100,6 +106,7 @@ def admm_bb(prob_or_w, rho=None, eps_abs=1e-4, eps_rel=1e-4, max_iter=1000,
     cg_total = 0
     it = 0
     step = rho
+    steps = np.full(N, rho)
     for k in range(max_iter):
         # 1. scenario subproblems
         xn = np.empty_like(x)
@@ -127,18 +134,28 @@ def admm_bb(prob_or_w, rho=None, eps_abs=1e-4, eps_rel=1e-4, max_iter=1000,
             raise ValueError(zmode)
         # 3. BB step and dual update
         d = xn - zn[None, :]
-        step = rho
-        if bb != "off" and y_prev is not None:
-            dd = (d - d_prev).ravel()
-            dy = (y - y_prev).ravel()
-            den = float(dd @ dd)
-            if den > 0.0:
-                beta = -float(dd @ dy) / den
-                if math.isfinite(beta) and beta > 0.0:
-                    step = beta
-                    if bb == "guarded":
-                        step = min(max(step, rho / bb_kappa), bb_kappa * rho)
-        yn = y + step * d
+
+        def bb_step(dd, dy):
+            st = rho
+            if bb != "off" and y_prev is not None:
+                den = float(dd @ dd)
+                if den > 0.0:
+                    beta = -float(dd @ dy) / den
+                    if math.isfinite(beta) and beta > 0.0:
+                        st = beta
+                        if bb == "guarded":
+                            st = min(max(st, rho / bb_kappa), bb_kappa * rho)
+            return st
+
+        if bb_per_scenario:
+            steps = np.array([bb_step(d[s] - d_prev[s], None if y_prev is None else y[s] - y_prev[s])
+                              for s in range(N)])
+            step = float(np.mean(steps))
+            yn = y + steps[:, None] * d
+        else:
+            step = bb_step((d - d_prev).ravel(), None if y_prev is None else (y - y_prev).ravel())
+            steps = np.full(N, step)
+            yn = y + step * d
         # 4. residuals and stopping rule
         r_prim = float(np.linalg.norm(d))
         r_dual = math.sqrt(N) * rho * float(np.linalg.norm(zn - z))
@@ -164,7 +181,7 @@ def admm_bb(prob_or_w, rho=None, eps_abs=1e-4, eps_rel=1e-4, max_iter=1000,
         if ok:
             status = "converged"
             break
-    return dict(z=z, x=x, y=y, iterations=it, status=status, rho=rho, step=step,
+    return dict(z=z, x=x, y=y, iterations=it, status=status, rho=rho, step=step, steps=steps,
                 r_prim=r_prim, r_dual=r_dual, eps_prim=eps_prim, eps_dual=eps_dual,
                 cg_iterations=cg_total, f=W.f(z), history=hist,
                 seconds=time.perf_counter() - t0)

@@ -197,6 +197,53 @@ def test_hand_worked_iterates():
     assert r["f"] == pytest.approx(g["optimum"]["f"], rel=1e-10)
 
 
+def test_hand_worked_per_scenario_bb_iterates():
+    """Eq. 8 applied per scenario on a 2-scenario example whose bound binds, so
+    that the two scenarios' steps differ (4 and 10 at k = 2)."""
+    g = json.load(open(os.path.join(GOLD, "hand_admm_bb_scen_2x1.json")))
+    pr = g["problem"]
+    W = Weighted(from_dense(pr["A"], pr["w"], pr["p"], pr["lb"], pr["ub"]))
+    rho = g["params"]["rho"]
+    for k, it in enumerate(g["iterates"], start=1):
+        r = admm_bb(W, rho=rho, max_iter=k, eps_abs=0.0, eps_rel=0.0, bb_per_scenario=True)
+        np.testing.assert_allclose(r["x"], it["x"], rtol=1e-14, atol=1e-14)
+        np.testing.assert_allclose(r["z"], it["z"], rtol=1e-14, atol=1e-14)
+        np.testing.assert_allclose(r["y"], it["y"], rtol=1e-13, atol=1e-13)
+        np.testing.assert_allclose(r["steps"], it["steps"], rtol=1e-12)
+        assert r["step"] == pytest.approx(float(np.mean(it["steps"])), rel=1e-12)
+        if "r_prim" in it:
+            assert r["r_prim"] == pytest.approx(it["r_prim"], rel=1e-14, abs=1e-15)
+            assert r["r_dual"] == pytest.approx(it["r_dual"], rel=1e-14, abs=1e-15)
+    r = admm_bb(W, rho=rho, max_iter=100, eps_abs=1e-12, eps_rel=1e-12, bb_per_scenario=True)
+    assert r["status"] == "converged" and r["iterations"] == 4
+    assert r["f"] == pytest.approx(g["optimum"]["f"], rel=1e-14)
+    # the global rule differs at k = 2 on the same example
+    rg = admm_bb(W, rho=rho, max_iter=3, eps_abs=0.0, eps_rel=0.0)
+    assert rg["step"] == pytest.approx(0.29624 / 0.067124, rel=1e-12)
+
+
+@pytest.mark.parametrize("N,bb", [(1, "paper"), (1, "guarded"), (3, "off")])
+def test_per_scenario_bb_reduces_to_global(N, bb):
+    """With one scenario, or with the BB step off, the per-scenario rule is the global one."""
+    P = _tiny_dense(8, m=15, n=5, N=N, lb=0.0, ub=1.0, sw=True)
+    W = Weighted(P)
+    for k in (1, 2, 5, 20):
+        a = admm_bb(W, rho=1.1, max_iter=k, eps_abs=0.0, eps_rel=0.0, bb=bb)
+        b = admm_bb(W, rho=1.1, max_iter=k, eps_abs=0.0, eps_rel=0.0, bb=bb, bb_per_scenario=True)
+        np.testing.assert_allclose(b["y"], a["y"], rtol=1e-12, atol=1e-14)
+        np.testing.assert_allclose(b["z"], a["z"], rtol=1e-12, atol=1e-14)
+
+
+def test_per_scenario_bb_reaches_the_optimum():
+    P = _tiny_dense(9, m=16, n=6, N=4, lb=0.0, ub=0.8, sw=True)
+    W = Weighted(P)
+    xs = kkt_bruteforce(W)
+    r = admm_bb(W, eps_abs=1e-12, eps_rel=1e-12, max_iter=20000, bb_per_scenario=True)
+    assert r["status"] == "converged"
+    assert r["f"] == pytest.approx(W.f(xs), rel=1e-10)
+    assert len(set(np.round(r["steps"], 12))) > 1          # the steps did differ
+
+
 def test_bb_off_equals_textbook_scaled_consensus_admm():
     P = _tiny_dense(5, m=13, n=5, N=3, lb=0.0, ub=1.2, sw=True)
     W = Weighted(P)
