@@ -117,6 +117,10 @@ typedef struct {
                              then x_s = B_s^{-1} c_s each iteration (4 n^2 N bytes of device memory,
                              plus as much again while it is formed) */
   int32_t trace;          /* 1: record one entry per iteration (see rpt_trace_get); default 0 */
+  int32_t bb_per_scenario;/* 0 (default): one dual step over the concatenated vectors (Eq. 8 as
+                             written); 1: Eq. 8 applied to each scenario's own blocks dd_s, dy_s,
+                             one step beta_s per scenario (same bb_mode rules per scenario);
+                             rpt_solve_info.step then reports the mean of the beta_s */
 } rpt_admm_params;
 
 #define RPT_SUB_CG   0

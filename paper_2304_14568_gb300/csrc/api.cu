@@ -729,6 +729,7 @@ int create_plan(const rpt_problem* pr, const rpt_device_opts* opts, rpt_plan** o
   P->aprev = A.get<double>(N);
   P->cgi = A.get<int>(N);
   P->beta = A.get<double>(N);
+  P->bb_step = A.get<double>(N);
   P->act = A.get<int>(N);
   P->act_next = A.get<int>(N);
   P->cgcnt = A.get<int>(N);
@@ -1009,6 +1010,7 @@ void rpt_admm_params_default(rpt_admm_params* p) {
   p->cg_precond = 1;
   p->subproblem = RPT_SUB_CG;
   p->trace = 0;
+  p->bb_per_scenario = 0;
 }
 
 void rpt_pgd_params_default(rpt_pgd_params* p) {

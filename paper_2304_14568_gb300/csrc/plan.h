@@ -33,6 +33,10 @@ struct Ctl {
   double* trace;
   int trace_cap, trace_on;
   unsigned long long t_start;      // %globaltimer at the first iteration (trace time base)
+  // per-scenario dual steps (rpt_admm_params.bb_per_scenario): [N], each holding the
+  // step of the scenario's last dual update until the next BB computation replaces it
+  double* step_s;
+  int bb_scen, pad4;
 };
 
 // trace entry: iteration, seconds since the solve started, r_prim, r_dual,
@@ -63,6 +67,7 @@ struct Plan {
   double *w = nullptr, *q = nullptr, *dinv = nullptr;   // CG: B u, B p, M^{-1}
   float *diag = nullptr;          // [N][n] diag(A~_s^T A~_s)
   double *gam = nullptr, *tol = nullptr, *r0n = nullptr, *alpha = nullptr, *beta = nullptr;
+  double *bb_step = nullptr;      // [N] per-scenario ADMM dual steps
   double *gprev = nullptr, *aprev = nullptr;
   int *act = nullptr, *act_next = nullptr, *cgcnt = nullptr, *cgi = nullptr;
   int *err = nullptr;             // device error word of the row passes

@@ -383,10 +383,37 @@ __global__ void k_admm_d(DevPlan P, Ctl* C, const double* __restrict__ x,
   if (!last_block(&C->cnt_d, gridDim.x * gridDim.y)) return;
   double S[4];
   last_block_sums<4>(vpart + (size_t)nchunk * 8, gridDim.x * gridDim.y, 8, 0, S, sh);
+  const double rho = C->rho;
+  const bool use_bb = C->bb_mode != 2 && C->have_prev;
+  if (C->bb_scen) {
+    // Eq. 8 on scenario s's own blocks: its partial sums in chunk order, and
+    // dy_s = step_s d_prev_s with step_s the scenario's last dual step
+    for (int s = threadIdx.x; s < P.N; s += blockDim.x) {
+      const double* vp = vpart + (size_t)(nchunk + s * nchunk) * 8;
+      double a = 0.0, b = 0.0;
+      for (int c = 0; c < nchunk; ++c) {
+        a += __ldcg(&vp[(size_t)c * 8 + 0]);
+        b += __ldcg(&vp[(size_t)c * 8 + 1]);
+      }
+      double st = rho;
+      if (use_bb && b > 0.0) {
+        const double bb = -C->step_s[s] * a / b;
+        if (isfinite(bb) && bb > 0.0) {
+          st = bb;
+          if (C->bb_mode == 1) st = fmin(fmax(st, rho / C->bb_kappa), C->bb_kappa * rho);
+        }
+      }
+      C->step_s[s] = st;
+    }
+    __syncthreads();
+  }
   if (threadIdx.x == 0) {
-    const double rho = C->rho;
     double step = rho;
-    if (C->bb_mode != 2 && C->have_prev && S[1] > 0.0) {
+    if (C->bb_scen) {
+      double acc = 0.0;
+      for (int s = 0; s < P.N; ++s) acc += C->step_s[s];
+      step = acc / (double)P.N;
+    } else if (use_bb && S[1] > 0.0) {
       const double bb = -C->step_prev * S[0] / S[1];
       if (isfinite(bb) && bb > 0.0) {
         step = bb;
@@ -410,7 +437,7 @@ __global__ void k_admm_y(DevPlan P, Ctl* C, const double* __restrict__ x, double
                          int use_cond) {
   __shared__ double sh[32];
   const int s = blockIdx.y, j = blockIdx.x * VT + threadIdx.x;
-  const double step = __ldcg(&C->step);
+  const double step = C->bb_scen ? __ldcg(&C->step_s[s]) : __ldcg(&C->step);
   double v[1] = {0.0};
   if (j < P.n) {
     const size_t o = (size_t)s * P.n + j;
@@ -449,12 +476,12 @@ __global__ void k_admm_y(DevPlan P, Ctl* C, const double* __restrict__ x, double
       e[3] = C->r_dual;
       e[4] = C->eps_prim;
       e[5] = C->eps_dual;
-      e[6] = step;
+      e[6] = C->step;
       e[7] = (double)C->cg_total;
     }
     C->k += 1;
     C->have_prev = 1;
-    C->step_prev = step;
+    C->step_prev = C->step;
     C->first = 0;
     if (!(isfinite(C->r_prim) && isfinite(C->r_dual) && isfinite(Y))) C->diverged = 1;
     C->status = conv;
@@ -989,6 +1016,7 @@ int admm_solve_impl(Plan* P, const rpt_admm_params* prm, const double* z0, const
   }
   if (prm->max_iter < 1 || prm->cg_max < 0 || prm->eps_abs < 0 || prm->eps_rel < 0 ||
       prm->bb_mode < 0 || prm->bb_mode > 2 || prm->z_mode < 0 || prm->z_mode > 1 ||
+      prm->bb_per_scenario < 0 || prm->bb_per_scenario > 1 ||
       prm->cg_precond < 0 || prm->cg_precond > 1 || prm->subproblem < 0 || prm->subproblem > 1 ||
       !(prm->bb_kappa >= 1.0) || !(prm->cg_theta > 0) || !(prm->cg_eta0 > 0) ||
       !(prm->cg_floor_rel >= 0) || std::isnan(prm->tol_obj)) {
@@ -1043,6 +1071,8 @@ int admm_solve_impl(Plan* P, const rpt_admm_params* prm, const double* z0, const
   c.max_iter = prm->max_iter;
   c.cg_max = prm->cg_max;
   c.bb_mode = prm->bb_mode;
+  c.bb_scen = prm->bb_per_scenario;
+  c.step_s = P->bb_step;
   c.z_mode = prm->z_mode;
   c.precond = prm->cg_precond;
   c.use_obj = use_obj;

@@ -64,7 +64,7 @@ class AdmmParams(C.Structure):
                 ("cg_max", C.c_int32), ("cg_theta", C.c_double), ("cg_eta0", C.c_double),
                 ("cg_floor_rel", C.c_double), ("use_graph", C.c_int32), ("check_every", C.c_int32),
                 ("resume", C.c_int32), ("cg_precond", C.c_int32), ("subproblem", C.c_int32),
-                ("trace", C.c_int32)]
+                ("trace", C.c_int32), ("bb_per_scenario", C.c_int32)]
 
 
 class PgdParams(C.Structure):
