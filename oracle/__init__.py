@@ -22,6 +22,10 @@ against the paper by eye:
                 bfloat16 or FP8-e4m3 codes) as a plain definition
   mlp.py        the learned warm start's network: forward pass, MSE loss and
                 its gradient by the chain rule (float64)
+  dose_constraints.py
+                linear dose limits (maximum, minimum, mean) as extra ADMM
+                blocks (Sec. 4 names them; the splitting is a reading) and the
+                exact constrained optimum by active-set enumeration
 
 Readings where the paper is silent or garbled (each one is a parameter):
   * z-update: z = P(mean_s(x_s + y_s/rho)) by default ("std"); the paper's
@@ -37,3 +41,4 @@ from .pgd import pgd  # noqa: F401
 from .exact import kkt_bruteforce, lsq_box, box_qp_newton, normal_equations, certificates  # noqa: F401
 from .boyd import consensus_admm_scaled  # noqa: F401
 from .quantize import quantised_problem, quantise_values, bf16_round, e4m3_round  # noqa: F401
+from .dose_constraints import DoseConstraint, constraint_rows, admm_bb_constrained, kkt_bruteforce_lin  # noqa: F401
