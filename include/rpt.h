@@ -196,9 +196,11 @@ int rpt_plan_query(const rpt_plan* plan, rpt_plan_stats* out);
 /* ---- solvers ------------------------------------------------------------ */
 
 /* ADMM-BB (Sec. 2.2, Eqs. 5-9; App. A).  Each iteration: x_s-updates
- * (Eq. 6) by warm-started conjugate gradients on B_s x = c_s (App. A) for all
- * scenarios at once; z-update (box projection of the scenario mean); BB
- * dual step (Eq. 8) and dual update (Eq. 7); stopping rule (Eq. 9).
+ * (Eq. 6) on B_s x = c_s (App. A) for all scenarios at once, by warm-started
+ * conjugate gradients (RPT_SUB_CG) or by the cached inverse of B_s
+ * (RPT_SUB_CHOL); z-update (box projection of the scenario mean); BB dual step
+ * (Eq. 8; global, or per scenario with bb_per_scenario) and dual update
+ * (Eq. 7); stopping rule (Eq. 9).
  * z0: [n] initial consensus point (projected onto the box) or NULL for 0.
  * y0: [N*n] initial duals or NULL for 0.  x_out: [n] the final z.
  * info may be NULL.  Returns RPT_OK when Eq. 9 (and the optional tol_obj
