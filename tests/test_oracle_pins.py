@@ -177,6 +177,29 @@ def test_subproblem_normal_equations_vs_stacked_lstsq():
 # the iteration (Sec. 2.2): hand-worked example and textbook ADMM
 # ---------------------------------------------------------------------------
 
+@pytest.mark.parametrize("precond", [False, True])
+def test_cg_subproblem_solver_matches_dense_solve_within_n_steps(precond):
+    """The oracle's (preconditioned) conjugate gradients on B_s x = c: in exact
+    arithmetic CG ends within n steps, so with n = 6 and 8 steps allowed it
+    must reach the dense solve to rounding, from any warm start."""
+    from oracle.admm_bb import _cg
+    P = _tiny_dense(12, m=14, n=6, N=2, sw=True)
+    W = Weighted(P)
+    rho = 0.8
+    rng = np.random.default_rng(3)
+    for s in range(P.N):
+        B = W.B_dense(s, rho)
+        c = rng.normal(size=P.n)
+        x0 = rng.normal(size=P.n)
+        minv = 1.0 / np.diag(B) if precond else None
+        x, its = _cg(W, s, rho, c, x0.copy(), lambda r0: 1e-13 * r0, 8, minv)
+        np.testing.assert_allclose(x, np.linalg.solve(B, c), rtol=1e-10, atol=1e-12)
+        assert 1 <= its <= 8
+        # the warm start counts: starting at the solution needs no step
+        x2, its2 = _cg(W, s, rho, c, np.linalg.solve(B, c), lambda r0: max(1e-13 * r0, 1e-12), 8, minv)
+        assert its2 == 0
+
+
 def test_hand_worked_iterates():
     g = json.load(open(os.path.join(GOLD, "hand_admm_bb_2x1.json")))
     pr = g["problem"]
