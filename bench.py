@@ -223,6 +223,72 @@ def run_batch(args, rpt, dev, stream, peak):
                                  "stages": st["stages"], "configs_timed": st["autotuned"]}}}
 
 
+def run_learned(args, rpt, dev, stream):
+    """Learned warm start against the cold start: an MLP trained (on the GPU,
+    by the library's kernels) on solutions the solver generates over a sweep
+    of structure weights and prescriptions of the 20^3 tiny geometry; held-out
+    settings solved cold and from the network's z0, each to eps = 1e-4, timed
+    with CUDA events (the learned time includes the network's inference)."""
+    import numpy as np
+    import torch
+    from synthetic import config_tiny_plain, reweighted, sample_weights, N_WEIGHT_SLOTS
+
+    def features(sw, d):
+        f = np.zeros(N_WEIGHT_SLOTS + 1, dtype=np.float32)
+        nz = sw > 0
+        f[:N_WEIGHT_SLOTS][nz] = np.log10(sw[nz]) / 2.0
+        f[-1] = (d - 67.5) / 7.5
+        return f
+
+    def timed(fn):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        return out, e0.elapsed_time(e1) / 1e3
+
+    base = config_tiny_plain(args.seed)
+    rng = np.random.default_rng(7)
+    n_train, n_test = 96, 16
+    feats, targets, held = [], [], []
+    t0 = time.perf_counter()
+    for k in range(n_train + n_test):
+        sw, d = sample_weights(rng, base.labels)
+        prob = reweighted(base, sw, d)
+        if k < n_train:
+            with rpt.Plan.from_problem(prob, device=dev, stream=stream.cuda_stream) as P:
+                z, _ = P.admm_bb_solve(eps_abs=1e-6, eps_rel=1e-6, max_iter=20000)
+            feats.append(features(sw, d))
+            targets.append((z / prob.ub).astype(np.float32))
+        else:
+            held.append((prob, features(sw, d)))
+    gen_s = time.perf_counter() - t0
+    X, Y = np.stack(feats), np.stack(targets)
+    rows = []
+    with rpt.Mlp(X.shape[1], 256, 2, base.n, seed=2, device=dev) as net:
+        torch.cuda.synchronize(dev)
+        t1 = time.perf_counter()
+        net.train(X, Y, epochs=400, batch=32, lr=1e-3)
+        torch.cuda.synchronize(dev)
+        train_s = time.perf_counter() - t1
+        for prob, f in held:
+            with rpt.Plan.from_problem(prob, device=dev, stream=stream.cuda_stream) as P:
+                P.admm_bb_solve()                                    # warm-up (graph capture)
+                (_, ic), tc = timed(lambda: P.admm_bb_solve())
+                (_, iw, used), tw = timed(lambda: rpt.admm_bb_solve_learned(P, net, f, prob.ub))
+                rows.append((tc, ic["iterations"], tw, iw["iterations"], bool(used), ic["f"], iw["f"]))
+    return {"workload": "tiny geometry (20^3 grid, 200 spots, 13 scenarios); 96 training and 16 held-out "
+                        "weight settings (structure weights log-uniform in [0.1, 100], prescription in [60, 75] Gy)",
+            "solves_to_generate_s": round(gen_s, 2), "train_s": train_s,
+            "cold_s": statistics.mean(r[0] for r in rows), "cold_iterations": statistics.mean(r[1] for r in rows),
+            "learned_s": statistics.mean(r[2] for r in rows),
+            "learned_iterations": statistics.mean(r[3] for r in rows),
+            "warm_start_used": sum(r[4] for r in rows), "held_out": len(rows),
+            "max_rel_f_diff": max(abs(r[6] - r[5]) / r[5] for r in rows)}
+
+
 def run_reference(args):
     rank = _env_int("RANK", 0)
     if rank != 0:
@@ -259,6 +325,8 @@ def main():
     ap.add_argument("--no-forms", action="store_true", help="skip the reduced-precision storage forms")
     ap.add_argument("--no-chol", action="store_true", help="skip the cached-factor subproblem solver")
     ap.add_argument("--no-variants", action="store_true", help="skip the per-scenario BB step variant")
+    ap.add_argument("--learned", action="store_true",
+                    help="also run the learned warm start against the cold start (tiny geometry, weight sweep)")
     ap.add_argument("--batch", nargs="?", const="large", default=None, choices=["large", "small"],
                     help="also run the batched form, one stacked plan vs one by one: 'large' = 4 plans x 49 "
                          "scenarios (~9 GB), 'small' = 8 small plans x 13 scenarios")
@@ -468,6 +536,9 @@ def main():
 
     if args.batch:
         out["batch"] = run_batch(args, rpt, dev, stream, peak)
+
+    if args.learned:
+        out["learned"] = run_learned(args, rpt, dev, stream)
 
     if not args.no_e2e:
         # end to end through the C ABI with host buffers: upload + solve + result read-back
