@@ -289,6 +289,38 @@ def run_learned(args, rpt, dev, stream):
             "max_rel_f_diff": max(abs(r[6] - r[5]) / r[5] for r in rows)}
 
 
+def run_scenario_sweep(args, rpt, dev, stream, prob):
+    """Time to tolerance against the number of scenarios (the paper's scenario
+    scaling study, Sec. 3.1): the realistic plan restricted to its first N
+    scenarios (nominal first), ADMM-BB to eps = 1e-4 and PGD to the objective
+    ADMM-BB reached, both timed with CUDA events after a warm-up solve."""
+    import torch
+
+    def timed(fn):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        return out, e0.elapsed_time(e1) / 1e3
+
+    rows = []
+    for N in (1, 3, 7, 13):
+        if N > prob.N:
+            break
+        sub = prob.subset_scenarios(range(N))
+        with rpt.Plan.from_problem(sub, device=dev, stream=stream.cuda_stream, autotune=1) as P:
+            P.admm_bb_solve()                                        # warm-up (graph capture)
+            (_, ia), ta = timed(lambda: P.admm_bb_solve())
+            (_, ip), tp = timed(lambda: P.pgd_solve(f_target=ia["f"] * (1 + 1e-6), tol_rel_df=0.0,
+                                                    max_iter=20000))
+            rows.append({"N": N, "admm_s": ta, "admm_iterations": ia["iterations"], "admm_status": ia["status"],
+                         "pgd_s": tp, "pgd_iterations": ip["iterations"], "pgd_status": ip["status"],
+                         "speedup_admm_over_pgd": tp / ta})
+    return rows
+
+
 def run_reference(args):
     rank = _env_int("RANK", 0)
     if rank != 0:
@@ -325,6 +357,8 @@ def main():
     ap.add_argument("--no-forms", action="store_true", help="skip the reduced-precision storage forms")
     ap.add_argument("--no-chol", action="store_true", help="skip the cached-factor subproblem solver")
     ap.add_argument("--no-variants", action="store_true", help="skip the per-scenario BB step variant")
+    ap.add_argument("--scenario-sweep", action="store_true",
+                    help="also time ADMM-BB and PGD on the first 1, 3, 7 and 13 scenarios of the workload")
     ap.add_argument("--learned", action="store_true",
                     help="also run the learned warm start against the cold start (tiny geometry, weight sweep)")
     ap.add_argument("--batch", nargs="?", const="large", default=None, choices=["large", "small"],
@@ -539,6 +573,9 @@ def main():
 
     if args.learned:
         out["learned"] = run_learned(args, rpt, dev, stream)
+
+    if args.scenario_sweep:
+        out["scenario_sweep"] = run_scenario_sweep(args, rpt, dev, stream, prob)
 
     if not args.no_e2e:
         # end to end through the C ABI with host buffers: upload + solve + result read-back
