@@ -134,3 +134,16 @@ def test_weight_sweep_inputs():
         np.testing.assert_array_equal(q.voxel_w, sw[prob.labels])
         np.testing.assert_array_equal(q.presc, np.where(prob.labels == 1, d, 0.0))
         assert q.val is prob.val                      # matrices shared, not copied
+
+
+def test_realistic_workload_matches_the_golden_file():
+    """The full-size workload regenerates exactly what the stored golden values
+    were computed on (entry counts per scenario and the sum of all values)."""
+    import json
+    import os
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "realistic_seed0_oracle.json")))
+    prob = config_realistic(0, workers=8)
+    assert (prob.m, prob.n, prob.N) == (g["m"], g["n"], g["N"])
+    assert prob.nnz() == g["nnz"]
+    value_sum = float(sum(float(np.sum(v.astype(np.float64))) for v in prob.val))
+    assert value_sum == pytest.approx(g["value_sum"], rel=1e-12)
