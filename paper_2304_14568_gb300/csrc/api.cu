@@ -168,14 +168,13 @@ void free_plan(Plan* P) {
   delete P;
 }
 
-// Lanes per row: the smallest power of two G >= g_min with G * kKeep >= len
-// (at most 32).  g_min > 1 keeps the rows that share one warp instruction few:
+// Lanes per row: the smallest power of two G >= min_lanes with G * kKeep >= len
+// (at most 32).  min_lanes > 1 keeps the rows that share one warp instruction few:
 // lanes of different rows can hit the same spot column in the same shared-memory
 // atomic, which serialises; short rows (the dose periphery) often do.
 constexpr int kKeep = 8;   // entries per lane held in registers by the row-pass kernels
-int g_min_lanes = 8;
-int lanes_for(int len) {
-  int g = g_min_lanes;
+int lanes_for(int len, int min_lanes) {
+  int g = min_lanes;
   while (g < 32 && g * kKeep < len) g <<= 1;
   return g;
 }
@@ -189,7 +188,9 @@ struct RowLists {
   std::vector<int4> rec;       // {start, c_s w, p, kept-row index}
 };
 
-double row_cost(int len, double per_lane) { return (double)len + per_lane * lanes_for(len); }
+double row_cost(int len, double per_lane, int min_lanes) {
+  return (double)len + per_lane * lanes_for(len, min_lanes);
+}
 
 // Row-length classes of the streaming path (see k_rowpass_stream): lanes per row
 // 8/16/32/32/32 for padded rows of at most 32/64/128/256/any entries.
@@ -206,9 +207,9 @@ int stream_lanes(int len) { return kStreamLanes[stream_class(len)]; }
 // scenario s's chunks.  For the ring, returns false if a single row does not fit
 // a stage; the streaming path takes such a row as a chunk of its own.
 bool build_chunks(const RowLists& R, const std::vector<int64_t>& base, int N, int cmax, int rmax, bool stream,
-                  std::vector<ChunkDesc>* chunks, std::vector<int>* scen_chunk) {
+                  int min_lanes, std::vector<ChunkDesc>* chunks, std::vector<int>* scen_chunk) {
   scen_chunk->assign(N + 1, 0);
-  auto cls = [&](int len) { return stream ? stream_class(len) : lanes_for(len); };
+  auto cls = [&](int len) { return stream ? stream_class(len) : lanes_for(len, min_lanes); };
   for (int s = 0; s < N; ++s) {
     (*scen_chunk)[s] = (int)chunks->size();
     const int4* r = &R.rec[R.rec_base[s]];
@@ -463,8 +464,8 @@ int create_plan(const rpt_problem* pr, const rpt_device_opts* opts, rpt_plan** o
   const int bi = pr->index_width == 16 ? 2 : 4;
   const int bv = pr->value_format == RPT_F32 ? 4 : (pr->value_format == RPT_BF16 ? 2 : 1);
 
-  g_min_lanes = std::min(32, std::max(1, env_int("RPT_MIN_LANES", 8)));
-  g_min_lanes = 1 << (31 - __builtin_clz((unsigned)g_min_lanes));   // power of two
+  int min_lanes = std::min(32, std::max(1, env_int("RPT_MIN_LANES", 8)));
+  min_lanes = 1 << (31 - __builtin_clz((unsigned)min_lanes));   // power of two
   // row path: the caller's choice, else RPT_ROW_PATH from the environment, else
   // the bulk-copy ring when the plan fits it and the register path otherwise
   const int want_path = (opts && opts->row_path) ? opts->row_path : env_int("RPT_ROW_PATH", 0);
@@ -522,7 +523,7 @@ int create_plan(const rpt_problem* pr, const rpt_device_opts* opts, rpt_plan** o
         lv.assign(plen, 0.f);
         std::memcpy(lc.data(), pr->col_idx[s] + a, sizeof(int32_t) * len);
         std::memcpy(lv.data(), pr->val[s] + a, sizeof(float) * len);
-        bank_balance(lc.data(), lv.data(), len, interleave ? stream_lanes(plen) : lanes_for(plen), bb);
+        bank_balance(lc.data(), lv.data(), len, interleave ? stream_lanes(plen) : lanes_for(plen, min_lanes), bb);
         if (!interleave) {
           std::memcpy(&col_h[base[s] + pos], lc.data(), sizeof(int32_t) * plen);
           std::memcpy(&val_h[base[s] + pos], lv.data(), sizeof(float) * plen);
@@ -571,7 +572,7 @@ int create_plan(const rpt_problem* pr, const rpt_device_opts* opts, rpt_plan** o
     dp.stages = 0;
     ctas = 1;
     if (stream_smem_bytes(n_pad, dp.rmax, true) + 1024 <= (size_t)smem_optin)
-      use_stream = build_chunks(R, base, N, dp.cmax, dp.rmax, true, &chunks, &scen_chunk);
+      use_stream = build_chunks(R, base, N, dp.cmax, dp.rmax, true, min_lanes, &chunks, &scen_chunk);
     if (!use_stream) {
       free_plan(P);
       set_error("streaming row path not possible for this plan (shared memory)");
@@ -599,7 +600,7 @@ int create_plan(const rpt_problem* pr, const rpt_device_opts* opts, rpt_plan** o
       rc.cmax = c.x;
       rc.rmax = c.y;
       rc.stages = c.z;
-      if (!build_chunks(R, base, N, rc.cmax, rc.rmax, false, &rc.chunks, &rc.scen_chunk)) continue;
+      if (!build_chunks(R, base, N, rc.cmax, rc.rmax, false, min_lanes, &rc.chunks, &rc.scen_chunk)) continue;
       ring_cfgs.push_back(std::move(rc));
       if (!autotune) break;   // first that fits
     }
@@ -629,7 +630,7 @@ int create_plan(const rpt_problem* pr, const rpt_device_opts* opts, rpt_plan** o
     double total = 0.0;
     for (int s = 0; s < N; ++s) {
       const int4* r = &R.rec[R.rec_base[s]];
-      for (int q = 0; q < R.nrows[s]; ++q) total += row_cost(r[q + 1].x - r[q].x, per_lane);
+      for (int q = 0; q < R.nrows[s]; ++q) total += row_cost(r[q + 1].x - r[q].x, per_lane, min_lanes);
     }
     const double target = std::max(1.0, total / (double)(P->sm_count * ctas));
     for (int s = 0; s < N; ++s) {
@@ -638,18 +639,18 @@ int create_plan(const rpt_problem* pr, const rpt_device_opts* opts, rpt_plan** o
       // runs of equal lanes-per-row, each cut into blocks of about `target` cost
       int q = 0;
       while (q < R.nrows[s]) {
-        const int g0 = lanes_for(r[q + 1].x - r[q].x);
+        const int g0 = lanes_for(r[q + 1].x - r[q].x, min_lanes);
         int q1 = q;
         double run = 0.0;
-        while (q1 < R.nrows[s] && lanes_for(r[q1 + 1].x - r[q1].x) == g0) {
-          run += row_cost(r[q1 + 1].x - r[q1].x, per_lane);
+        while (q1 < R.nrows[s] && lanes_for(r[q1 + 1].x - r[q1].x, min_lanes) == g0) {
+          run += row_cost(r[q1 + 1].x - r[q1].x, per_lane, min_lanes);
           ++q1;
         }
         const int nb = std::max(1, (int)std::lround(run / target));
         double acc = 0.0, goal = run / nb;
         int qb = q;
         for (int k = q; k < q1; ++k) {
-          acc += row_cost(r[k + 1].x - r[k].x, per_lane);
+          acc += row_cost(r[k + 1].x - r[k].x, per_lane, min_lanes);
           if (acc >= goal - 1e-9 && (int)blocks.size() - blk_first[s] < 1 << 30) {
             blocks.push_back(make_int4(s, qb, k + 1, g0));
             qb = k + 1;
@@ -899,7 +900,7 @@ int create_plan(const rpt_problem* pr, const rpt_device_opts* opts, rpt_plan** o
   S.default_rho = 2.0 * (tr / N) / n;
   S.const_term = const_term;
   S.row_path = dp.path == 2 ? 3 : (dp.path == 1 ? 2 : 1);
-  S.min_lanes = g_min_lanes;
+  S.min_lanes = min_lanes;
   S.chunk_entries = dp.path >= 1 ? dp.cmax : 0;
   S.chunk_rows = dp.path >= 1 ? dp.rmax : 0;
   S.stages = dp.path == 1 ? dp.stages : 0;
