@@ -177,6 +177,25 @@ def _dptr(a):
     return None if a is None else a.ctypes.data_as(C.POINTER(C.c_double))
 
 
+def _vec(a, dtype, size, name, at_least=False):
+    """a as a contiguous flat array of `dtype`, or ValueError if it does not
+    hold `size` elements (at least `size` with at_least).  The C ABI takes
+    plain pointers and reads exactly the documented counts, so every length is
+    checked here, before the call."""
+    v = np.ascontiguousarray(a, dtype=dtype).reshape(-1)
+    if (v.size < size) if at_least else (v.size != size):
+        raise ValueError(f"{name}: {v.size} elements, need {'at least ' if at_least else ''}{size}")
+    return v
+
+
+def _rows(a, dtype, cols, name):
+    """a as a contiguous [k, cols] array of `dtype` (one row allowed as 1-D)."""
+    v = np.ascontiguousarray(np.atleast_2d(a), dtype=dtype)
+    if v.ndim != 2 or v.shape[1] != cols:
+        raise ValueError(f"{name}: shape {v.shape}, need [k, {cols}]")
+    return v
+
+
 def _check(rc, allow=(OK,)):
     if rc not in allow:
         raise RptError(rc, lib().rpt_last_error().decode() or lib().rpt_status_string(rc).decode())
@@ -210,14 +229,20 @@ class Plan:
                  lb=None, ub=None, value_format=F32, index_width=32, device=0, stream=None,
                  ctas_per_sm=0, row_path=0, autotune=0):
         L = lib()
-        rp = [np.ascontiguousarray(a, dtype=np.int32) for a in row_ptr]
-        ci = [np.ascontiguousarray(a, dtype=np.int32) for a in col_idx]
-        va = [np.ascontiguousarray(a, dtype=np.float32) for a in val]
-        w = np.ascontiguousarray(voxel_w, dtype=np.float64)
-        p = np.ascontiguousarray(presc, dtype=np.float64)
-        sw = None if scen_weight is None else np.ascontiguousarray(scen_weight, dtype=np.float64)
-        lbv = None if lb is None else np.ascontiguousarray(lb, dtype=np.float64)
-        ubv = None if ub is None else np.ascontiguousarray(ub, dtype=np.float64)
+        m, n, N = int(m), int(n), int(N)
+        if m < 1 or n < 1 or N < 1:
+            raise ValueError("m, n and N must be >= 1")
+        if not (len(row_ptr) == len(col_idx) == len(val) == N):
+            raise ValueError("row_ptr, col_idx and val need one array per scenario")
+        rp = [_vec(a, np.int32, m + 1, f"row_ptr[{s}]") for s, a in enumerate(row_ptr)]
+        nnz = [max(int(a[-1]), 0) for a in rp]
+        ci = [_vec(a, np.int32, k, f"col_idx[{s}]", at_least=True) for s, (a, k) in enumerate(zip(col_idx, nnz))]
+        va = [_vec(a, np.float32, k, f"val[{s}]", at_least=True) for s, (a, k) in enumerate(zip(val, nnz))]
+        w = _vec(voxel_w, np.float64, m, "voxel_w")
+        p = _vec(presc, np.float64, m, "presc")
+        sw = None if scen_weight is None else _vec(scen_weight, np.float64, N, "scen_weight")
+        lbv = None if lb is None else _vec(lb, np.float64, n, "lb")
+        ubv = None if ub is None else _vec(ub, np.float64, n, "ub")
         RP = (C.POINTER(C.c_int32) * N)(*[a.ctypes.data_as(C.POINTER(C.c_int32)) for a in rp])
         CI = (C.POINTER(C.c_int32) * N)(*[a.ctypes.data_as(C.POINTER(C.c_int32)) for a in ci])
         VA = (C.POINTER(C.c_float) * N)(*[a.ctypes.data_as(C.POINTER(C.c_float)) for a in va])
@@ -262,8 +287,8 @@ class Plan:
     def admm_bb_solve(self, params: AdmmParams | None = None, z0=None, y0=None, **kw):
         prm = params if params is not None else admm_params(**kw)
         x = np.empty(self.n)
-        z0a = None if z0 is None else np.ascontiguousarray(z0, dtype=np.float64)
-        y0a = None if y0 is None else np.ascontiguousarray(y0, dtype=np.float64).reshape(-1)
+        z0a = None if z0 is None else _vec(z0, np.float64, self.n, "z0")
+        y0a = None if y0 is None else _vec(y0, np.float64, self.N * self.n, "y0")
         info = _Info()
         rc = lib().rpt_admm_bb_solve(self._h, C.byref(prm), _dptr(z0a), _dptr(y0a), _dptr(x), C.byref(info))
         _check(rc, allow=(OK, NOT_CONVERGED))
@@ -272,28 +297,28 @@ class Plan:
     def pgd_solve(self, params: PgdParams | None = None, x0=None, **kw):
         prm = params if params is not None else pgd_params(**kw)
         x = np.empty(self.n)
-        x0a = None if x0 is None else np.ascontiguousarray(x0, dtype=np.float64)
+        x0a = None if x0 is None else _vec(x0, np.float64, self.n, "x0")
         info = _Info()
         rc = lib().rpt_pgd_solve(self._h, C.byref(prm), _dptr(x0a), _dptr(x), C.byref(info))
         _check(rc, allow=(OK, NOT_CONVERGED))
         return x, info.as_dict()
 
     def objective(self, x, dose=False):
-        xa = np.ascontiguousarray(x, dtype=np.float64)
+        xa = _vec(x, np.float64, self.n, "x")
         f = C.c_double()
         d = np.empty(self.N * self.m) if dose else None
         _check(lib().rpt_objective(self._h, _dptr(xa), C.byref(f), _dptr(d)))
         return (f.value, d.reshape(self.N, self.m)) if dose else f.value
 
     def gradient(self, x):
-        xa = np.ascontiguousarray(x, dtype=np.float64)
+        xa = _vec(x, np.float64, self.n, "x")
         g = np.empty(self.n)
         f = C.c_double()
         _check(lib().rpt_gradient(self._h, _dptr(xa), _dptr(g), C.byref(f)))
         return g, f.value
 
     def apply_normal(self, v, rho=0.0):
-        va = np.ascontiguousarray(v, dtype=np.float64).reshape(-1)
+        va = _vec(v, np.float64, self.N * self.n, "v")
         u = np.empty(self.N * self.n)
         _check(lib().rpt_apply_normal(self._h, _dptr(va), float(rho), _dptr(u)))
         return u.reshape(self.N, self.n)
@@ -325,9 +350,9 @@ class Plan:
         return z, x.reshape(self.N, self.n), y.reshape(self.N, self.n)
 
     def state_set(self, z, x, y):
-        za = np.ascontiguousarray(z, dtype=np.float64)
-        xa = np.ascontiguousarray(x, dtype=np.float64).reshape(-1)
-        ya = np.ascontiguousarray(y, dtype=np.float64).reshape(-1)
+        za = _vec(z, np.float64, self.n, "z")
+        xa = _vec(x, np.float64, self.N * self.n, "x")
+        ya = _vec(y, np.float64, self.N * self.n, "y")
         _check(lib().rpt_state_set(self._h, _dptr(za), _dptr(xa), _dptr(ya)))
 
 
@@ -392,12 +417,14 @@ class Mlp:
         return p
 
     def set_params(self, p):
-        pa = np.ascontiguousarray(p, dtype=np.float32)
+        pa = _vec(p, np.float32, self.param_count(), "params")
         _check(lib().rpt_mlp_set_params(self._h, _fptr(pa)))
 
     def loss_grad(self, X, Y):
-        Xa = np.ascontiguousarray(X, dtype=np.float32)
-        Ya = np.ascontiguousarray(Y, dtype=np.float32)
+        Xa = _rows(X, np.float32, self.n_in, "X")
+        Ya = _rows(Y, np.float32, self.n_out, "Y")
+        if Ya.shape[0] != Xa.shape[0]:
+            raise ValueError("X and Y need the same number of rows")
         loss = C.c_double()
         g = np.empty(self.param_count(), dtype=np.float32)
         _check(lib().rpt_mlp_loss_grad(self._h, _fptr(Xa), _fptr(Ya), int(Xa.shape[0]), C.byref(loss), _fptr(g)))
@@ -405,14 +432,16 @@ class Mlp:
 
     def train(self, X, Y, params: MlpTrainParams | None = None, **kw):
         tp = params if params is not None else mlp_train_params(**kw)
-        Xa = np.ascontiguousarray(X, dtype=np.float32)
-        Ya = np.ascontiguousarray(Y, dtype=np.float32)
+        Xa = _rows(X, np.float32, self.n_in, "X")
+        Ya = _rows(Y, np.float32, self.n_out, "Y")
+        if Ya.shape[0] != Xa.shape[0]:
+            raise ValueError("X and Y need the same number of rows")
         loss = C.c_double()
         _check(lib().rpt_mlp_train(self._h, _fptr(Xa), _fptr(Ya), int(Xa.shape[0]), C.byref(tp), C.byref(loss)))
         return loss.value
 
     def predict(self, X):
-        Xa = np.ascontiguousarray(np.atleast_2d(X), dtype=np.float32)
+        Xa = _rows(X, np.float32, self.n_in, "X")
         Y = np.empty((Xa.shape[0], self.n_out), dtype=np.float32)
         _check(lib().rpt_mlp_predict(self._h, _fptr(Xa), int(Xa.shape[0]), _fptr(Y)))
         return Y
@@ -422,8 +451,8 @@ def admm_bb_solve_learned(plan, mlp, features, zscale, params: AdmmParams | None
     """ADMM-BB warm-started by the network (cold-start fallback); returns
     (x, info, used_warm_start)."""
     prm = params if params is not None else admm_params(**kw)
-    f = np.ascontiguousarray(features, dtype=np.float32)
-    zs = np.ascontiguousarray(zscale, dtype=np.float64)
+    f = _vec(features, np.float32, mlp.n_in, "features")
+    zs = _vec(zscale, np.float64, plan.n, "zscale")
     x = np.empty(plan.n)
     info = _Info()
     used = C.c_int32()

@@ -117,3 +117,35 @@ def test_null_arguments_are_errors(lib):
     assert lib.rpt_pgd_solve(None, None, None, None, None) == rpt.EINVAL
     assert lib.rpt_objective(None, None, None, None) == rpt.EINVAL
     lib.rpt_plan_destroy(None)   # accepted
+
+
+@pytest.mark.parametrize("mutate", [
+    lambda d: d["row_ptr"].__setitem__(0, np.array([0, 2], np.int32)),         # m + 1 entries needed
+    lambda d: d["col_idx"].__setitem__(0, np.array([0, 1], np.int32)),         # fewer than row_ptr[m]
+    lambda d: d["val"].__setitem__(0, np.array([1.0], np.float32)),
+    lambda d: d.update(voxel_w=np.array([1.0])),                               # m weights needed
+    lambda d: d.update(presc=np.array([1.0, 0.0, 3.0])),
+    lambda d: d.update(scen_weight=np.array([1.0, 1.0])),                      # N weights needed
+    lambda d: d.update(lb=np.zeros(3)),                                        # n bounds needed
+    lambda d: d.update(N=2),                                                   # one array per scenario
+])
+def test_binding_checks_array_lengths_before_the_call(lib, mutate):
+    """The C ABI reads exactly the documented counts through plain pointers, so
+    the binding refuses arrays of the wrong length before calling it."""
+    d = _tiny()
+    mutate(d)
+    with pytest.raises(ValueError):
+        rpt.Plan(**d)
+
+
+def test_vector_helper_shapes():
+    v = rpt._vec([[1, 2], [3, 4]], np.float64, 4, "x")
+    assert v.shape == (4,) and v.dtype == np.float64 and v.flags.c_contiguous
+    with pytest.raises(ValueError):
+        rpt._vec(np.zeros(3), np.float64, 4, "x")
+    assert rpt._vec(np.zeros(5), np.float32, 4, "x", at_least=True).size == 5
+    with pytest.raises(ValueError):
+        rpt._vec(np.zeros(3), np.float32, 4, "x", at_least=True)
+    assert rpt._rows(np.zeros(9), np.float32, 9, "X").shape == (1, 9)
+    with pytest.raises(ValueError):
+        rpt._rows(np.zeros((4, 8)), np.float32, 9, "X")
