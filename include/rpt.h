@@ -183,9 +183,10 @@ void rpt_pgd_params_default(rpt_pgd_params* p);
  * partition and the default penalty.  Fails with RPT_EINVAL on malformed CSR
  * (row_ptr not starting at 0 or decreasing, column out of range or not
  * strictly increasing within a row), non-finite or negative val/w/p, lb > ub,
- * non-finite lb (ub may be +inf); RPT_EUNSUPPORTED for n > RPT_MAX_SPOTS or
- * an unsupported format; RPT_ENOMEM/RPT_ECUDA on device failures.  *out is
- * set only on success. */
+ * non-finite lb (ub may be +inf); RPT_EUNSUPPORTED for n > RPT_MAX_SPOTS, an
+ * unsupported format, or a scenario with more than 2^31 - 65 entries once
+ * every row is padded to a multiple of 4; RPT_ENOMEM/RPT_ECUDA on device
+ * failures.  *out is set only on success. */
 int rpt_plan_create(const rpt_problem* prob, const rpt_device_opts* opts, rpt_plan** out);
 
 /* Release a plan and its device memory.  NULL is accepted. */

@@ -3,6 +3,7 @@
 #include <algorithm>
 #include <cstdlib>
 #include <atomic>
+#include <climits>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -418,7 +419,13 @@ int create_plan(const rpt_problem* pr, const rpt_device_opts* opts, rpt_plan** o
     const int32_t* rp = pr->row_ptr[s];
     nnz[s] = rp[m];
     int64_t pn = 0;
-    for (int i = 0; i < m; ++i) pn += (rp[i + 1] - rp[i] + 3) & ~3;
+    for (int i = 0; i < m; ++i) pn += ((int64_t)(rp[i + 1] - rp[i]) + 3) & ~(int64_t)3;
+    // row records hold a scenario's entry offsets as int32
+    if (pn > (int64_t)INT32_MAX - 64) {
+      set_error("scenario " + std::to_string(s) + " has " + std::to_string(pn) +
+                " entries after row padding; at most 2^31 - 65 per scenario are supported");
+      return RPT_EUNSUPPORTED;
+    }
     pnnz[s] = pn;
     base[s] = NNZp;
     NNZ += nnz[s];
