@@ -11,6 +11,7 @@
 #include <thread>
 #include <vector>
 
+#include "layout.h"
 #include "plan.h"
 
 namespace rpt {
@@ -169,132 +170,7 @@ void free_plan(Plan* P) {
   delete P;
 }
 
-// Lanes per row: the smallest power of two G >= min_lanes with G * kKeep >= len
-// (at most 32).  min_lanes > 1 keeps the rows that share one warp instruction few:
-// lanes of different rows can hit the same spot column in the same shared-memory
-// atomic, which serialises; short rows (the dose periphery) often do.
-constexpr int kKeep = 8;   // entries per lane held in registers by the row-pass kernels
-int lanes_for(int len, int min_lanes) {
-  int g = min_lanes;
-  while (g < 32 && g * kKeep < len) g <<= 1;
-  return g;
-}
-
-// Per-scenario row lists (non-empty rows only, sorted by decreasing length):
-// rec_base[s] .. rec_base[s] + nrows[s] are the rows of scenario s, followed by
-// a terminator record holding the scenario's entry count.
-struct RowLists {
-  std::vector<int> rec_base;   // [N+1]
-  std::vector<int> nrows;      // [N]
-  std::vector<int4> rec;       // {start, c_s w, p, kept-row index}
-};
-
-double row_cost(int len, double per_lane, int min_lanes) {
-  return (double)len + per_lane * lanes_for(len, min_lanes);
-}
-
-// Row-length classes of the streaming path (see k_rowpass_stream): lanes per row
-// 8/16/32/32/32 for padded rows of at most 32/64/128/256/any entries.
-int stream_class(int len) {
-  const int q = (len + 3) >> 2;   // quads of the padded row
-  return q <= 8 ? 0 : q <= 16 ? 1 : q <= 32 ? 2 : q <= 64 ? 3 : 4;
-}
-constexpr int kStreamLanes[5] = {8, 16, 32, 32, 32};
-int stream_lanes(int len) { return kStreamLanes[stream_class(len)]; }
-
-// Cut every scenario's row list into chunks of rows of one class (lanes per row
-// for the ring, the streaming class otherwise), at most cmax entries in the
-// 16-entry aligned span and rmax rows.  scen_chunk[s]..scen_chunk[s+1] are
-// scenario s's chunks.  For the ring, returns false if a single row does not fit
-// a stage; the streaming path takes such a row as a chunk of its own.
-bool build_chunks(const RowLists& R, const std::vector<int64_t>& base, int N, int cmax, int rmax, bool stream,
-                  int min_lanes, std::vector<ChunkDesc>* chunks, std::vector<int>* scen_chunk) {
-  scen_chunk->assign(N + 1, 0);
-  auto cls = [&](int len) { return stream ? stream_class(len) : lanes_for(len, min_lanes); };
-  for (int s = 0; s < N; ++s) {
-    (*scen_chunk)[s] = (int)chunks->size();
-    const int4* r = &R.rec[R.rec_base[s]];
-    int q = 0;
-    while (q < R.nrows[s]) {
-      const int g0 = cls(r[q + 1].x - r[q].x);
-      const int64_t g_al = (base[s] + r[q].x) & ~(int64_t)15;
-      int qe = q;
-      while (qe < R.nrows[s] && qe - q < rmax && cls(r[qe + 1].x - r[qe].x) == g0) {
-        const int64_t g_end = (base[s] + r[qe + 1].x + 15) & ~(int64_t)15;
-        if (g_end - g_al > cmax && !(stream && qe == q)) break;
-        ++qe;
-      }
-      if (qe == q) return false;
-      const int64_t n_ent = std::max<int64_t>(16, ((base[s] + r[qe].x + 15) & ~(int64_t)15) - g_al);
-      if (n_ent > (int64_t)1 << 28) return false;
-      ChunkDesc ch{};
-      ch.g_al = g_al;
-      ch.row_begin = q;
-      ch.n_rows = qe - q;
-      ch.n_ent = (int)n_ent;
-      ch.group = stream ? kStreamLanes[g0] : g0;
-      ch.s = s;
-      ch.pad = stream ? g0 : 0;
-      chunks->push_back(ch);
-      q = qe;
-    }
-  }
-  (*scen_chunk)[N] = (int)chunks->size();
-  return true;
-}
-
-// Reorder a row's entries (the order is free: a pass sums over them) so that
-// every aligned group of G consecutive entries, the entries that the G lanes of
-// the row touch in one instruction, falls in as many distinct shared-memory banks
-// (spot column mod 32) as the row allows: each group takes one entry from each of
-// the banks with the most entries left, largest first.  The gather from v_s and
-// the scatter into the accumulator then conflict less.
-struct BankScratch {
-  std::vector<int> order, idx;
-  std::vector<int32_t> c;
-  std::vector<float> v;
-};
-
-void bank_balance(int32_t* col, float* val, int len, int G, BankScratch& S) {
-  if (len <= 1) return;
-  int cnt[32] = {0}, start[33], cur[32];
-  for (int i = 0; i < len; ++i) ++cnt[col[i] & 31];
-  start[0] = 0;
-  for (int b = 0; b < 32; ++b) start[b + 1] = start[b] + cnt[b];
-  S.idx.resize(len);
-  for (int b = 0; b < 32; ++b) cur[b] = start[b];
-  for (int i = 0; i < len; ++i) S.idx[cur[col[i] & 31]++] = i;   // entries by bank, stable
-  for (int b = 0; b < 32; ++b) cur[b] = start[b];
-  S.order.clear();
-  int banks[32];
-  while ((int)S.order.size() < len) {
-    // banks by entries left, largest first
-    int nb = 0;
-    for (int b = 0; b < 32; ++b)
-      if (cur[b] < start[b + 1]) banks[nb++] = b;
-    std::sort(banks, banks + nb, [&](int x, int y) {
-      const int rx = start[x + 1] - cur[x], ry = start[y + 1] - cur[y];
-      return rx != ry ? rx > ry : x < y;
-    });
-    const int want = std::min(G, len - (int)S.order.size());
-    int taken = 0;
-    for (int k = 0; k < nb && taken < want; ++k, ++taken) S.order.push_back(S.idx[cur[banks[k]]++]);
-    // fewer non-empty banks than lanes: fill the group from the largest banks again
-    for (int k = 0; taken < want; k = (k + 1) % nb) {
-      const int b = banks[k];
-      if (cur[b] < start[b + 1]) {
-        S.order.push_back(S.idx[cur[b]++]);
-        ++taken;
-      }
-    }
-  }
-  S.c.assign(col, col + len);
-  S.v.assign(val, val + len);
-  for (int i = 0; i < len; ++i) {
-    col[i] = S.c[S.order[i]];
-    val[i] = S.v[S.order[i]];
-  }
-}
+using namespace layout;   // lanes per row, row lists, bank balance, chunks (layout.h)
 
 // One bulk-copy ring configuration and its chunk lists.
 struct RingCfg {
@@ -498,14 +374,7 @@ int create_plan(const rpt_problem* pr, const rpt_device_opts* opts, rpt_plan** o
   std::vector<int32_t> col_h((size_t)NNZp, 0);
   std::vector<float> val_h((size_t)NNZp, 0.f);
   {
-    // The streaming path reads a row as quads (4 stored entries) with lane sl of
-    // the row's G lanes taking quads sl, sl + G, ...; its rows are stored
-    // lane-interleaved so that, for each quad block b (g_b <= G lanes) and each
-    // component k, the lanes hold consecutive entries of the row:
-    //   stored[4 (b G + sl) + k] = row[4 b G + k g_b + sl].
-    // (Row order is free: the pass sums over the row's entries.)  Consecutive
-    // entries have nearby spot columns, which then fall in different
-    // shared-memory banks for the gather and the scatter.
+    // streaming-path plans store rows lane-interleaved (interleave_row)
     const bool interleave = (want_path == 3);
     auto fill = [&](int s) {
       const int32_t* rp = pr->row_ptr[s];
@@ -535,17 +404,8 @@ int create_plan(const rpt_problem* pr, const rpt_device_opts* opts, rpt_plan** o
           std::memcpy(&col_h[base[s] + pos], lc.data(), sizeof(int32_t) * plen);
           std::memcpy(&val_h[base[s] + pos], lv.data(), sizeof(float) * plen);
         } else {
-          const int G = stream_lanes(plen), nq = plen / 4;
-          for (int b = 0; b * G < nq; ++b) {
-            const int gb = std::min(G, nq - b * G);
-            for (int sl = 0; sl < gb; ++sl)
-              for (int k = 0; k < 4; ++k) {
-                const size_t dst = (size_t)base[s] + pos + 4 * (b * G + sl) + k;
-                const int src = 4 * b * G + k * gb + sl;
-                col_h[dst] = lc[src];
-                val_h[dst] = lv[src];
-              }
-          }
+          interleave_row(lc.data(), lv.data(), plen, stream_lanes(plen), &col_h[base[s] + pos],
+                         &val_h[base[s] + pos]);
         }
         pos += plen;
       }

@@ -32,22 +32,14 @@
 #include <cuda_fp8.h>
 #include <stdint.h>
 
+#include "chunk.h"
+
 namespace rpt {
 
 constexpr int kRowThreads = 512;      // threads of a register-path row-pass CTA
 constexpr int kTmaThreads = 1024;     // threads of a TMA-path CTA (1 producer + 31 consumer warps)
 constexpr int kStrThreads = 512;      // threads of a streaming-path CTA (16 independent warps)
 constexpr int kVecThreads = 256;      // threads of a vector CTA (one column each)
-
-struct ChunkDesc {
-  long long g_al;                     // first copied entry (global index, multiple of 16)
-  int row_begin;                      // first row of the chunk (index in the scenario's row list)
-  int n_rows;                         // rows in the chunk (-1: end-of-work marker)
-  int n_ent;                          // copied entries (multiple of 16)
-  int group;                          // lanes per row (1..32), the same for every row of the chunk
-  int s;                              // scenario
-  int pad;                            // streaming path: row-length class of the chunk's rows
-};
 
 struct DevPlan {
   int m, n, N, m_act, n_pad, nblocks;  // nblocks = partial slots

@@ -1,0 +1,67 @@
+// C entry points over the plan-layout header, built by tests/test_layout_host.py
+// with the host compiler alone (no CUDA runtime, no device), so that the host
+// layout logic of plan creation is tested on the CPU.
+#include <cstdint>
+#include <vector>
+
+#include "layout.h"
+
+using namespace rpt;
+using namespace rpt::layout;
+
+extern "C" {
+
+int shim_lanes_for(int len, int min_lanes) { return lanes_for(len, min_lanes); }
+int shim_stream_class(int len) { return stream_class(len); }
+int shim_stream_lanes(int len) { return stream_lanes(len); }
+
+void shim_bank_balance(int32_t* col, float* val, int len, int G) {
+  BankScratch S;
+  bank_balance(col, val, len, G, S);
+}
+
+void shim_interleave_row(const int32_t* col, const float* val, int plen, int G, int32_t* col_out,
+                         float* val_out) {
+  interleave_row(col, val, plen, G, col_out, val_out);
+}
+
+// Row lists from padded row lengths (scenario-major, nrows[s] rows each, in
+// list order); base[s] = the scenario's first stored entry.  Writes up to cap
+// chunks (fields in separate arrays) and scen_chunk[N+1]; returns the chunk
+// count, -1 when build_chunks refuses, -2 when cap is too small.
+int shim_build_chunks(int N, const int* nrows, const int* plen, const int64_t* base, int cmax, int rmax,
+                      int stream, int min_lanes, int cap, int64_t* g_al, int* row_begin, int* n_rows,
+                      int* n_ent, int* group, int* s_out, int* pad, int* scen_chunk) {
+  RowLists R;
+  R.rec_base.assign(N + 1, 0);
+  R.nrows.assign(nrows, nrows + N);
+  for (int s = 0; s < N; ++s) R.rec_base[s + 1] = R.rec_base[s] + nrows[s] + 1;
+  R.rec.resize(R.rec_base[N]);
+  int k = 0;
+  for (int s = 0; s < N; ++s) {
+    int pos = 0;
+    for (int q = 0; q < nrows[s]; ++q) {
+      R.rec[R.rec_base[s] + q] = int4{pos, 0, 0, q};
+      pos += plen[k++];
+    }
+    R.rec[R.rec_base[s] + nrows[s]] = int4{pos, 0, 0, 0};
+  }
+  std::vector<int64_t> b(base, base + N);
+  std::vector<ChunkDesc> chunks;
+  std::vector<int> sc;
+  if (!build_chunks(R, b, N, cmax, rmax, stream != 0, min_lanes, &chunks, &sc)) return -1;
+  if ((int)chunks.size() > cap) return -2;
+  for (size_t i = 0; i < chunks.size(); ++i) {
+    g_al[i] = chunks[i].g_al;
+    row_begin[i] = chunks[i].row_begin;
+    n_rows[i] = chunks[i].n_rows;
+    n_ent[i] = chunks[i].n_ent;
+    group[i] = chunks[i].group;
+    s_out[i] = chunks[i].s;
+    pad[i] = chunks[i].pad;
+  }
+  for (int s = 0; s <= N; ++s) scen_chunk[s] = sc[s];
+  return (int)chunks.size();
+}
+
+}  // extern "C"
