@@ -194,6 +194,41 @@ void rpt_plan_destroy(rpt_plan* plan);
 
 int rpt_plan_query(const rpt_plan* plan, rpt_plan_stats* out);
 
+/* ---- batched plans: several problems in one plan and one launch per pass ----
+ *
+ * rpt_plans_create_batched stacks n_plans problems with the same scenario count
+ * N into one plan: their voxels and spots are placed side by side, so each
+ * scenario matrix is block-diagonal, the objective (Eq. 2) is the sum of the
+ * problems' objectives and the box is the product of their boxes.  The
+ * stacked optimum is therefore the problems' optima side by side, and one
+ * persistent row pass covers every problem's scenarios.  The problems must
+ * share N, value_format, index_width and scen_weight (all NULL, or equal
+ * values); a NULL lb/ub of one problem means its defaults (0 / +inf).  The
+ * penalty, the BB step and the stopping rule of a solve are shared by all
+ * problems (the default rho is computed on the stacked plan).
+ *   probs: n_plans host pointers, each valid as for rpt_plan_create (checked
+ *          per problem, so a column index is checked against its own problem).
+ *   *out:  one plan holding all problems; destroy it with rpt_plan_destroy.
+ * Errors: RPT_EINVAL for n_plans < 1, NULL arguments, an invalid problem or
+ * problems that differ in N, format, index width or scenario weights;
+ * RPT_EUNSUPPORTED when the stacked plan exceeds a limit of rpt_plan_create
+ * (e.g. the stacked spot count above RPT_MAX_SPOTS); RPT_ENOMEM, RPT_ECUDA. */
+int rpt_plans_create_batched(int32_t n_plans, const rpt_problem* const* probs, const rpt_device_opts* opts,
+                             rpt_plan** out);
+
+/* Problems in a plan and their spot ranges: *n_plans (1 for a plan made by
+ * rpt_plan_create); col_offsets [n_plans + 1] or NULL: problem k owns the
+ * stacked spots col_offsets[k] .. col_offsets[k+1]. */
+int rpt_plan_batch_query(const rpt_plan* plan, int32_t* n_plans, int32_t* col_offsets);
+
+/* ADMM-BB on a batched plan (as rpt_admm_bb_solve, from a cold start), with the
+ * result split per problem: x_out[k] is a host array of problem k's n_k spots.
+ * x_out holds one non-NULL pointer per problem (rpt_plan_batch_query).  The
+ * return value and info are those of the stacked solve; x_out is written on
+ * RPT_OK and RPT_NOT_CONVERGED. */
+int rpt_admm_bb_solve_batched(rpt_plan* plan, const rpt_admm_params* params, double* const* x_out,
+                              rpt_solve_info* info);
+
 /* ---- solvers ------------------------------------------------------------ */
 
 /* ADMM-BB (Sec. 2.2, Eqs. 5-9; App. A).  Each iteration: x_s-updates

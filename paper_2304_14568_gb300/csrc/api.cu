@@ -11,6 +11,7 @@
 #include <thread>
 #include <vector>
 
+#include "batch.h"
 #include "layout.h"
 #include "plan.h"
 
@@ -896,6 +897,96 @@ void rpt_pgd_params_default(rpt_pgd_params* p) {
 
 int rpt_plan_create(const rpt_problem* prob, const rpt_device_opts* opts, rpt_plan** out) {
   return guarded([&] { return create_plan(prob, opts, out); });
+}
+
+int rpt_plans_create_batched(int32_t n_plans, const rpt_problem* const* probs, const rpt_device_opts* opts,
+                             rpt_plan** out) {
+  if (!out || !probs || n_plans < 1) {
+    set_error("n_plans >= 1 and non-null probs and out needed");
+    return RPT_EINVAL;
+  }
+  return guarded([&] {
+    // every problem valid on its own (a column index is checked against its own
+    // problem's spot count, before the stacking offsets hide it)
+    for (int k = 0; k < n_plans; ++k) {
+      const rpt_problem* q = probs[k];
+      if (!q || q->m < 1 || q->n < 1 || q->N < 1 || !q->row_ptr || !q->col_idx || !q->val || !q->voxel_w ||
+          !q->presc) {
+        set_error("problem " + std::to_string(k) + ": null or empty");
+        return RPT_EINVAL;
+      }
+      for (int s = 0; s < q->N; ++s) {
+        if (!q->row_ptr[s] || (q->row_ptr[s][q->m] > 0 && (!q->col_idx[s] || !q->val[s]))) {
+          set_error("problem " + std::to_string(k) + ": null CSR array for scenario " + std::to_string(s));
+          return RPT_EINVAL;
+        }
+        ScenarioCheck chk;
+        check_scenario(q, s, &chk);
+        if (!chk.err.empty()) {
+          set_error("problem " + std::to_string(k) + ": " + chk.err);
+          return RPT_EINVAL;
+        }
+      }
+    }
+    batch::Stacked st;
+    std::string err;
+    int rc = batch::stack_problems(n_plans, probs, &st, &err);
+    if (rc != RPT_OK) {
+      set_error(err);
+      return rc;
+    }
+    rpt_plan* h = nullptr;
+    rc = create_plan(&st.view, opts, &h);
+    if (rc != RPT_OK) return rc;
+    as_plan(h)->batch_col_off = st.col_off;
+    *out = h;
+    return RPT_OK;
+  });
+}
+
+int rpt_plan_batch_query(const rpt_plan* plan, int32_t* n_plans, int32_t* col_offsets) {
+  if (!plan || !n_plans) {
+    set_error("null argument");
+    return RPT_EINVAL;
+  }
+  const Plan* P = reinterpret_cast<const Plan*>(plan);
+  const bool batched = !P->batch_col_off.empty();
+  *n_plans = batched ? (int32_t)P->batch_col_off.size() - 1 : 1;
+  if (col_offsets) {
+    if (batched) {
+      for (size_t k = 0; k < P->batch_col_off.size(); ++k) col_offsets[k] = P->batch_col_off[k];
+    } else {
+      col_offsets[0] = 0;
+      col_offsets[1] = P->dp.n;
+    }
+  }
+  return RPT_OK;
+}
+
+int rpt_admm_bb_solve_batched(rpt_plan* plan, const rpt_admm_params* params, double* const* x_out,
+                              rpt_solve_info* info) {
+  if (!plan || !params || !x_out) {
+    set_error("null argument");
+    return RPT_EINVAL;
+  }
+  Plan* P = as_plan(plan);
+  std::vector<int32_t> off = P->batch_col_off;
+  if (off.empty()) off = {0, P->dp.n};
+  const int nb = (int)off.size() - 1;
+  for (int k = 0; k < nb; ++k)
+    if (!x_out[k]) {
+      set_error("x_out[" + std::to_string(k) + "] is NULL");
+      return RPT_EINVAL;
+    }
+  return guarded([&] {
+    DeviceScope ds(P->device);
+    std::vector<double> x((size_t)P->dp.n);
+    const int rc = admm_solve(P, params, nullptr, nullptr, x.data(), info);
+    if (rc != RPT_OK && rc != RPT_NOT_CONVERGED) return rc;
+    for (int k = 0; k < nb; ++k)
+      std::memcpy(x_out[k], x.data() + off[k], sizeof(double) * (size_t)(off[k + 1] - off[k]));
+    return rc;
+  });
 }
 
 void rpt_plan_destroy(rpt_plan* plan) {

@@ -92,6 +92,7 @@ struct Plan {
   int admm_chol_exec_obj = -1;
 
   std::vector<int32_t> kept_rows; // original row index of each device row
+  std::vector<int32_t> batch_col_off;  // batched plan: problem k owns spots [off[k], off[k+1]); else empty
   double lipschitz = 0.0;         // cached 2 lambda_max, 0 = not computed
   bool state_valid = false;
 

@@ -26,7 +26,8 @@ EXPORTED = [
     "rpt_apply_normal", "rpt_profile_row_pass", "rpt_normal_apply_noalloc", "rpt_state_get", "rpt_state_set", "rpt_status_string", "rpt_last_error",
     "rpt_version", "rpt_mlp_train_params_default", "rpt_mlp_create", "rpt_mlp_destroy", "rpt_mlp_param_count",
     "rpt_mlp_get_params", "rpt_mlp_set_params", "rpt_mlp_loss_grad", "rpt_mlp_train", "rpt_mlp_predict",
-    "rpt_admm_bb_solve_learned", "rpt_trace_get",
+    "rpt_admm_bb_solve_learned", "rpt_trace_get", "rpt_plans_create_batched", "rpt_plan_batch_query",
+    "rpt_admm_bb_solve_batched",
 ]
 
 
@@ -169,6 +170,14 @@ def lib():
     L.rpt_admm_bb_solve_learned.restype = C.c_int
     L.rpt_trace_get.argtypes = [C.c_void_p, dp, C.c_int32, C.POINTER(C.c_int32)]
     L.rpt_trace_get.restype = C.c_int
+    L.rpt_plans_create_batched.argtypes = [C.c_int32, C.POINTER(C.POINTER(_Problem)), C.POINTER(_DeviceOpts),
+                                           C.POINTER(C.c_void_p)]
+    L.rpt_plans_create_batched.restype = C.c_int
+    L.rpt_plan_batch_query.argtypes = [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
+    L.rpt_plan_batch_query.restype = C.c_int
+    L.rpt_admm_bb_solve_batched.argtypes = [C.c_void_p, C.POINTER(AdmmParams), C.POINTER(C.POINTER(C.c_double)),
+                                            C.POINTER(_Info)]
+    L.rpt_admm_bb_solve_batched.restype = C.c_int
     _lib = L
     return L
 
@@ -222,6 +231,37 @@ def pgd_params(**kw) -> PgdParams:
     return p
 
 
+def _problem_struct(m, n, N, row_ptr, col_idx, val, voxel_w, presc, scen_weight=None, lb=None, ub=None,
+                    value_format=F32, index_width=32):
+    """An rpt_problem over contiguous copies of the arrays, after checking every
+    length; returns (struct, arrays to keep alive while the struct is used)."""
+    m, n, N = int(m), int(n), int(N)
+    if m < 1 or n < 1 or N < 1:
+        raise ValueError("m, n and N must be >= 1")
+    if not (len(row_ptr) == len(col_idx) == len(val) == N):
+        raise ValueError("row_ptr, col_idx and val need one array per scenario")
+    rp = [_vec(a, np.int32, m + 1, f"row_ptr[{s}]") for s, a in enumerate(row_ptr)]
+    nnz = [max(int(a[-1]), 0) for a in rp]
+    ci = [_vec(a, np.int32, k, f"col_idx[{s}]", at_least=True) for s, (a, k) in enumerate(zip(col_idx, nnz))]
+    va = [_vec(a, np.float32, k, f"val[{s}]", at_least=True) for s, (a, k) in enumerate(zip(val, nnz))]
+    w = _vec(voxel_w, np.float64, m, "voxel_w")
+    p = _vec(presc, np.float64, m, "presc")
+    sw = None if scen_weight is None else _vec(scen_weight, np.float64, N, "scen_weight")
+    lbv = None if lb is None else _vec(lb, np.float64, n, "lb")
+    ubv = None if ub is None else _vec(ub, np.float64, n, "ub")
+    RP = (C.POINTER(C.c_int32) * N)(*[a.ctypes.data_as(C.POINTER(C.c_int32)) for a in rp])
+    CI = (C.POINTER(C.c_int32) * N)(*[a.ctypes.data_as(C.POINTER(C.c_int32)) for a in ci])
+    VA = (C.POINTER(C.c_float) * N)(*[a.ctypes.data_as(C.POINTER(C.c_float)) for a in va])
+    pr = _Problem(m, n, N, RP, CI, VA, _dptr(w), _dptr(p), _dptr(sw), _dptr(lbv), _dptr(ubv),
+                  value_format, index_width)
+    return pr, (rp, ci, va, w, p, sw, lbv, ubv, RP, CI, VA)
+
+
+def _problem_fields(prob):
+    return (prob.m, prob.n, prob.N, prob.row_ptr, prob.col_idx, prob.val, prob.voxel_w, prob.presc,
+            prob.scen_weight, prob.lb, prob.ub)
+
+
 class Plan:
     """A device-resident plan (rpt_plan_create / rpt_plan_destroy)."""
 
@@ -230,24 +270,8 @@ class Plan:
                  ctas_per_sm=0, row_path=0, autotune=0):
         L = lib()
         m, n, N = int(m), int(n), int(N)
-        if m < 1 or n < 1 or N < 1:
-            raise ValueError("m, n and N must be >= 1")
-        if not (len(row_ptr) == len(col_idx) == len(val) == N):
-            raise ValueError("row_ptr, col_idx and val need one array per scenario")
-        rp = [_vec(a, np.int32, m + 1, f"row_ptr[{s}]") for s, a in enumerate(row_ptr)]
-        nnz = [max(int(a[-1]), 0) for a in rp]
-        ci = [_vec(a, np.int32, k, f"col_idx[{s}]", at_least=True) for s, (a, k) in enumerate(zip(col_idx, nnz))]
-        va = [_vec(a, np.float32, k, f"val[{s}]", at_least=True) for s, (a, k) in enumerate(zip(val, nnz))]
-        w = _vec(voxel_w, np.float64, m, "voxel_w")
-        p = _vec(presc, np.float64, m, "presc")
-        sw = None if scen_weight is None else _vec(scen_weight, np.float64, N, "scen_weight")
-        lbv = None if lb is None else _vec(lb, np.float64, n, "lb")
-        ubv = None if ub is None else _vec(ub, np.float64, n, "ub")
-        RP = (C.POINTER(C.c_int32) * N)(*[a.ctypes.data_as(C.POINTER(C.c_int32)) for a in rp])
-        CI = (C.POINTER(C.c_int32) * N)(*[a.ctypes.data_as(C.POINTER(C.c_int32)) for a in ci])
-        VA = (C.POINTER(C.c_float) * N)(*[a.ctypes.data_as(C.POINTER(C.c_float)) for a in va])
-        pr = _Problem(m, n, N, RP, CI, VA, _dptr(w), _dptr(p), _dptr(sw), _dptr(lbv), _dptr(ubv),
-                      value_format, index_width)
+        pr, _keep = _problem_struct(m, n, N, row_ptr, col_idx, val, voxel_w, presc, scen_weight, lb, ub,
+                                    value_format, index_width)
         opts = _DeviceOpts(device, stream, ctas_per_sm, row_path, autotune)
         h = C.c_void_p()
         _check(L.rpt_plan_create(C.byref(pr), C.byref(opts), C.byref(h)))
@@ -257,8 +281,43 @@ class Plan:
     @classmethod
     def from_problem(cls, prob, **kw):
         """Build from any object with the fields of the C struct rpt_problem."""
-        return cls(prob.m, prob.n, prob.N, prob.row_ptr, prob.col_idx, prob.val, prob.voxel_w,
-                   prob.presc, prob.scen_weight, prob.lb, prob.ub, **kw)
+        return cls(*_problem_fields(prob), **kw)
+
+    @classmethod
+    def batched(cls, problems, value_format=F32, index_width=32, device=0, stream=None, ctas_per_sm=0,
+                row_path=0, autotune=0):
+        """One plan holding several problems side by side (rpt_plans_create_batched)."""
+        L = lib()
+        built = [_problem_struct(*_problem_fields(p), value_format=value_format, index_width=index_width)
+                 for p in problems]
+        arr = (C.POINTER(_Problem) * len(built))(*[C.pointer(pr) for pr, _ in built])
+        opts = _DeviceOpts(device, stream, ctas_per_sm, row_path, autotune)
+        h = C.c_void_p()
+        _check(L.rpt_plans_create_batched(len(built), arr, C.byref(opts), C.byref(h)))
+        self = cls.__new__(cls)
+        self._h = h
+        st = self.stats()
+        self.m, self.n, self.N = st["m"], st["n"], st["N"]
+        return self
+
+    def batch_offsets(self):
+        """Spot ranges of the plan's problems: offsets [n_plans + 1] (rpt_plan_batch_query)."""
+        k = C.c_int32()
+        _check(lib().rpt_plan_batch_query(self._h, C.byref(k), None))
+        off = np.empty(k.value + 1, dtype=np.int32)
+        _check(lib().rpt_plan_batch_query(self._h, C.byref(k), off.ctypes.data_as(C.POINTER(C.c_int32))))
+        return off
+
+    def admm_bb_solve_batched(self, params: AdmmParams | None = None, **kw):
+        """ADMM-BB on the whole plan; returns ([x_k per problem], info)."""
+        prm = params if params is not None else admm_params(**kw)
+        off = self.batch_offsets()
+        xs = [np.empty(int(off[k + 1] - off[k])) for k in range(len(off) - 1)]
+        ptrs = (C.POINTER(C.c_double) * len(xs))(*[_dptr(x) for x in xs])
+        info = _Info()
+        rc = lib().rpt_admm_bb_solve_batched(self._h, C.byref(prm), ptrs, C.byref(info))
+        _check(rc, allow=(OK, NOT_CONVERGED))
+        return xs, info.as_dict()
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
