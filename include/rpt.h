@@ -353,7 +353,13 @@ int rpt_mlp_loss_grad(rpt_mlp* mlp, const float* X, const float* Y, int32_t n, d
 /* Train on n samples; final_loss (may be NULL) = loss of the last minibatch. */
 int rpt_mlp_train(rpt_mlp* mlp, const float* X, const float* Y, int32_t n, const rpt_mlp_train_params* tp,
                   double* final_loss);
+/* Network outputs for n inputs: X [n][n_in] host, Y [n][n_out] host (written). */
 int rpt_mlp_predict(rpt_mlp* mlp, const float* X, int32_t n, float* Y);
+/* One input: features [n_in] host -> z0_out [n_out] host, the network's warm
+ * start in its training scale (multiply by the scale used for training, e.g.
+ * ub, and project onto the box to use it as z0).  RPT_EINVAL for NULL
+ * arguments. */
+int rpt_mlp_infer(rpt_mlp* mlp, const float* features, float* z0_out);
 /* ADMM-BB started from z0 = P_[lb,ub](prediction(features) * zscale) (features:
  * [n_in] host, zscale: [n] host, the scale the network was trained in, e.g. ub).
  * If that solve ends RPT_NOT_CONVERGED or RPT_DIVERGED, the cold-start solve is

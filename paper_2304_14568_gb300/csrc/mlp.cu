@@ -318,6 +318,14 @@ int rpt_mlp_predict(rpt_mlp* mlp, const float* X, int32_t n, float* Y) {
   return check(e, "rpt_mlp_predict");
 }
 
+int rpt_mlp_infer(rpt_mlp* mlp, const float* features, float* z0_out) {
+  if (!mlp || !features || !z0_out) {
+    set_error("rpt_mlp_infer: bad argument");
+    return RPT_EINVAL;
+  }
+  return rpt_mlp_predict(mlp, features, 1, z0_out);
+}
+
 int rpt_mlp_loss_grad(rpt_mlp* mlp, const float* X, const float* Y, int32_t n, double* loss, float* grad) {
   if (!mlp || !X || !Y || n < 1) {
     set_error("rpt_mlp_loss_grad: bad argument");

@@ -27,7 +27,7 @@ EXPORTED = [
     "rpt_version", "rpt_mlp_train_params_default", "rpt_mlp_create", "rpt_mlp_destroy", "rpt_mlp_param_count",
     "rpt_mlp_get_params", "rpt_mlp_set_params", "rpt_mlp_loss_grad", "rpt_mlp_train", "rpt_mlp_predict",
     "rpt_admm_bb_solve_learned", "rpt_trace_get", "rpt_plans_create_batched", "rpt_plan_batch_query",
-    "rpt_admm_bb_solve_batched",
+    "rpt_admm_bb_solve_batched", "rpt_mlp_infer",
 ]
 
 
@@ -165,6 +165,8 @@ def lib():
     L.rpt_mlp_train.restype = C.c_int
     L.rpt_mlp_predict.argtypes = [C.c_void_p, fp, C.c_int32, fp]
     L.rpt_mlp_predict.restype = C.c_int
+    L.rpt_mlp_infer.argtypes = [C.c_void_p, fp, fp]
+    L.rpt_mlp_infer.restype = C.c_int
     L.rpt_admm_bb_solve_learned.argtypes = [C.c_void_p, C.c_void_p, fp, dp, C.POINTER(AdmmParams), dp,
                                             C.POINTER(_Info), C.POINTER(C.c_int32)]
     L.rpt_admm_bb_solve_learned.restype = C.c_int
@@ -504,6 +506,14 @@ class Mlp:
         Y = np.empty((Xa.shape[0], self.n_out), dtype=np.float32)
         _check(lib().rpt_mlp_predict(self._h, _fptr(Xa), int(Xa.shape[0]), _fptr(Y)))
         return Y
+
+
+def mlp_infer(mlp, features):
+    """The network's output for one feature vector (rpt_mlp_infer)."""
+    f = _vec(features, np.float32, mlp.n_in, "features")
+    out = np.empty(mlp.n_out, dtype=np.float32)
+    _check(lib().rpt_mlp_infer(mlp._h, _fptr(f), _fptr(out)))
+    return out
 
 
 def admm_bb_solve_learned(plan, mlp, features, zscale, params: AdmmParams | None = None, **kw):

@@ -116,6 +116,7 @@ def test_null_arguments_are_errors(lib):
     assert lib.rpt_admm_bb_solve(None, None, None, None, None, None) == rpt.EINVAL
     assert lib.rpt_pgd_solve(None, None, None, None, None) == rpt.EINVAL
     assert lib.rpt_objective(None, None, None, None) == rpt.EINVAL
+    assert lib.rpt_mlp_infer(None, None, None) == rpt.EINVAL
     lib.rpt_plan_destroy(None)   # accepted
 
 

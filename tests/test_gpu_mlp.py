@@ -28,8 +28,11 @@ def test_gradient_and_forward_match_oracle(rpt):
         p = net.get_params().astype(np.float64)
         loss, g = net.loss_grad(X, Y)
         out = net.predict(X)
+        one = rpt.mlp_infer(net, X[5])
     ref_out = forward(p, dims, X)[-1]
     np.testing.assert_allclose(out, ref_out, rtol=1e-4, atol=1e-5 * np.abs(ref_out).max())
+    # rpt_mlp_infer: the same network on one input
+    np.testing.assert_allclose(one, out[5], rtol=1e-5, atol=1e-6 * np.abs(out[5]).max())
     ref_loss, ref_g = loss_grad(p, dims, X, Y)
     assert loss == pytest.approx(ref_loss, rel=1e-5)
     np.testing.assert_allclose(g, ref_g, rtol=1e-3, atol=1e-4 * np.abs(ref_g).max())
