@@ -106,7 +106,9 @@ typedef struct {
   int32_t cg_max;         /* CG iterations per subproblem solve (default 50) */
   double  cg_theta;       /* CG stops at ||c_s - B_s x|| <= theta (rho/2) max(r_prim, eps_prim)/sqrt(N) (default 0.15) */
   double  cg_eta0;        /* first ADMM iteration: CG stops at ||r|| <= eta0 ||r_0|| (default 1e-2) */
-  double  cg_floor_rel;   /* never ask CG for ||r|| below floor_rel * ||r_0|| of the first solve (default 1e-6) */
+  double  cg_floor_rel;   /* do not ask CG for ||r|| below floor_rel * ||r_0|| of the first solve
+                             (default 1e-6), unless Eq. 9 needs it: the floor is capped at
+                             (rho/2) eps_prim / sqrt(N), so that tight eps_abs / eps_rel are reached */
   int32_t use_graph;      /* 1 (default): one CUDA graph with device-side loops; 0: host-driven loop */
   int32_t check_every;    /* host-driven loop: read the convergence flag every k iterations (default 1) */
   int32_t resume;         /* 1: start from the plan's stored state (rpt_state_set / previous solve) */

@@ -33,9 +33,13 @@ Jacobi preconditioner M = diag(B_s).  CG on scenario s stops
 when ||c_s - B_s x|| <= tol_s with
     k = 0:  tol_s = eta0 ||r0_s||,  r0_s = c_s - B_s x_s^0 (the first residual)
     k >= 1: tol_s = max(theta (rho/2) max(r_prim^k, eps_prim^k) / sqrt(N),
-                        floor_rel ||r0_s||)
+                        min(floor_rel ||r0_s||, (rho/2) eps_prim^k / sqrt(N)))
 Since ||x_err|| <= 2 ||residual|| / rho, the subproblem error stays a
-fraction theta of the primal residual.
+fraction theta of the primal residual.  The floor saves steps on a
+subproblem that is already accurate, but it is capped at the accuracy that
+Eq. 9 needs: summed over the scenarios, a subproblem error of up to eps_prim.
+An uncapped floor (floor_rel ||r0_s|| above that) leaves the x-updates less
+accurate than the stopping rule asks, and the iteration stalls above eps.
 """
 from __future__ import annotations
 
@@ -122,7 +126,7 @@ def admm_bb(prob_or_w, rho=None, eps_abs=1e-4, eps_rel=1e-4, max_iter=1000,
                 else:
                     def tol_fn(r0n, s=s):
                         return max(cg_theta * 0.5 * rho * max(rp_prev, ep_prev) / math.sqrt(N),
-                                   cg_floor_rel * r0[s])
+                                   min(cg_floor_rel * r0[s], 0.5 * rho * ep_prev / math.sqrt(N)))
                 xn[s], kk = _cg(W, s, rho, c, x[s].copy(), tol_fn, cg_max, minv[s])
                 cg_total += kk
         # 2. consensus projection

@@ -196,8 +196,11 @@ __global__ void k_cg_init(DevPlan P, Ctl* C, const float* __restrict__ partial,
       r0n[s] = rn;
       t = C->cg_eta0 * rn;
     } else {
-      t = fmax(C->cg_theta * 0.5 * rho * fmax(C->r_prim, C->eps_prim) / sqrt((double)P.N),
-               C->cg_floor * __ldcg(&r0n[s]));
+      // theta-rule, with the floor capped at the accuracy Eq. 9 needs (a summed
+      // subproblem error of eps_prim): a floor above it stalls the iteration
+      const double sN = sqrt((double)P.N);
+      t = fmax(C->cg_theta * 0.5 * rho * fmax(C->r_prim, C->eps_prim) / sN,
+               fmin(C->cg_floor * __ldcg(&r0n[s]), 0.5 * rho * C->eps_prim / sN));
     }
     gam[s] = g;
     tol[s] = t;
