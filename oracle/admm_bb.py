@@ -82,7 +82,12 @@ def admm_bb(prob_or_w, rho=None, eps_abs=1e-4, eps_rel=1e-4, max_iter=1000,
             subproblem="chol", bb="paper", zmode="std", bb_kappa=10.0,
             z0=None, y0=None, tol_obj=math.inf, cg_theta=0.15, cg_eta0=1e-2,
             cg_floor_rel=0.0, cg_max=200, cg_precond="jacobi", record=False, record_f=False,
-            bb_per_scenario=False):
+            bb_per_scenario=False, xupdate=None):
+    """xupdate: optional callable (z, y) -> x [N, n] that performs step 1 with
+    the cached factors held elsewhere (oracle.parallel: the scenario subproblems
+    on worker processes, as the paper ran them); only with subproblem="chol"."""
+    if xupdate is not None and subproblem != "chol":
+        raise ValueError("xupdate replaces the cached-factor x-update only")
     W = prob_or_w if isinstance(prob_or_w, Weighted) else Weighted(prob_or_w)
     N, n = W.N, W.n
     if rho is None:
@@ -90,7 +95,7 @@ def admm_bb(prob_or_w, rho=None, eps_abs=1e-4, eps_rel=1e-4, max_iter=1000,
         rho = default_rho(W)
     t0 = time.perf_counter()
     b = [W.b(s) for s in range(N)]
-    if subproblem == "chol":
+    if subproblem == "chol" and xupdate is None:
         fac = [sla.cho_factor(W.B_dense(s, rho), lower=False) for s in range(N)]
     minv = [None] * N
     if subproblem == "cg" and cg_precond == "jacobi":
@@ -114,7 +119,9 @@ def admm_bb(prob_or_w, rho=None, eps_abs=1e-4, eps_rel=1e-4, max_iter=1000,
     for k in range(max_iter):
         # 1. scenario subproblems
         xn = np.empty_like(x)
-        for s in range(N):
+        if xupdate is not None:
+            xn[:] = xupdate(z, y)
+        for s in range(N if xupdate is None else 0):
             c = b[s] + 0.5 * rho * (z - y[s] / rho)
             if subproblem == "chol":
                 xn[s] = sla.cho_solve(fac[s], c)
