@@ -28,20 +28,35 @@ def unpack(params, dims):
     return out
 
 
-def forward(params, dims, X):
-    """All layer outputs: acts[0] = X, acts[l+1] = output of layer l."""
+def bf16_operand(x):
+    """The bfloat16 compute form's rounding of a GEMM operand: the value as the
+    GPU holds it (float32), rounded to the nearest bfloat16 (ties to even)."""
+    from .quantize import bf16_round
+    return bf16_round(np.asarray(x, dtype=np.float64).astype(np.float32)).astype(np.float64)
+
+
+def forward(params, dims, X, rnd=None):
+    """All layer outputs: acts[0] = X, acts[l+1] = output of layer l.
+    rnd: None for exact arithmetic, or a rounding applied to both operands of
+    every layer product (bf16_operand: the bfloat16 compute form, whose weights
+    and layer inputs are bfloat16 and whose sums, biases and ReLUs are exact)."""
     acts = [np.asarray(X, dtype=np.float64)]
     layers = unpack(params, dims)
+    r = (lambda a: a) if rnd is None else rnd
     for l, (W, b) in enumerate(layers):
-        z = acts[-1] @ W.T + b
+        z = r(acts[-1]) @ r(W).T + b
         acts.append(np.maximum(z, 0.0) if l + 1 < len(layers) else z)
     return acts
 
 
-def loss_grad(params, dims, X, Y):
-    """(loss, gradient as one array in the parameter layout)."""
+def loss_grad(params, dims, X, Y, rnd=None):
+    """(loss, gradient as one array in the parameter layout).  rnd as in
+    forward; in the backward products it rounds the layer-output gradient (after
+    the ReLU mask), the layer input and the weights; the bias gradient sums the
+    unrounded layer-output gradient."""
     layers = unpack(params, dims)
-    acts = forward(params, dims, X)
+    acts = forward(params, dims, X, rnd)
+    r = (lambda a: a) if rnd is None else rnd
     Y = np.asarray(Y, dtype=np.float64)
     B, n_out = Y.shape
     err = acts[-1] - Y
@@ -52,7 +67,7 @@ def loss_grad(params, dims, X, Y):
         if l + 1 < len(layers):
             d = d * (acts[l + 1] > 0.0)           # through the ReLU of layer l
         W, _ = layers[l]
-        grads[l] = (d.T @ acts[l], d.sum(axis=0))
-        d = d @ W                                 # dL/d acts[l]
+        grads[l] = (r(d).T @ r(acts[l]), d.sum(axis=0))
+        d = r(d) @ r(W)                           # dL/d acts[l]
     flat = np.concatenate([np.concatenate([gW.ravel(), gb]) for gW, gb in grads])
     return loss, flat

@@ -6,11 +6,15 @@
 // Network: n_in -> H -> ... -> H (L hidden layers, ReLU) -> n_out (linear).
 // Loss: mean squared error over the batch and the outputs.  Training: Adam on
 // minibatches drawn from a seeded permutation every epoch.  Everything runs in
-// the library's kernels (FP32): the tiled shared-memory GEMM of gemm.cuh with its
-// fused bias/ReLU epilogue, the ReLU and bias gradients, the loss gradient
-// and the Adam update.  The network is small (a few hundred thousand weights,
-// batches of a few hundred rows), so the GEMMs are latency- and launch-bound;
-// they use the CUDA cores, not the tensor cores.
+// the library's kernels: the GEMMs with their fused bias/ReLU epilogue, the ReLU
+// and bias gradients, the loss gradient and the Adam update.  Two compute forms:
+//   BF16 (default): weights, activations and activation gradients enter the
+//     GEMMs as bfloat16 and the tensor cores accumulate in FP32 (gemm_bf16.cuh,
+//     mma.sync); the FP32 master weights take the Adam step and are rounded to
+//     the bfloat16 copy after it; biases, losses and gradients stay FP32.
+//   F32: the tiled shared-memory FP32 GEMM of gemm.cuh on the CUDA cores.
+// The network is small (under a million weights, batches of a few hundred rows),
+// so its GEMMs are latency- and launch-bound either way.
 //
 // Parameter layout (one float array): for each layer l, W_l (row-major,
 // [out_l][in_l]) followed by b_l ([out_l]).
@@ -22,6 +26,7 @@
 #include <vector>
 
 #include "gemm.cuh"
+#include "gemm_bf16.cuh"
 #include "plan.h"
 
 namespace rpt {
@@ -70,6 +75,11 @@ __global__ void k_adam(int64_t n, float* __restrict__ p, const float* __restrict
   }
 }
 
+__global__ void k_to_bf16(int64_t n, const float* __restrict__ src, __nv_bfloat16* __restrict__ dst) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+    dst[k] = __float2bfloat16_rn(src[k]);
+}
+
 __global__ void k_gather_rows(int rows, int cols, const int* __restrict__ idx, const float* __restrict__ src,
                               float* __restrict__ dst) {
   const int64_t n = (int64_t)rows * cols;
@@ -88,6 +98,9 @@ struct Mlp {
   std::vector<int64_t> woff, boff;    // offsets of W_l, b_l in the parameter array
   int64_t nparam = 0;
   float *p = nullptr, *g = nullptr, *m = nullptr, *v = nullptr;
+  int bf16 = 1;                       // compute form: 1 bfloat16 tensor cores, 0 FP32 CUDA cores
+  __nv_bfloat16* pb = nullptr;        // bfloat16 copy of p (the weights the BF16 GEMMs read)
+  std::vector<__nv_bfloat16*> actb, dactb;   // bfloat16 copies of act / dact
   int cap = 0;                        // rows the activation buffers hold
   std::vector<float*> act;            // act[0] = input batch, act[l+1] = output of layer l
   std::vector<float*> dact;           // gradients w.r.t. act[l+1]
@@ -104,8 +117,12 @@ namespace {
 void free_acts(Mlp* M) {
   for (float* a : M->act) cudaFree(a);
   for (float* a : M->dact) cudaFree(a);
+  for (__nv_bfloat16* a : M->actb) cudaFree(a);
+  for (__nv_bfloat16* a : M->dactb) cudaFree(a);
   M->act.clear();
   M->dact.clear();
+  M->actb.clear();
+  M->dactb.clear();
   cudaFree(M->y);
   M->y = nullptr;
   cudaFree(M->idx);
@@ -120,9 +137,13 @@ cudaError_t ensure_cap(Mlp* M, int rows) {
   cudaError_t e = cudaSuccess;
   M->act.assign(L + 1, nullptr);
   M->dact.assign(L + 1, nullptr);
+  M->actb.assign(L + 1, nullptr);
+  M->dactb.assign(L + 1, nullptr);
   for (int l = 0; l <= L && e == cudaSuccess; ++l) {
     e = cudaMalloc(&M->act[l], sizeof(float) * (size_t)rows * M->dims[l]);
     if (e == cudaSuccess) e = cudaMalloc(&M->dact[l], sizeof(float) * (size_t)rows * M->dims[l]);
+    if (e == cudaSuccess) e = cudaMalloc(&M->actb[l], sizeof(__nv_bfloat16) * (size_t)rows * M->dims[l]);
+    if (e == cudaSuccess) e = cudaMalloc(&M->dactb[l], sizeof(__nv_bfloat16) * (size_t)rows * M->dims[l]);
   }
   if (e == cudaSuccess) e = cudaMalloc(&M->y, sizeof(float) * (size_t)rows * M->dims[L]);
   if (e == cudaSuccess) e = cudaMalloc(&M->idx, sizeof(int) * (size_t)rows);
@@ -135,10 +156,18 @@ int blocks_for(int64_t n) { return (int)std::min<int64_t>(4096, std::max<int64_t
 // Forward pass of `rows` rows already in act[0].
 void forward(Mlp* M, int rows) {
   const int L = (int)M->dims.size() - 1;
+  if (M->bf16) {
+    const int64_t n0 = (int64_t)rows * M->dims[0];
+    k_to_bf16<<<blocks_for(n0), 256, 0, M->stream>>>(n0, M->act[0], M->actb[0]);
+  }
   for (int l = 0; l < L; ++l) {
     const int in = M->dims[l], out = M->dims[l + 1];
-    gemm<false, true>(M->stream, rows, out, in, M->act[l], in, M->p + M->woff[l], in, M->act[l + 1], out,
-                      M->p + M->boff[l], l + 1 < L);
+    if (M->bf16)
+      gemm_bf16<false, true>(M->stream, rows, out, in, M->actb[l], in, M->pb + M->woff[l], in, M->act[l + 1], out,
+                             M->actb[l + 1], M->p + M->boff[l], l + 1 < L);
+    else
+      gemm<false, true>(M->stream, rows, out, in, M->act[l], in, M->p + M->woff[l], in, M->act[l + 1], out,
+                        M->p + M->boff[l], l + 1 < L);
   }
 }
 
@@ -155,18 +184,34 @@ void backward(Mlp* M, int rows) {
       const int64_t k = (int64_t)rows * out;
       k_relu_bwd<<<blocks_for(k), 256, 0, M->stream>>>(k, M->act[l + 1], M->dact[l + 1]);
     }
-    // dW_l = dAct_{l+1}^T act_l   ([out][rows] x [rows][in])
-    gemm<true, false>(M->stream, out, in, rows, M->dact[l + 1], out, M->act[l], in, M->g + M->woff[l], in,
-                      nullptr, false);
     k_bias_grad<<<(out + 255) / 256, 256, 0, M->stream>>>(rows, out, M->dact[l + 1], M->g + M->boff[l]);
-    // dAct_l = dAct_{l+1} W_l   ([rows][out] x [out][in]); not needed for the input
-    if (l > 0)
-      gemm<false, false>(M->stream, rows, in, out, M->dact[l + 1], out, M->p + M->woff[l], in, M->dact[l], in,
-                         nullptr, false);
+    if (M->bf16) {
+      const int64_t k = (int64_t)rows * out;
+      k_to_bf16<<<blocks_for(k), 256, 0, M->stream>>>(k, M->dact[l + 1], M->dactb[l + 1]);
+      // dW_l = dAct_{l+1}^T act_l   ([out][rows] x [rows][in])
+      gemm_bf16<true, false>(M->stream, out, in, rows, M->dactb[l + 1], out, M->actb[l], in, M->g + M->woff[l],
+                             in);
+      // dAct_l = dAct_{l+1} W_l   ([rows][out] x [out][in]); not needed for the input
+      if (l > 0)
+        gemm_bf16<false, false>(M->stream, rows, in, out, M->dactb[l + 1], out, M->pb + M->woff[l], in,
+                                M->dact[l], in);
+    } else {
+      gemm<true, false>(M->stream, out, in, rows, M->dact[l + 1], out, M->act[l], in, M->g + M->woff[l], in,
+                        nullptr, false);
+      if (l > 0)
+        gemm<false, false>(M->stream, rows, in, out, M->dact[l + 1], out, M->p + M->woff[l], in, M->dact[l], in,
+                           nullptr, false);
+    }
   }
 }
 
 int check(cudaError_t e, const char* what) { return e == cudaSuccess ? RPT_OK : cuda_fail(e, what); }
+
+// the bfloat16 copy of the weights, after every change of the FP32 ones
+cudaError_t refresh_bf16(Mlp* M) {
+  k_to_bf16<<<blocks_for(M->nparam), 256, 0, M->stream>>>(M->nparam, M->p, M->pb);
+  return cudaGetLastError();
+}
 
 }  // namespace
 }  // namespace rpt
@@ -230,7 +275,10 @@ int rpt_mlp_create(int32_t n_in, int32_t n_hidden, int32_t n_hidden_layers, int3
   if (e == cudaSuccess) e = cudaMalloc(&M->m, bytes);
   if (e == cudaSuccess) e = cudaMalloc(&M->v, bytes);
   if (e == cudaSuccess) e = cudaMalloc(&M->loss, sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&M->pb, sizeof(__nv_bfloat16) * (size_t)M->nparam);
   if (e == cudaSuccess) e = cudaMemcpy(M->p, h.data(), bytes, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = refresh_bf16(M);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(M->stream);
   if (e == cudaSuccess) e = cudaMemset(M->m, 0, bytes);
   if (e == cudaSuccess) e = cudaMemset(M->v, 0, bytes);
   if (e != cudaSuccess) {
@@ -252,6 +300,7 @@ int rpt_mlp_destroy(rpt_mlp* mlp) {
   cudaFree(M->m);
   cudaFree(M->v);
   cudaFree(M->loss);
+  cudaFree(M->pb);
   cudaFree(M->xall);
   cudaFree(M->yall);
   if (M->stream) cudaStreamDestroy(M->stream);
@@ -292,9 +341,19 @@ int rpt_mlp_set_params(rpt_mlp* mlp, const float* params) {
   cudaError_t e = cudaMemcpyAsync(M->p, params, bytes, cudaMemcpyHostToDevice, M->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(M->m, 0, bytes, M->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(M->v, 0, bytes, M->stream);
+  if (e == cudaSuccess) e = refresh_bf16(M);
   if (e == cudaSuccess) e = cudaStreamSynchronize(M->stream);
   M->step = 0;
   return check(e, "rpt_mlp_set_params");
+}
+
+int rpt_mlp_set_compute(rpt_mlp* mlp, int32_t value_format) {
+  if (!mlp || (value_format != RPT_F32 && value_format != RPT_BF16)) {
+    set_error("rpt_mlp_set_compute: need a network and RPT_F32 or RPT_BF16");
+    return RPT_EINVAL;
+  }
+  reinterpret_cast<Mlp*>(mlp)->bf16 = value_format == RPT_BF16 ? 1 : 0;
+  return RPT_OK;
 }
 
 int rpt_mlp_predict(rpt_mlp* mlp, const float* X, int32_t n, float* Y) {
@@ -400,6 +459,7 @@ int rpt_mlp_train(rpt_mlp* mlp, const float* X, const float* Y, int32_t n, const
       k_adam<<<blocks_for(M->nparam), 256, 0, M->stream>>>(M->nparam, M->p, M->g, M->m, M->v, lr_t, b1, b2,
                                                            (float)tp->eps, (float)tp->weight_decay);
       e = cudaGetLastError();
+      if (e == cudaSuccess && M->bf16) e = refresh_bf16(M);
     }
     // stream ordering keeps the host-side permutation valid: wait before the next shuffle
     if (e == cudaSuccess) e = cudaStreamSynchronize(M->stream);

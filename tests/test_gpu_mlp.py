@@ -20,11 +20,12 @@ def rpt():
 
 
 def test_gradient_and_forward_match_oracle(rpt):
+    """FP32 compute form (CUDA cores) against the float64 oracle."""
     dims = [9, 70, 70, 45]                     # sizes that leave ragged GEMM tiles
     rng = np.random.default_rng(3)
     X = rng.normal(size=(37, 9)).astype(np.float32)
     Y = rng.normal(size=(37, 45)).astype(np.float32)
-    with rpt.Mlp(9, 70, 2, 45, seed=5) as net:
+    with rpt.Mlp(9, 70, 2, 45, seed=5, compute=rpt.F32) as net:
         p = net.get_params().astype(np.float64)
         loss, g = net.loss_grad(X, Y)
         out = net.predict(X)
@@ -36,6 +37,38 @@ def test_gradient_and_forward_match_oracle(rpt):
     ref_loss, ref_g = loss_grad(p, dims, X, Y)
     assert loss == pytest.approx(ref_loss, rel=1e-5)
     np.testing.assert_allclose(g, ref_g, rtol=1e-3, atol=1e-4 * np.abs(ref_g).max())
+
+
+@pytest.mark.parametrize("dims,rows", [([9, 70, 70, 45], 37), ([9, 512, 512, 512, 200], 128)])
+def test_bf16_tensor_core_gradient_matches_oracle(rpt, dims, rows):
+    """BF16 compute form (tensor cores, FP32 accumulation) against the float64
+    oracle of the same form (oracle.mlp with bf16_operand: every operand of the
+    layer products rounded to bfloat16, sums, biases and ReLUs exact).  What
+    remains is float32 accumulation and the rare activation whose float32 value
+    rounds to the other bfloat16 neighbour: 1e-3 relative per tensor (in norm).
+    The form's own deviation from the exact float64 network is reported.
+    Ragged tiles (70, 45, 37 rows) and the learned form's own shape
+    (9 -> 512 x 3 -> 200, batch 128)."""
+    from oracle.mlp import unpack, bf16_operand
+    rng = np.random.default_rng(4)
+    X = rng.normal(size=(rows, dims[0])).astype(np.float32)
+    Y = rng.normal(size=(rows, dims[-1])).astype(np.float32)
+    with rpt.Mlp(dims[0], dims[1], len(dims) - 2, dims[-1], seed=6) as net:
+        p = net.get_params().astype(np.float64)
+        loss, g = net.loss_grad(X, Y)
+        out = net.predict(X)
+    ref_out = forward(p, dims, X, bf16_operand)[-1]
+    assert np.linalg.norm(out - ref_out) <= 1e-3 * np.linalg.norm(ref_out)
+    ref_loss, ref_g = loss_grad(p, dims, X, Y, bf16_operand)
+    assert loss == pytest.approx(ref_loss, rel=1e-3)
+    worst = 0.0
+    for (W, b), (Wr, br) in zip(unpack(g, dims), unpack(ref_g, dims)):
+        assert np.linalg.norm(W - Wr) <= 1e-3 * np.linalg.norm(Wr)
+        assert np.linalg.norm(b - br) <= 1e-3 * np.linalg.norm(br)
+    _, exact_g = loss_grad(p, dims, X, Y)
+    for (W, _), (We, _) in zip(unpack(g, dims), unpack(exact_g, dims)):
+        worst = max(worst, float(np.linalg.norm(W - We) / np.linalg.norm(We)))
+    print(f"bfloat16 form vs exact float64 network, worst weight-gradient tensor: {worst:.2e}")
 
 
 def test_set_params_round_trip_and_training_reduces_loss(rpt):
@@ -61,35 +94,39 @@ def _features(sw, d):
 
 
 def test_learned_warm_start_gains_over_cold_start(rpt):
+    """The learned form's network (9 -> 512 x 3 -> n, bfloat16 tensor cores) trained
+    on solutions of one plan reweighted in place (rpt_plan_set_weights) over a
+    weight sweep; on held-out settings the warm start needs fewer iterations
+    than the cold start, and the oracle judges both results."""
     base = config_tiny_plain(0)
     rng = np.random.default_rng(7)
     n_train, n_test = 96, 8
-    feats, targets, tests = [], [], []
-    for k in range(n_train + n_test):
-        sw, d = sample_weights(rng, base.labels)
-        prob = reweighted(base, sw, d)
-        if k < n_train:
-            with plan_of(rpt, prob) as P:
-                z, info = P.admm_bb_solve(eps_abs=1e-6, eps_rel=1e-6, max_iter=20000)
+    settings = [sample_weights(rng, base.labels) for _ in range(n_train + n_test)]
+    feats, targets = [], []
+    cold_it, warm_it = [], []
+    with plan_of(rpt, base) as P:
+        for sw, d in settings[:n_train]:
+            prob = reweighted(base, sw, d)
+            P.set_weights(prob.voxel_w, prob.presc)
+            z, info = P.admm_bb_solve(eps_abs=1e-6, eps_rel=1e-6, max_iter=20000, subproblem=rpt.SUB_CHOL)
+            assert info["status"] == 0
             feats.append(_features(sw, d))
             targets.append((z / prob.ub).astype(np.float32))
-        else:
-            tests.append((prob, _features(sw, d)))
-    X, Y = np.stack(feats), np.stack(targets)
-    cold_it, warm_it = [], []
-    with rpt.Mlp(X.shape[1], 256, 2, base.n, seed=2) as net:
-        net.train(X, Y, epochs=400, batch=32, lr=1e-3)
-        for prob, f in tests:
-            W = Weighted(prob)
-            with plan_of(rpt, prob) as P:
+        X, Y = np.stack(feats), np.stack(targets)
+        with rpt.Mlp(X.shape[1], 512, 3, base.n, seed=2) as net:
+            net.train(X, Y, epochs=300, batch=32, lr=1e-3)
+            for sw, d in settings[n_train:]:
+                prob = reweighted(base, sw, d)
+                W = Weighted(prob)
+                P.set_weights(prob.voxel_w, prob.presc)
                 xc, ic = P.admm_bb_solve()
-                xw, iw, used = rpt.admm_bb_solve_learned(P, net, f, prob.ub)
-            assert ic["status"] == 0 and iw["status"] == 0
-            # the oracle checks both results: same objective to the tolerance, near-optimal
-            fc, fw = W.f(xc), W.f(xw)
-            assert abs(fw - fc) / fc <= 1e-3, (fw, fc)
-            assert certificates(W, xw)["pg"] < 1e-2
-            cold_it.append(ic["iterations"])
-            warm_it.append(iw["iterations"] if used else iw["iterations"])
+                xw, iw, used = rpt.admm_bb_solve_learned(P, net, _features(sw, d), prob.ub)
+                assert ic["status"] == 0 and iw["status"] == 0
+                # the oracle checks both results: same objective to the tolerance, near-optimal
+                fc, fw = W.f(xc), W.f(xw)
+                assert abs(fw - fc) / fc <= 1e-3, (fw, fc)
+                assert certificates(W, xw)["pg"] < 1e-2
+                cold_it.append(ic["iterations"])
+                warm_it.append(iw["iterations"])
     print(f"held-out iterations to 1e-4: cold {np.mean(cold_it):.1f}, learned warm start {np.mean(warm_it):.1f}")
     assert np.mean(warm_it) < 0.9 * np.mean(cold_it), (cold_it, warm_it)
