@@ -84,12 +84,31 @@ typedef struct {
   int32_t device;                   /* CUDA device ordinal */
   void*   stream;                   /* cudaStream_t to run on, or NULL for a stream owned by the plan */
   int32_t ctas_per_sm;              /* row-pass CTAs per SM (0 = library choice) */
-  int32_t row_path;                 /* 1 register-direct loads, 2 bulk-copy (TMA) ring, 3 streaming (warps
-                                       claim chunks, entries go straight to registers); 0: RPT_ROW_PATH
-                                       from the environment, else 2 when the plan fits it and 1 otherwise */
+  int32_t row_path;                 /* row-pass layout and kernel:
+                                       1 register-direct loads of CSR rows;
+                                       2 bulk-copy (TMA) ring over CSR rows;
+                                       3 streaming (warps claim chunks, entries go straight to registers);
+                                       4 bundled ring: rows grouped 4 at a time in the given row order, one
+                                         spot index per column of a group (rows that are neighbours in the
+                                         input order should share spots, as voxels in grid order do), and
+                                         exact 64-bit fixed-point sums, so every result is bitwise
+                                         reproducible;
+                                       0: 4 when its shared-memory stage fits the plan, else 2, else 1 */
   int32_t autotune;                 /* 1: time every ring configuration that fits this plan (entries and
                                        rows per stage, stages) on its own row pass and keep the fastest;
-                                       0: RPT_AUTOTUNE from the environment, else the first that fits */
+                                       0: the first that fits */
+  int32_t chunk_entries;            /* ring geometry (paths 2-4): entries (path 4: block columns) per stage;
+                                       0 = library choice.  With chunk_rows and stages it replaces the
+                                       candidate list (and the autotuner) */
+  int32_t chunk_rows;               /* rows (path 4: bundles) per stage; 0 = library choice */
+  int32_t stages;                   /* ring stages (2..8, paths 2 and 4); 0 = library choice */
+  int32_t min_lanes;                /* smallest lanes-per-row group of paths 1 and 2 (1..32, rounded down to a
+                                       power of two); 0 = 8 */
+  int32_t inject_timeout;           /* testing hook: 1 makes the ring's producer (paths 2 and 4) issue no
+                                       copy, so every consumer wait runs out after its one-second bound and
+                                       the call returns RPT_TIMEOUT (no GPU fault is involved); 0 normally */
+  int64_t device_mem_cap;           /* testing hook: bytes the plan may allocate on the device (a request past
+                                       it fails as an out-of-memory would, RPT_ENOMEM); 0 = no cap */
 } rpt_device_opts;
 
 /* ADMM-BB parameters (Sec. 2.2).  Fill with rpt_admm_params_default(). */
@@ -123,6 +142,9 @@ typedef struct {
                              written); 1: Eq. 8 applied to each scenario's own blocks dd_s, dy_s,
                              one step beta_s per scenario (same bb_mode rules per scenario);
                              rpt_solve_info.step then reports the mean of the beta_s */
+  double  f_target;       /* > 0: stop as soon as f(z) <= f_target instead of by Eq. 9 (one objective
+                             pass per iteration checks it; tol_obj is then ignored), e.g.
+                             (1 + 1e-4) f* for a time to a given objective; 0 = off (default) */
 } rpt_admm_params;
 
 #define RPT_SUB_CG   0
@@ -165,13 +187,18 @@ typedef struct {
   int32_t sm_count;
   double  default_rho;    /* 2 mean_s(trace(A~_s^T A~_s))/n (without rho_scale) */
   double  const_term;     /* sum over rows not stored for a scenario of c_s w_i p_i^2 (part of every f) */
-  int32_t row_path;       /* row-pass implementation in use: 1 register-direct, 2 bulk-copy ring, 3 streaming */
+  int32_t row_path;       /* row-pass implementation in use: 1 register-direct, 2 bulk-copy ring, 3 streaming,
+                             4 bundled ring */
   int32_t min_lanes;      /* smallest lanes-per-row group */
   int32_t chunk_entries;  /* ring / streaming: entries per chunk (0 for the register path) */
   int32_t chunk_rows;     /* ring / streaming: rows per chunk */
   int32_t stages;         /* ring: stages */
   int32_t autotuned;      /* ring configurations timed at plan creation (0: none) */
   double  autotune_ms;    /* the chosen configuration's pass time in that timing */
+  int64_t bundles;        /* path 4: row bundles over all scenarios (0 otherwise) */
+  int64_t block_cols;     /* path 4: stored block columns (4 values and one index each) */
+  double  bundle_fill;    /* path 4: stored entries / (4 block_cols): the share of stored values that
+                             are entries of the matrix */
 } rpt_plan_stats;
 
 /* ---- defaults ----------------------------------------------------------- */
@@ -190,6 +217,20 @@ void rpt_pgd_params_default(rpt_pgd_params* p);
  * every row is padded to a multiple of 4; RPT_ENOMEM/RPT_ECUDA on device
  * failures.  *out is set only on success. */
 int rpt_plan_create(const rpt_problem* prob, const rpt_device_opts* opts, rpt_plan** out);
+
+/* New objective weights for an existing plan (weight sweeps: the same
+ * dose-influence matrices under other structure weights or prescriptions, as
+ * the learned warm start is trained on).  voxel_w, presc: host [m], finite and
+ * >= 0, indexed like rpt_problem.  Rewrites the stored row weights and
+ * prescriptions, the Jacobi preconditioner (summed exactly in fixed point),
+ * the default rho, the constant of Eq. 2 and, for row path 4, its fixed-point
+ * bounds; forgets the cached factor and the Lipschitz estimate.  The stored
+ * state (rpt_state_get) is kept.  The row passes then compute what a plan
+ * created with these weights computes (the Jacobi diagonal and the default rho
+ * may differ from a fresh plan's in the last bits, as they are summed in
+ * another order).  Allocates and frees temporary device memory.  RPT_EINVAL
+ * for null or invalid arrays. */
+int rpt_plan_set_weights(rpt_plan* plan, const double* voxel_w, const double* presc);
 
 /* Release a plan and its device memory.  NULL is accepted. */
 void rpt_plan_destroy(rpt_plan* plan);
@@ -302,7 +343,10 @@ int rpt_profile_row_pass(rpt_plan* plan, int mode, int reps, double* ms_per_pass
  * capture.  The call enqueues two kernels and returns without synchronising.
  * Every call overwrites the scratch slots it reads, so nothing needs clearing,
  * but calls that overlap on the GPU (on different streams, or on different
- * threads) share the array and race.  Allocates nothing (no cudaMalloc,
+ * threads) share the array and race.  Results are within the float32 bound of
+ * the sums but not bitwise reproducible (shared-memory float atomics).  The
+ * looked-up address is kept for the process: do not call this entry point on a
+ * device after a cudaDeviceReset of it.  Allocates nothing (no cudaMalloc,
  * cudaFree or allocating library routine).  Errors: RPT_EINVAL for bad sizes,
  * null pointers or rho < 0; RPT_EUNSUPPORTED for n > 8192; RPT_ECUDA if a
  * launch fails. */
@@ -325,10 +369,11 @@ int rpt_state_set(rpt_plan* plan, const double* z, const double* x, const double
  * as z0 of ADMM-BB; cold-start ADMM-BB is the fallback.  Network: n_in ->
  * n_hidden (x n_hidden_layers, ReLU) -> n_out (linear); loss: mean squared error
  * over the batch and the outputs; training: Adam on minibatches (every
- * minibatch full; the remainder of an epoch's permutation is skipped).  FP32 on
+ * minibatch full; the remainder of an epoch's permutation is skipped), on
  * the device.  Parameters as one float array: for each layer W ([out][in],
  * row-major) then b ([out]).  Host arrays X [n][n_in] and Y [n][n_out] are
- * row-major.  Errors: RPT_EINVAL for bad sizes or null pointers, RPT_ECUDA. */
+ * row-major.  Compute form: see rpt_mlp_set_compute.  Errors: RPT_EINVAL for bad
+ * sizes or null pointers, RPT_ECUDA. */
 typedef struct rpt_mlp rpt_mlp;
 
 typedef struct {
@@ -346,6 +391,11 @@ int rpt_mlp_train_params_default(rpt_mlp_train_params* tp);
 int rpt_mlp_create(int32_t n_in, int32_t n_hidden, int32_t n_hidden_layers, int32_t n_out, uint64_t seed,
                    int32_t device, rpt_mlp** out);
 int rpt_mlp_destroy(rpt_mlp* mlp);
+/* Compute form of the network's GEMMs: RPT_BF16 (default) bfloat16 weights,
+ * activations and activation gradients on the tensor cores with FP32
+ * accumulation (FP32 master weights take the Adam step); RPT_F32 FP32 on the
+ * CUDA cores.  RPT_EINVAL for any other value. */
+int rpt_mlp_set_compute(rpt_mlp* mlp, int32_t value_format);
 int rpt_mlp_param_count(const rpt_mlp* mlp, int64_t* count);
 int rpt_mlp_get_params(rpt_mlp* mlp, float* params);          /* params: [count] host */
 int rpt_mlp_set_params(rpt_mlp* mlp, const float* params);    /* also resets the Adam moments */

@@ -31,11 +31,13 @@ namespace {
 
 // ---- quantisation kernels (plan creation only) ---------------------------------
 
-__global__ void k_colmax(const float* __restrict__ val, const int32_t* __restrict__ col, int64_t nnz,
+// Values and columns: value k belongs to stored entry k >> sh (sh = 0 for CSR
+// rows, 2 for row bundles with 4 values per block column).
+__global__ void k_colmax(const float* __restrict__ val, const int32_t* __restrict__ col, int64_t nval, int sh,
                          unsigned int* __restrict__ mx) {
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nnz;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nval;
        k += (int64_t)gridDim.x * blockDim.x)
-    atomicMax(&mx[col[k]], __float_as_uint(fabsf(val[k])));   // |a| >= 0 orders like its bits
+    atomicMax(&mx[col[k >> sh]], __float_as_uint(fabsf(val[k])));   // |a| >= 0 orders like its bits
 }
 
 __global__ void k_scales(const unsigned int* __restrict__ mx, int n, int n_pad, float fmt_max,
@@ -51,25 +53,25 @@ __global__ void k_scales(const unsigned int* __restrict__ mx, int n, int n_pad, 
 }
 
 template <typename Q>
-__global__ void k_quantise(const float* __restrict__ val, const int32_t* __restrict__ col, int64_t nnz,
+__global__ void k_quantise(const float* __restrict__ val, const int32_t* __restrict__ col, int64_t nval, int sh,
                            const float* __restrict__ scale, Q* __restrict__ out);
 
 template <>
 __global__ void k_quantise<__nv_bfloat16>(const float* __restrict__ val, const int32_t* __restrict__ col,
-                                          int64_t nnz, const float* __restrict__ scale,
+                                          int64_t nval, int sh, const float* __restrict__ scale,
                                           __nv_bfloat16* __restrict__ out) {
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nnz;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nval;
        k += (int64_t)gridDim.x * blockDim.x)
-    out[k] = __float2bfloat16_rn(val[k] / scale[col[k]]);
+    out[k] = __float2bfloat16_rn(val[k] / scale[col[k >> sh]]);
 }
 
 template <>
 __global__ void k_quantise<__nv_fp8_e4m3>(const float* __restrict__ val, const int32_t* __restrict__ col,
-                                          int64_t nnz, const float* __restrict__ scale,
+                                          int64_t nval, int sh, const float* __restrict__ scale,
                                           __nv_fp8_e4m3* __restrict__ out) {
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nnz;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nval;
        k += (int64_t)gridDim.x * blockDim.x)
-    out[k] = __nv_fp8_e4m3(val[k] / scale[col[k]]);   // round to nearest, saturating
+    out[k] = __nv_fp8_e4m3(val[k] / scale[col[k >> sh]]);   // round to nearest, saturating
 }
 
 __global__ void k_to_u16(const int32_t* __restrict__ in, int64_t nnz, uint16_t* __restrict__ out) {
@@ -82,6 +84,7 @@ struct ScenarioCheck {
   std::string err;
   double trace = 0.0;          // sum_i w_i sum_j a_ij^2
   std::vector<double> diag;    // [n] sum_i w_i a_ij^2 (Jacobi preconditioner)
+  double colsq_max = 0.0;      // max_j sum_i a_ij^2 (unweighted)
 };
 
 void check_scenario(const rpt_problem* pr, int s, ScenarioCheck* out) {
@@ -95,6 +98,7 @@ void check_scenario(const rpt_problem* pr, int s, ScenarioCheck* out) {
   }
   double tr = 0.0;
   out->diag.assign(n, 0.0);
+  std::vector<double> colsq(n, 0.0);
   for (int i = 0; i < m; ++i) {
     const int32_t a = rp[i], b = rp[i + 1];
     if (b < a) {
@@ -122,21 +126,23 @@ void check_scenario(const rpt_problem* pr, int s, ScenarioCheck* out) {
       }
       rs += (double)v * (double)v;
       out->diag[c] += pr->voxel_w[i] * (double)v * (double)v;
+      colsq[c] += (double)v * (double)v;
     }
     tr += pr->voxel_w[i] * rs;
   }
   out->trace = tr;
+  for (int j = 0; j < n; ++j) out->colsq_max = std::max(out->colsq_max, colsq[j]);
 }
 
-// Device allocations of a plan.  RPT_DEVICE_MEM_CAP (bytes, environment) caps the
-// plan's total, so that running out of device memory can be tested without
-// exhausting the device: a request past the cap fails as cudaMalloc would.
+// Device allocations of a plan.  cap (rpt_device_opts.device_mem_cap, bytes; 0:
+// none) caps the plan's total, so that running out of device memory can be
+// tested without exhausting the device: a request past it fails as cudaMalloc
+// would.
 struct Alloc {
   Plan* P;
+  size_t cap = 0;
   cudaError_t err = cudaSuccess;
   size_t total = 0;
-  size_t cap = (size_t)std::strtoull(std::getenv("RPT_DEVICE_MEM_CAP") ? std::getenv("RPT_DEVICE_MEM_CAP") : "0",
-                                     nullptr, 10);
   template <typename T>
   T* get(size_t count) {
     if (err != cudaSuccess) return nullptr;
@@ -180,10 +186,14 @@ struct RingCfg {
   std::vector<int> scen_chunk;
 };
 
-int env_int(const char* name, int dflt) {
-  const char* v = std::getenv(name);
-  if (!v || !*v) return dflt;
-  return std::atoi(v);
+// The caller's ring geometry (rpt_device_opts chunk_entries / chunk_rows /
+// stages), as the only candidate; empty when the caller leaves all three to
+// the library.  Unset fields take the given defaults.
+std::vector<int3> ring_override(const rpt_device_opts* o, int cmax, int rmax, int stages) {
+  if (!o || (o->chunk_entries <= 0 && o->chunk_rows <= 0 && o->stages <= 0)) return {};
+  return {make_int3(std::max(64, o->chunk_entries > 0 ? o->chunk_entries : cmax) & ~15,
+                    std::max(1, o->chunk_rows > 0 ? o->chunk_rows : rmax),
+                    std::min(8, std::max(2, o->stages > 0 ? o->stages : stages)))};
 }
 
 int create_plan(const rpt_problem* pr, const rpt_device_opts* opts, rpt_plan** out) {
@@ -277,13 +287,18 @@ int create_plan(const rpt_problem* pr, const rpt_device_opts* opts, rpt_plan** o
   std::vector<int32_t> kept;
   kept.reserve(m);
   double const_term = 0.0;
+  std::vector<int32_t> dropped;
   for (int i = 0; i < m; ++i) {
-    if (keep[i]) kept.push_back(i);
-    else
+    if (keep[i]) {
+      kept.push_back(i);
+    } else {
+      dropped.push_back(i);
       for (int s = 0; s < N; ++s) const_term += cs[s] * pr->voxel_w[i] * pr->presc[i] * pr->presc[i];
+    }
   }
   if (kept.empty()) {   // keep one (empty) row so every launch has work items
     kept.push_back(0);
+    dropped.erase(dropped.begin());
     for (int s = 0; s < N; ++s) const_term -= cs[s] * pr->voxel_w[0] * pr->presc[0] * pr->presc[0];
   }
   const int m_act = (int)kept.size();
@@ -338,33 +353,177 @@ int create_plan(const rpt_problem* pr, const rpt_device_opts* opts, rpt_plan** o
   dp.m_act = m_act;
   dp.n_pad = n_pad;
   dp.value_format = pr->value_format;
-  // RPT_INJECT_TIMEOUT=1 (environment): the bulk-copy ring's producer issues no
-  // copy, so every consumer wait runs out (after its one-second bound) and the
-  // pass reports RPT_TIMEOUT; for testing the bounded waits without a GPU fault
-  dp.inject_timeout = env_int("RPT_INJECT_TIMEOUT", 0) != 0 ? 1 : 0;
+  // testing hook: the bulk-copy rings' producer issues no copy, so every
+  // consumer wait runs out (after its one-second bound) and the pass reports
+  // RPT_TIMEOUT; the bounded waits are tested without a GPU fault
+  dp.inject_timeout = (opts && opts->inject_timeout) ? 1 : 0;
   dp.index_width = pr->index_width;
   P->nchunk = (n + kVecThreads - 1) / kVecThreads;
   P->kept_rows = kept;
   const int bi = pr->index_width == 16 ? 2 : 4;
   const int bv = pr->value_format == RPT_F32 ? 4 : (pr->value_format == RPT_BF16 ? 2 : 1);
 
-  int min_lanes = std::min(32, std::max(1, env_int("RPT_MIN_LANES", 8)));
+  int min_lanes = std::min(32, std::max(1, (opts && opts->min_lanes > 0) ? opts->min_lanes : 8));
   min_lanes = 1 << (31 - __builtin_clz((unsigned)min_lanes));   // power of two
-  // row path: the caller's choice, else RPT_ROW_PATH from the environment, else
-  // the bulk-copy ring when the plan fits it and the register path otherwise
-  const int want_path = (opts && opts->row_path) ? opts->row_path : env_int("RPT_ROW_PATH", 0);
-  // ---- per-scenario row lists, sorted by decreasing length; entries permuted to match ----
-  RowLists R;
-  R.rec_base.assign(N + 1, 0);
-  R.nrows.assign(N, 0);
+  // row path: the caller's choice, else the bundled ring when its stage fits the
+  // plan, else the bulk-copy ring when it fits, else the register path
+  const int want_path = opts ? opts->row_path : 0;
+  if (want_path < 0 || want_path > 4) {
+    free_plan(P);
+    set_error("row_path must be 0..4");
+    return RPT_EINVAL;
+  }
+  int smem_optin = 0;
+  cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, P->device);
+  const bool autotune = opts && opts->autotune;
+  // each scenario's non-empty rows in kept order (rows empty in a scenario add
+  // c_s w p^2 to the constant)
   std::vector<std::vector<int32_t>> order(N);
+  P->empty_kept.assign(N, {});
   for (int s = 0; s < N; ++s) {
     const int32_t* rp = pr->row_ptr[s];
     for (int k = 0; k < m_act; ++k) {
       const int len = rp[kept[k] + 1] - rp[kept[k]];
-      if (len > 0) order[s].push_back(k);
-      else const_term += cs[s] * pr->voxel_w[kept[k]] * pr->presc[kept[k]] * pr->presc[kept[k]];
+      if (len > 0) {
+        order[s].push_back(k);
+      } else {
+        const_term += cs[s] * pr->voxel_w[kept[k]] * pr->presc[kept[k]] * pr->presc[kept[k]];
+        P->empty_kept[s].push_back(k);
+      }
     }
+  }
+  P->scen_c = cs;
+  P->dropped_rows = dropped;
+  P->colsq_max.assign(N, 0.0);
+  for (int s = 0; s < N; ++s) P->colsq_max[s] = chk[s].colsq_max;
+  // stored layout, filled by one of the branches below
+  RowLists R;                        // per scenario: rows (CSR) or bundles, with entry offsets
+  std::vector<int32_t> col_h;        // [NE] spot index per stored entry (block column)
+  std::vector<float> val_h;          // [NE * vpe]
+  std::vector<int4> rec_h;           // records uploaded to the device
+  std::vector<int> recbase_h(N + 1, 0);
+  std::vector<int64_t> ebase(N, 0), ecount(N, 0);   // first stored entry and count per scenario
+  std::vector<int> rec_of_h((size_t)N * m_act, -1);
+  int64_t NE = 0;
+  int vpe = 1;
+  bool bundled = false, dyn = false;
+  int64_t n_bundles = 0;
+  std::vector<int4> blocks;
+  std::vector<int> blk_first(N + 1, 0);
+  std::vector<ChunkDesc> chunks;
+  std::vector<int> scen_chunk;
+  bool use_tma = false, use_stream = false;
+  int ctas = 0;
+  std::vector<RingCfg> ring_cfgs;   // ring configurations that fit (all of them when autotuning)
+  // ---- bundled layout (path 4) ----
+  if (want_path == 4 || want_path == 0) {
+    std::vector<int3> cands = ring_override(opts, 3072, 192, 2);
+    if (cands.empty())
+      cands = {make_int3(3072, 192, 2), make_int3(2048, 128, 3), make_int3(4096, 256, 2), make_int3(2048, 128, 2),
+               make_int3(1536, 96, 3), make_int3(1024, 64, 3), make_int3(1024, 64, 2), make_int3(512, 32, 2)};
+    std::vector<int3> fit;
+    for (const int3& c : cands)
+      if (tma_smem_bytes(n_pad, c.x, c.y, c.z, bv, bi, true, true) + 1024 <= (size_t)smem_optin) fit.push_back(c);
+    if (!fit.empty()) {
+      std::vector<BundleScen> B(N);
+      {
+        const int hw = std::max(1u, std::thread::hardware_concurrency());
+        const int nt = std::min(N, std::min(hw, 32));
+        std::atomic<int> next(0);
+        std::vector<std::thread> th;
+        for (int t = 0; t < nt; ++t)
+          th.emplace_back([&]() {
+            BankScratch bs;
+            std::vector<BundleInRow> rows;
+            for (int s = next++; s < N; s = next++) {
+              const int32_t* rp = pr->row_ptr[s];
+              rows.clear();
+              for (int32_t k : order[s]) {
+                const int32_t i = kept[k], a0 = rp[i];
+                BundleInRow br;
+                br.kept = k;
+                br.col = pr->col_idx[s] + a0;
+                br.val = pr->val[s] + a0;
+                br.len = rp[i + 1] - a0;
+                br.wc = (float)(cs[s] * pr->voxel_w[i]);
+                br.p = (float)pr->presc[i];
+                rows.push_back(br);
+              }
+              build_bundles(rows, &B[s], bs);
+            }
+          });
+        for (auto& t : th) t.join();
+      }
+      RowLists RB;
+      RB.rec_base.assign(N + 1, 0);
+      RB.nrows.assign(N, 0);
+      int64_t nbc = 0, recs = 0;
+      bool too_many = false;
+      for (int s = 0; s < N; ++s) {
+        ebase[s] = nbc;
+        ecount[s] = B[s].nbc;
+        nbc += B[s].nbc;
+        if (B[s].nbc > (int64_t)INT32_MAX - 64) too_many = true;
+        RB.nrows[s] = B[s].nb;
+        RB.rec_base[s + 1] = RB.rec_base[s] + B[s].nb + 1;
+        recbase_h[s] = (int)recs;
+        recs += 4 * (int64_t)(B[s].nb + 1);
+        n_bundles += B[s].nb;
+      }
+      recbase_h[N] = (int)recs;
+      RB.rec.resize(RB.rec_base[N]);
+      for (int s = 0; s < N; ++s)
+        for (int q = 0; q <= B[s].nb; ++q) RB.rec[RB.rec_base[s] + q] = B[s].rec[(size_t)4 * q];
+      if (!too_many && recs < (int64_t)INT32_MAX) {
+        for (const int3& c : fit) {
+          RingCfg rc;
+          rc.cmax = c.x;
+          rc.rmax = c.y;
+          rc.stages = c.z;
+          if (!build_chunks(RB, ebase, N, rc.cmax, rc.rmax, false, kBunMinLanes, &rc.chunks, &rc.scen_chunk,
+                            kBunKeep))
+            continue;
+          ring_cfgs.push_back(std::move(rc));
+          if (!autotune) break;
+        }
+      }
+      if (!ring_cfgs.empty()) {
+        bundled = true;
+        vpe = kBunRows;
+        NE = nbc;
+        col_h.resize((size_t)nbc);
+        val_h.resize((size_t)nbc * kBunRows);
+        rec_h.resize((size_t)recs);
+        for (int s = 0; s < N; ++s) {
+          std::copy(B[s].col.begin(), B[s].col.end(), col_h.begin() + ebase[s]);
+          std::copy(B[s].val.begin(), B[s].val.end(), val_h.begin() + ebase[s] * kBunRows);
+          std::copy(B[s].rec.begin(), B[s].rec.end(), rec_h.begin() + recbase_h[s]);
+          for (int q = 0; q < B[s].nb; ++q) rec_of_h[(size_t)s * m_act + q] = B[s].pos_of[q];
+          std::vector<int4>().swap(B[s].rec);
+          std::vector<int32_t>().swap(B[s].col);
+          std::vector<float>().swap(B[s].val);
+        }
+        R = std::move(RB);
+        ctas = 1;
+        dp.cmax = ring_cfgs[0].cmax;
+        dp.rmax = ring_cfgs[0].rmax;
+        dp.stages = ring_cfgs[0].stages;
+        chunks = ring_cfgs[0].chunks;
+        scen_chunk = ring_cfgs[0].scen_chunk;
+      }
+    }
+    if (!bundled && want_path == 4) {
+      free_plan(P);
+      set_error("bundled row path not possible for this plan (shared memory, or a bundle wider than a stage)");
+      return RPT_EUNSUPPORTED;
+    }
+  }
+  if (!bundled) {
+  // ---- per-scenario row lists, sorted by decreasing length; entries permuted to match ----
+  R.rec_base.assign(N + 1, 0);
+  R.nrows.assign(N, 0);
+  for (int s = 0; s < N; ++s) {
+    const int32_t* rp = pr->row_ptr[s];
     std::stable_sort(order[s].begin(), order[s].end(), [&](int32_t a, int32_t b) {
       return rp[kept[a] + 1] - rp[kept[a]] > rp[kept[b] + 1] - rp[kept[b]];
     });
@@ -372,8 +531,8 @@ int create_plan(const rpt_problem* pr, const rpt_device_opts* opts, rpt_plan** o
     R.rec_base[s + 1] = R.rec_base[s] + R.nrows[s] + 1;
   }
   R.rec.resize(R.rec_base[N]);
-  std::vector<int32_t> col_h((size_t)NNZp, 0);
-  std::vector<float> val_h((size_t)NNZp, 0.f);
+  col_h.assign((size_t)NNZp, 0);
+  val_h.assign((size_t)NNZp, 0.f);
   {
     // streaming-path plans store rows lane-interleaved (interleave_row)
     const bool interleave = (want_path == 3);
@@ -423,20 +582,10 @@ int create_plan(const rpt_problem* pr, const rpt_device_opts* opts, rpt_plan** o
     for (auto& t : th) t.join();
   }
   // ---- work decomposition: register-direct row blocks (default) or bulk-copy ring ----
-  const double per_lane = std::max(0, env_int("RPT_ROW_COST_LANE", 4));   // per-row overhead per lane, in entries
-  std::vector<int4> blocks;
-  std::vector<int> blk_first(N + 1, 0);
-  std::vector<ChunkDesc> chunks;
-  std::vector<int> scen_chunk;
-  bool use_tma = false, use_stream = false;
-  int ctas = 0;
-  const bool autotune = (opts && opts->autotune) || env_int("RPT_AUTOTUNE", 0) != 0;
-  std::vector<RingCfg> ring_cfgs;   // ring configurations that fit (all of them when autotuning)
+  const double per_lane = 4.0;   // register path: per-row overhead per lane, in entries
   if (want_path == 3) {
-    int smem_optin = 0;
-    cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, P->device);
-    dp.cmax = std::max(16, env_int("RPT_STR_CMAX", 1536)) & ~15;
-    dp.rmax = std::max(1, env_int("RPT_STR_RMAX", 128));
+    dp.cmax = std::max(16, (opts && opts->chunk_entries > 0) ? opts->chunk_entries : 1536) & ~15;
+    dp.rmax = std::max(1, (opts && opts->chunk_rows > 0) ? opts->chunk_rows : 128);
     dp.stages = 0;
     ctas = 1;
     if (stream_smem_bytes(n_pad, dp.rmax, true) + 1024 <= (size_t)smem_optin)
@@ -447,18 +596,12 @@ int create_plan(const rpt_problem* pr, const rpt_device_opts* opts, rpt_plan** o
       return RPT_EUNSUPPORTED;
     }
   } else if (want_path != 1) {
-    int smem_optin = 0;
-    cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, P->device);
     ctas = (opts && opts->ctas_per_sm > 0) ? opts->ctas_per_sm : 1;
     // ring configurations {entries per stage, rows per stage, stages}: the
-    // environment's, else the default followed by smaller ones for wide plans
+    // caller's, else the default followed by smaller ones for wide plans
     // (the spot vector and the accumulator share the shared memory with the ring)
-    std::vector<int3> cands;
-    if (std::getenv("RPT_TMA_CMAX") || std::getenv("RPT_TMA_STAGES") || std::getenv("RPT_TMA_RMAX"))
-      cands.push_back(make_int3(std::max(64, env_int("RPT_TMA_CMAX", 6144)) & ~15,
-                                std::max(8, env_int("RPT_TMA_RMAX", 512)),
-                                std::min(8, std::max(2, env_int("RPT_TMA_STAGES", 3)))));
-    else
+    std::vector<int3> cands = ring_override(opts, 6144, 512, 3);
+    if (cands.empty())
       cands = {make_int3(6144, 512, 3), make_int3(8192, 512, 2), make_int3(4096, 512, 4),
                make_int3(4096, 512, 3), make_int3(4096, 512, 2), make_int3(3072, 256, 3),
                make_int3(3072, 256, 2), make_int3(2048, 256, 4), make_int3(2048, 256, 2)};
@@ -482,11 +625,11 @@ int create_plan(const rpt_problem* pr, const rpt_device_opts* opts, rpt_plan** o
     }
     if (!use_tma && want_path == 2) {
       free_plan(P);
-      set_error("bulk-copy row path not possible for this plan (shared memory, or a row longer than RPT_TMA_CMAX)");
+      set_error("bulk-copy row path not possible for this plan (shared memory, or a row longer than a stage)");
       return RPT_EUNSUPPORTED;
     }
   }
-  const bool dyn = use_tma || use_stream;   // chunk queues
+  dyn = use_tma || use_stream;   // chunk queues
   if (dyn) {
     dp.path = use_tma ? 1 : 2;
     dp.grid = P->sm_count * ctas;
@@ -536,6 +679,21 @@ int create_plan(const rpt_problem* pr, const rpt_device_opts* opts, rpt_plan** o
     dp.slot_cap = 1;
     for (int s = 0; s < N; ++s) dp.slot_cap = std::max(dp.slot_cap, blk_first[s + 1] - blk_first[s]);
   }
+    NE = NNZp;
+    ebase = base;
+    ecount = pnnz;
+    rec_h = R.rec;
+    recbase_h = R.rec_base;
+    for (int s = 0; s < N; ++s)
+      for (int q = 0; q < R.nrows[s]; ++q) rec_of_h[(size_t)s * m_act + R.rec[R.rec_base[s] + q].w] = q;
+  }
+  if (bundled) {
+    dyn = true;
+    dp.path = 3;
+    dp.grid = P->sm_count * ctas;
+    dp.nblocks = dp.grid * N;
+    dp.slot_cap = dp.grid;
+  }
   // slot lists: static for the register path (block b of scenario s), written
   // by the kernel for the bulk-copy path
   std::vector<int> slot_count(N, 0), slot_list((size_t)N * dp.slot_cap, 0);
@@ -551,11 +709,11 @@ int create_plan(const rpt_problem* pr, const rpt_device_opts* opts, rpt_plan** o
   // ---- device memory ----
   // entry arrays are padded so that 16-entry aligned bulk copies stay inside them
   constexpr int64_t kPad = 64;
-  Alloc A{P};
+  Alloc A{P, (opts && opts->device_mem_cap > 0) ? (size_t)opts->device_mem_cap : 0};
   int64_t* d_base = A.get<int64_t>(N);
-  int32_t* d_col32 = A.get<int32_t>(NNZp + kPad);   // replaced by 16-bit indices if requested
-  float* d_val32 = A.get<float>(NNZp + kPad);       // replaced by quantised values if requested
-  int4* d_rec = A.get<int4>(R.rec.size());
+  int32_t* d_col32 = A.get<int32_t>(NE + kPad);            // replaced by 16-bit indices if requested
+  float* d_val32 = A.get<float>((NE + kPad) * vpe);        // replaced by quantised values if requested
+  int4* d_rec = A.get<int4>(rec_h.size());
   int* d_recbase = A.get<int>(N + 1);
   size_t chunk_cap = chunks.size();
   for (const RingCfg& rc : ring_cfgs) chunk_cap = std::max(chunk_cap, rc.chunks.size());
@@ -588,7 +746,10 @@ int create_plan(const rpt_problem* pr, const rpt_device_opts* opts, rpt_plan** o
   P->znew = A.get<double>(n);
   P->v32 = A.get<float>((size_t)N * n_pad);
   P->vz32 = A.get<float>(n_pad);
-  P->partial = A.get<float>((size_t)dp.nblocks * n_pad);
+  // partial slots: float (paths 1-3) or 64-bit fixed point (bundled path), n_pad each
+  P->partial = A.get<float>((size_t)dp.nblocks * n_pad * 2);
+  int* d_fexp = A.get<int>(N);
+  double* d_kbound = A.get<double>(2 * (size_t)N);
   P->objp = A.get<double>(dp.nblocks);
   P->gam = A.get<double>(N);
   P->tol = A.get<double>(N);
@@ -629,15 +790,12 @@ int create_plan(const rpt_problem* pr, const rpt_device_opts* opts, rpt_plan** o
       return cuda_fail(e, "upload");                                                       \
     }                                                                                      \
   } while (0)
-  RPT_CP(d_base, base.data(), N * sizeof(int64_t));
-  RPT_CP(d_col32, col_h.data(), (size_t)NNZp * sizeof(int32_t));
-  RPT_CP(d_val32, val_h.data(), (size_t)NNZp * sizeof(float));
-  RPT_CP(d_rec, R.rec.data(), R.rec.size() * sizeof(int4));
-  RPT_CP(d_recbase, R.rec_base.data(), (N + 1) * sizeof(int));
-  std::vector<int> rec_of((size_t)N * m_act, -1);
-  for (int s = 0; s < N; ++s)
-    for (int q = 0; q < R.nrows[s]; ++q) rec_of[(size_t)s * m_act + R.rec[R.rec_base[s] + q].w] = q;
-  RPT_CP(P->rec_of, rec_of.data(), rec_of.size() * sizeof(int));
+  RPT_CP(d_base, ebase.data(), N * sizeof(int64_t));
+  RPT_CP(d_col32, col_h.data(), (size_t)NE * sizeof(int32_t));
+  RPT_CP(d_val32, val_h.data(), (size_t)NE * vpe * sizeof(float));
+  RPT_CP(d_rec, rec_h.data(), rec_h.size() * sizeof(int4));
+  RPT_CP(d_recbase, recbase_h.data(), (N + 1) * sizeof(int));
+  RPT_CP(P->rec_of, rec_of_h.data(), rec_of_h.size() * sizeof(int));
   if (!dyn) RPT_CP(d_blocks, blocks.data(), blocks.size() * sizeof(int4));
   RPT_CP(P->diag, diag_h.data(), diag_h.size() * sizeof(float));
   if (dyn) {
@@ -655,9 +813,11 @@ int create_plan(const rpt_problem* pr, const rpt_device_opts* opts, rpt_plan** o
       (e = cudaMemsetAsync(d_objs, 0, sizeof(double) * N, st)) ||
       (dyn && (e = cudaMemsetAsync(d_qnext, 0, sizeof(int) * N, st))) ||
       (dyn && (e = cudaMemsetAsync(d_visited, 0, (size_t)N * dp.grid, st))) ||
-      (e = cudaMemsetAsync(d_col32 + NNZp, 0, sizeof(int32_t) * kPad, st)) ||
-      (e = cudaMemsetAsync(d_val32 + NNZp, 0, sizeof(float) * kPad, st)) ||
+      (e = cudaMemsetAsync(d_col32 + NE, 0, sizeof(int32_t) * kPad, st)) ||
+      (e = cudaMemsetAsync(d_val32 + NE * vpe, 0, sizeof(float) * kPad * vpe, st)) ||
       (e = cudaMemsetAsync(P->ctl, 0, sizeof(Ctl), st)) ||
+      (e = cudaMemsetAsync(d_fexp, 0, sizeof(int) * N, st)) ||
+      (e = cudaMemsetAsync(d_kbound, 0, sizeof(double) * 2 * N, st)) ||
       (e = cudaMemsetAsync(P->v32, 0, sizeof(float) * (size_t)N * n_pad, st)) ||
       (e = cudaMemsetAsync(P->vz32, 0, sizeof(float) * n_pad, st))) {
     free_plan(P);
@@ -679,13 +839,16 @@ int create_plan(const rpt_problem* pr, const rpt_device_opts* opts, rpt_plan** o
   dp.err = P->err;
   dp.col32 = d_col32;
   dp.val32 = d_val32;
+  dp.acc64 = bundled ? 1 : 0;
+  dp.fexp = d_fexp;
+  dp.kbound = d_kbound;
   // ---- quantised values / narrow indices ----
   const int qgrid = std::max(1, P->sm_count * 8), qblock = 256;
   if (pr->value_format != RPT_F32) {
     float* scale = A.get<float>((size_t)N * n_pad);
     unsigned int* mx = A.get<unsigned int>(n_pad);
-    void* q = pr->value_format == RPT_BF16 ? (void*)A.get<__nv_bfloat16>(NNZp + kPad)
-                                           : (void*)A.get<__nv_fp8_e4m3>(NNZp + kPad);
+    void* q = pr->value_format == RPT_BF16 ? (void*)A.get<__nv_bfloat16>((NE + kPad) * vpe)
+                                           : (void*)A.get<__nv_fp8_e4m3>((NE + kPad) * vpe);
     if (A.err != cudaSuccess) {
       free_plan(P);
       return cuda_fail(A.err, "device allocation");
@@ -694,17 +857,19 @@ int create_plan(const rpt_problem* pr, const rpt_device_opts* opts, rpt_plan** o
     for (int s = 0; s < N && e == cudaSuccess; ++s) {
       e = cudaMemsetAsync(mx, 0, sizeof(unsigned int) * n_pad, st);
       if (e) break;
-      if (pnnz[s] > 0) k_colmax<<<qgrid, qblock, 0, st>>>(d_val32 + base[s], d_col32 + base[s], pnnz[s], mx);
+      const int sh = vpe == 4 ? 2 : 0;   // value e of the scenario belongs to stored entry e >> sh
+      if (ecount[s] > 0)
+        k_colmax<<<qgrid, qblock, 0, st>>>(d_val32 + ebase[s] * vpe, d_col32 + ebase[s], ecount[s] * vpe, sh, mx);
       k_scales<<<(n_pad + 255) / 256, 256, 0, st>>>(mx, n, n_pad, fmt_max, scale + (size_t)s * n_pad);
-      if (pnnz[s] > 0) {
+      if (ecount[s] > 0) {
         if (pr->value_format == RPT_BF16)
-          k_quantise<__nv_bfloat16><<<qgrid, qblock, 0, st>>>(d_val32 + base[s], d_col32 + base[s], pnnz[s],
-                                                              scale + (size_t)s * n_pad,
-                                                              (__nv_bfloat16*)q + base[s]);
+          k_quantise<__nv_bfloat16><<<qgrid, qblock, 0, st>>>(d_val32 + ebase[s] * vpe, d_col32 + ebase[s],
+                                                              ecount[s] * vpe, sh, scale + (size_t)s * n_pad,
+                                                              (__nv_bfloat16*)q + ebase[s] * vpe);
         else
-          k_quantise<__nv_fp8_e4m3><<<qgrid, qblock, 0, st>>>(d_val32 + base[s], d_col32 + base[s], pnnz[s],
-                                                              scale + (size_t)s * n_pad,
-                                                              (__nv_fp8_e4m3*)q + base[s]);
+          k_quantise<__nv_fp8_e4m3><<<qgrid, qblock, 0, st>>>(d_val32 + ebase[s] * vpe, d_col32 + ebase[s],
+                                                              ecount[s] * vpe, sh, scale + (size_t)s * n_pad,
+                                                              (__nv_fp8_e4m3*)q + ebase[s] * vpe);
       }
       e = cudaGetLastError();
     }
@@ -718,12 +883,12 @@ int create_plan(const rpt_problem* pr, const rpt_device_opts* opts, rpt_plan** o
     dp.val32 = nullptr;
   }
   if (pr->index_width == 16) {
-    uint16_t* c16 = A.get<uint16_t>(NNZp + kPad);
+    uint16_t* c16 = A.get<uint16_t>(NE + kPad);
     if (A.err != cudaSuccess) {
       free_plan(P);
       return cuda_fail(A.err, "device allocation");
     }
-    k_to_u16<<<qgrid, qblock, 0, st>>>(d_col32, NNZp + kPad, c16);
+    k_to_u16<<<qgrid, qblock, 0, st>>>(d_col32, NE + kPad, c16);
     if ((e = cudaGetLastError())) {
       free_plan(P);
       return cuda_fail(e, "index conversion");
@@ -745,6 +910,21 @@ int create_plan(const rpt_problem* pr, const rpt_device_opts* opts, rpt_plan** o
   };
   if (pr->value_format != RPT_F32) release(d_val32);
   if (pr->index_width == 16) release(d_col32);
+  if (bundled) {
+    // bounds of the fixed-point accumulation, from the stored values
+    double* kc = nullptr;
+    if ((e = cudaMalloc(&kc, sizeof(double) * 2 * n_pad))) {
+      free_plan(P);
+      return cuda_fail(e, "device allocation");
+    }
+    e = bundle_bounds(dp, kc, kc + n_pad, d_kbound, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(kc);
+    if (e != cudaSuccess) {
+      free_plan(P);
+      return cuda_fail(e, "fixed-point bounds");
+    }
+  }
   if ((e = rowpass_prepare(dp))) {
     free_plan(P);
     return cuda_fail(e, "kernel attributes");
@@ -760,22 +940,26 @@ int create_plan(const rpt_problem* pr, const rpt_device_opts* opts, rpt_plan** o
   S.nnz = NNZ;
   // values and indices, plus one 4-byte row offset per stored row (the records'
   // weight and prescription are counted by the kernels' algorithmic bytes)
-  S.matrix_bytes = NNZ * (int64_t)(bi + bv) + (int64_t)(R.rec_base[N]) * 4;
+  S.matrix_bytes = bundled ? NE * (int64_t)(bi + kBunRows * bv) + (n_bundles + N) * 4
+                           : NNZ * (int64_t)(bi + bv) + (int64_t)(R.rec_base[N]) * 4;
+  S.bundles = bundled ? n_bundles : 0;
+  S.block_cols = bundled ? NE : 0;
+  S.bundle_fill = (bundled && NE > 0) ? (double)NNZ / (double)(kBunRows * NE) : 0.0;
   S.value_format = pr->value_format;
   S.index_width = pr->index_width;
   S.row_blocks = dp.nblocks;
   S.sm_count = P->sm_count;
   S.default_rho = 2.0 * (tr / N) / n;
   S.const_term = const_term;
-  S.row_path = dp.path == 2 ? 3 : (dp.path == 1 ? 2 : 1);
+  S.row_path = dp.path + 1;
   S.min_lanes = min_lanes;
   S.chunk_entries = dp.path >= 1 ? dp.cmax : 0;
   S.chunk_rows = dp.path >= 1 ? dp.rmax : 0;
-  S.stages = dp.path == 1 ? dp.stages : 0;
+  S.stages = (dp.path == 1 || dp.path == 3) ? dp.stages : 0;
   S.autotuned = 0;
   S.autotune_ms = 0.0;
   // ---- autotuning: time every fitting ring configuration on this plan, keep the fastest ----
-  if (use_tma && ring_cfgs.size() > 1) {
+  if ((use_tma || bundled) && ring_cfgs.size() > 1) {
     std::vector<double> ms(ring_cfgs.size(), 1e30);
     auto apply = [&](const RingCfg& rc) -> cudaError_t {
       cudaError_t ee = cudaMemcpyAsync(d_chunks, rc.chunks.data(), rc.chunks.size() * sizeof(ChunkDesc),
@@ -880,6 +1064,7 @@ void rpt_admm_params_default(rpt_admm_params* p) {
   p->subproblem = RPT_SUB_CG;
   p->trace = 0;
   p->bb_per_scenario = 0;
+  p->f_target = 0.0;
 }
 
 void rpt_pgd_params_default(rpt_pgd_params* p) {
@@ -986,6 +1171,77 @@ int rpt_admm_bb_solve_batched(rpt_plan* plan, const rpt_admm_params* params, dou
     for (int k = 0; k < nb; ++k)
       std::memcpy(x_out[k], x.data() + off[k], sizeof(double) * (size_t)(off[k + 1] - off[k]));
     return rc;
+  });
+}
+
+int rpt_plan_set_weights(rpt_plan* plan, const double* voxel_w, const double* presc) {
+  if (!plan || !voxel_w || !presc) {
+    set_error("rpt_plan_set_weights: null argument");
+    return RPT_EINVAL;
+  }
+  Plan* P = as_plan(plan);
+  const int m = P->dp.m, N = P->dp.N, n = P->dp.n, m_act = P->dp.m_act, n_pad = P->dp.n_pad;
+  for (int i = 0; i < m; ++i)
+    if (!std::isfinite(voxel_w[i]) || voxel_w[i] < 0 || !std::isfinite(presc[i]) || presc[i] < 0) {
+      set_error("rpt_plan_set_weights: voxel_w[" + std::to_string(i) + "] or presc not finite or negative");
+      return RPT_EINVAL;
+    }
+  return guarded([&] {
+    DeviceScope ds(P->device);
+    cudaStream_t st = P->stream;
+    std::vector<double> wk(m_act), pk(m_act);
+    double wmax = 0.0;
+    for (int k = 0; k < m_act; ++k) {
+      wk[k] = voxel_w[P->kept_rows[k]];
+      pk[k] = presc[P->kept_rows[k]];
+      wmax = std::max(wmax, wk[k]);
+    }
+    double* d = nullptr;                     // [wk | pk] then the fixed-point sums
+    cudaError_t e = cudaMalloc(&d, sizeof(double) * (2 * (size_t)m_act + n_pad));
+    if (e != cudaSuccess) return cuda_fail(e, "rpt_plan_set_weights");
+    unsigned long long* acc = reinterpret_cast<unsigned long long*>(d + 2 * (size_t)m_act);
+    e = cudaMemcpyAsync(d, wk.data(), sizeof(double) * m_act, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d + m_act, pk.data(), sizeof(double) * m_act, cudaMemcpyHostToDevice, st);
+    std::vector<unsigned long long> h(n_pad);
+    std::vector<float> diag((size_t)N * n);
+    double tr = 0.0;
+    for (int s = 0; s < N && e == cudaSuccess; ++s) {
+      // sum_i c_s w_i a_ij^2 <= c_s max(w) max_j sum_i a_ij^2: scale so that 4x that stays below 2^62
+      const double bound = P->scen_c[s] * wmax * P->colsq_max[s] * 4.0;
+      int ex = 0;
+      if (bound > 0.0) std::frexp(bound, &ex);
+      const double scale = std::ldexp(1.0, 60 - ex);
+      e = plan_reweight(P->dp, s, P->scen_c[s], d, d + m_act, scale, acc, st);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), acc, sizeof(unsigned long long) * n_pad,
+                                                cudaMemcpyDeviceToHost, st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+      long long t = 0;
+      for (int j = 0; j < n; ++j) {
+        diag[(size_t)s * n + j] = (float)((double)(long long)h[j] / scale);
+        t += (long long)h[j];
+      }
+      tr += (double)t / scale;
+    }
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(P->diag, diag.data(), sizeof(float) * diag.size(), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && P->dp.path == 3) e = bundle_bounds(P->dp, d, d + n_pad, const_cast<double*>(P->dp.kbound), st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(d);
+    if (e != cudaSuccess) return cuda_fail(e, "rpt_plan_set_weights");
+    // the constant of Eq. 2 in the order plan creation sums it
+    double c = 0.0;
+    for (int32_t i : P->dropped_rows)
+      for (int s = 0; s < N; ++s) c += P->scen_c[s] * voxel_w[i] * presc[i] * presc[i];
+    for (int s = 0; s < N; ++s)
+      for (int32_t k : P->empty_kept[s]) {
+        const int32_t i = P->kept_rows[k];
+        c += P->scen_c[s] * voxel_w[i] * presc[i] * presc[i];
+      }
+    P->stats.const_term = c;
+    P->stats.default_rho = 2.0 * (tr / N) / n;
+    P->lipschitz = 0.0;
+    P->chol_ready = false;
+    return RPT_OK;
   });
 }
 

@@ -34,14 +34,19 @@ constexpr unsigned kFull = 0xffffffffu;
 
 // Lower triangle of B_s (row-major n x n, zero on entry) += sum over kept rows k
 // in [blockIdx.x * kRB, +kRB) of c_s w_k a_k a_k^T (A~ = diag(sqrt(c_s w)) A).
-template <typename VT, typename IT>
+// BUN = false: CSR rows, rec_of[s][k] = position of kept row k in the row list.
+// BUN = true: row bundles, rec_of[s][q] = position of the q-th bundle in creation
+// (kept-row) order; the block takes kRB / 4 consecutive bundles.
+template <typename VT, typename IT, bool BUN>
 __global__ void __launch_bounds__(256)
 k_btb(DevPlan P, int s, const int* __restrict__ rec_of, float* __restrict__ B) {
+  constexpr int RPU = BUN ? kBundleRows : 1;    // rows per unit (bundle or row)
+  constexpr int UPB = kRB / RPU;                // units per block
   extern __shared__ __align__(16) unsigned char smem[];
   int* map = reinterpret_cast<int*>(smem);            // [n_pad]: flag, then position in U (-1: absent)
   int* U = map + P.n_pad;                             // [kUMax] sorted union of columns
   float* D = reinterpret_cast<float*>(U + kUMax);     // [kRB][kUMax] dense block of A~
-  __shared__ int rlo[kRB], rhi[kRB];
+  __shared__ int rlo[UPB], rhi[UPB];
   __shared__ float rw[kRB];
   __shared__ int wsum[8];
   __shared__ int running;
@@ -49,22 +54,43 @@ k_btb(DevPlan P, int s, const int* __restrict__ rec_of, float* __restrict__ B) {
   const int n = P.n;
   const int4* rec = P.rowrec + P.rec_base[s];
   const long long base = P.nnz_base[s];
-  const VT* val = vals<VT>(P) + base;
+  const VT* val = vals<VT>(P) + base * RPU;
   const IT* col = cols<IT>(P) + base;
   const float* cs = P.colscale ? P.colscale + (size_t)s * P.n_pad : nullptr;
+  const int nunits = BUN ? (P.rec_base[s + 1] - P.rec_base[s]) / 4 - 1 : P.m_act;
+  if (tid < UPB) {
+    const int k = blockIdx.x * UPB + tid;
+    const int q = k < nunits ? rec_of[(size_t)s * P.m_act + k] : -1;
+    rlo[tid] = q >= 0 ? rec[q * RPU].x : 0;
+    rhi[tid] = q >= 0 ? rec[(q + 1) * RPU].x : 0;
+  }
   if (tid < kRB) {
-    const int k = blockIdx.x * kRB + tid;
-    const int q = k < P.m_act ? rec_of[(size_t)s * P.m_act + k] : -1;
-    rlo[tid] = q >= 0 ? rec[q].x : 0;
-    rhi[tid] = q >= 0 ? rec[q + 1].x : 0;
-    rw[tid] = q >= 0 ? sqrtf(__int_as_float(rec[q].y)) : 0.f;
+    const int u = tid / RPU, r = tid % RPU;
+    const int k = blockIdx.x * UPB + u;
+    const int q = k < nunits ? rec_of[(size_t)s * P.m_act + k] : -1;
+    const float wc = q < 0 ? 0.f
+                     : BUN ? __int_as_float(reinterpret_cast<const int*>(&rec[4 * q + 1])[r])
+                           : __int_as_float(rec[q].y);
+    rw[tid] = sqrtf(wc);
   }
   if (tid == 0) running = 0;
   for (int j = tid; j < P.n_pad; j += blockDim.x) map[j] = 0;
   __syncthreads();
-  for (int r = 0; r < kRB; ++r)
-    for (int e = rlo[r] + tid; e < rhi[r]; e += blockDim.x)
-      if (to_f<VT>(val[e]) != 0.f) map[(int)col[e]] = 1;
+  auto entry = [&](int e, float (&a)[RPU]) {     // the unit's values at stored entry e
+    if constexpr (BUN) {
+      quad_v<true, VT>(val + 4 * (size_t)e, a);
+    } else {
+      a[0] = to_f<VT>(val[e]);
+    }
+  };
+  for (int u = 0; u < UPB; ++u)
+    for (int e = rlo[u] + tid; e < rhi[u]; e += blockDim.x) {
+      float a[RPU];
+      entry(e, a);
+      bool nz = false;
+      for (int r = 0; r < RPU; ++r) nz |= a[r] != 0.f;
+      if (nz) map[(int)col[e]] = 1;
+    }
   __syncthreads();
   // ordered compaction of the flags: map[c] = position in U, U[position] = c
   for (int c0 = 0; c0 < P.n_pad; c0 += blockDim.x) {
@@ -90,20 +116,20 @@ k_btb(DevPlan P, int s, const int* __restrict__ rec_of, float* __restrict__ B) {
   }
   const int nu = running;
   if (nu > kUMax) {
-    // rare: rows too spread out for one dense block; add each row's pairs directly
-    for (int r = 0; r < kRB; ++r) {
-      const int lo = rlo[r], len = rhi[r] - rlo[r];
+    // rare: rows too spread out for one dense block; add each unit's pairs directly
+    for (int u = 0; u < UPB; ++u) {
+      const int lo = rlo[u], len = rhi[u] - rlo[u];
       const long long pairs = (long long)len * len;
       for (long long p = tid; p < pairs; p += blockDim.x) {
         const int e1 = lo + (int)(p / len), e2 = lo + (int)(p % len);
         const int c1 = (int)col[e1], c2 = (int)col[e2];
         if (c1 < c2) continue;
-        float a1 = to_f<VT>(val[e1]), a2 = to_f<VT>(val[e2]);
-        if (cs) {
-          a1 *= cs[c1];
-          a2 *= cs[c2];
-        }
-        const float v = rw[r] * rw[r] * a1 * a2;
+        float a1[RPU], a2[RPU];
+        entry(e1, a1);
+        entry(e2, a2);
+        float v = 0.f;
+        for (int r = 0; r < RPU; ++r) v += rw[u * RPU + r] * rw[u * RPU + r] * a1[r] * a2[r];
+        if (cs) v *= cs[c1] * cs[c2];
         if (v != 0.f) atomicAdd(&B[(size_t)c1 * n + c2], v);
       }
     }
@@ -111,14 +137,13 @@ k_btb(DevPlan P, int s, const int* __restrict__ rec_of, float* __restrict__ B) {
   }
   for (int e = tid; e < kRB * nu; e += blockDim.x) D[(e / nu) * kUMax + (e % nu)] = 0.f;
   __syncthreads();
-  for (int r = 0; r < kRB; ++r)
-    for (int e = rlo[r] + tid; e < rhi[r]; e += blockDim.x) {
+  for (int u = 0; u < UPB; ++u)
+    for (int e = rlo[u] + tid; e < rhi[u]; e += blockDim.x) {
       const int c = (int)col[e];
-      float a = to_f<VT>(val[e]);
-      if (a != 0.f) {
-        if (cs) a *= cs[c];
-        D[r * kUMax + map[c]] = rw[r] * a;
-      }
+      float a[RPU];
+      entry(e, a);
+      for (int r = 0; r < RPU; ++r)
+        if (a[r] != 0.f) D[(u * RPU + r) * kUMax + map[c]] = rw[u * RPU + r] * (cs ? a[r] * cs[c] : a[r]);
     }
   __syncthreads();
   // pairs a >= b of U (row U[a] >= column U[b]: the lower triangle): a warp takes
@@ -287,12 +312,20 @@ int chol_prepare(Plan* P, double rho) {
   // 1. B_s = A~_s^T A~_s (lower), + (rho/2) I
   const size_t smem = sizeof(int) * ((size_t)dp.n_pad + kUMax) + sizeof(float) * kRB * kUMax;
   void* fn;
-  if (dp.index_width == 16)
-    fn = dp.value_format == 1 ? (void*)k_btb<__nv_bfloat16, uint16_t>
-       : dp.value_format == 2 ? (void*)k_btb<__nv_fp8_e4m3, uint16_t> : (void*)k_btb<float, uint16_t>;
-  else
-    fn = dp.value_format == 1 ? (void*)k_btb<__nv_bfloat16, int32_t>
-       : dp.value_format == 2 ? (void*)k_btb<__nv_fp8_e4m3, int32_t> : (void*)k_btb<float, int32_t>;
+  if (dp.path == 3) {
+    if (dp.index_width == 16)
+      fn = dp.value_format == 1 ? (void*)k_btb<__nv_bfloat16, uint16_t, true>
+         : dp.value_format == 2 ? (void*)k_btb<__nv_fp8_e4m3, uint16_t, true> : (void*)k_btb<float, uint16_t, true>;
+    else
+      fn = dp.value_format == 1 ? (void*)k_btb<__nv_bfloat16, int32_t, true>
+         : dp.value_format == 2 ? (void*)k_btb<__nv_fp8_e4m3, int32_t, true> : (void*)k_btb<float, int32_t, true>;
+  } else if (dp.index_width == 16) {
+    fn = dp.value_format == 1 ? (void*)k_btb<__nv_bfloat16, uint16_t, false>
+       : dp.value_format == 2 ? (void*)k_btb<__nv_fp8_e4m3, uint16_t, false> : (void*)k_btb<float, uint16_t, false>;
+  } else {
+    fn = dp.value_format == 1 ? (void*)k_btb<__nv_bfloat16, int32_t, false>
+       : dp.value_format == 2 ? (void*)k_btb<__nv_fp8_e4m3, int32_t, false> : (void*)k_btb<float, int32_t, false>;
+  }
   if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
     return done(cuda_fail(e, "kernel attribute"));
   const dim3 gb((dp.m_act + kRB - 1) / kRB);

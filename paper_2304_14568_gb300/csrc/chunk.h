@@ -3,6 +3,12 @@
 
 namespace rpt {
 
+// Row bundles (bundled ring path): rows per bundle, and block columns per lane
+// that the bundled kernel keeps in registers (the lane classes of the chunks
+// are cut for it).
+constexpr int kBundleRows = 4;
+constexpr int kBundleKeep = 6;
+
 // A run of consecutive rows of one scenario's row list, of one lanes-per-row
 // class, copied to shared memory (ring path) or claimed by a warp (streaming
 // path) as a unit.

@@ -24,6 +24,10 @@
 //               partial slot per scenario it visited (slot = cta * N + s).
 //   path 2 (streaming): the same chunk queues (chunks cut by row-length class),
 //               but every warp of the persistent CTA claims chunks on its own.
+//   path 3 (bundled ring): the ring of path 1 over row bundles (layout.h):
+//               rows grouped 4 at a time, one spot index per block column of a
+//               bundle, records of 4 int4 per bundle; 64-bit fixed-point
+//               accumulators (exact, order-independent sums).
 //   The CTA that finishes last compacts the slots of every scenario into an
 //   ordered list, sums the objective per scenario and resets the queues.
 #pragma once
@@ -45,7 +49,7 @@ struct DevPlan {
   int m, n, N, m_act, n_pad, nblocks;  // nblocks = partial slots
   int value_format;                   // RPT_F32 / RPT_BF16 / RPT_FP8E4M3
   int index_width;                    // 32 or 16
-  int path;                           // 0 register, 1 TMA ring, 2 streaming
+  int path;                           // 0 register, 1 TMA ring, 2 streaming, 3 bundled ring
   int grid;                           // CTAs of one row pass
   int cmax, rmax, stages;             // TMA path: entries / rows per stage, ring depth
   int slot_cap;                       // capacity of each scenario's slot list
@@ -74,7 +78,18 @@ struct DevPlan {
   const ChunkDesc* chunks;            // path 1: scenario-major chunk list
   int* err;                           // device error word (bounded waits that ran out)
   int inject_timeout;                 // testing: the ring's producer issues nothing (waits run out)
+  // path 3 (bundled ring): partial slots hold exact 64-bit fixed-point sums.  A
+  // pass on scenario s scales every contribution by 2^fexp[s], chosen from the
+  // bound |acc_c| <= kbound[2s] max|v_s| (+ kbound[2s+1] with the prescription
+  // term) so that no sum can overflow; the reducers scale back by 2^-fexp[s].
+  int acc64;                          // 1: partial slots are int64 fixed point (path 3)
+  int* fexp;                          // [N] scale exponent of the last scatter pass per scenario
+  const double* kbound;               // [2N] max_c sum_i c_s w_i |a_ic| ||a_i||_1 and max_c sum_i c_s w_i |a_ic| p_i
 };
+
+// Fixed-point exponent that marks a scenario whose staged vector was not finite
+// (the reducers then return NaN, so that divergence is still detected).
+constexpr int kFexpNaN = -100000;
 
 // ---- row-pass modes ---------------------------------------------------------
 enum RowMode : int {
@@ -141,7 +156,15 @@ size_t rowpass_smem(const DevPlan& P, int mode);
 int rowpass_threads(const DevPlan& P);
 cudaError_t rowpass_prepare(const DevPlan& P);
 size_t tma_smem_bytes(int n_pad, int cmax, int rmax, int stages, int value_bytes, int index_bytes,
-                      bool scatter);
+                      bool scatter, bool bundled = false);
 size_t stream_smem_bytes(int n_pad, int rmax, bool scatter);
 void* stream_rowpass_kernel(const DevPlan& P, int mode);   // rowstream.cu
+// Bundled layout, at plan creation: kbound[2s], kbound[2s+1] of every scenario
+// (DevPlan::kbound) from the stored values; kc, pc: scratch [n_pad] doubles.
+cudaError_t bundle_bounds(const DevPlan& P, double* kc, double* pc, double* kbound, cudaStream_t st);
+// New weights for scenario s (rpt_plan_set_weights): rewrite its row records from
+// wk, pk (per kept row) and c_s, and add sum_i c_s w_i a_ij^2 * scale to acc
+// (int64 fixed point, [n_pad], zeroed here).
+cudaError_t plan_reweight(const DevPlan& P, int s, double cs, const double* wk, const double* pk, double scale,
+                          unsigned long long* acc, cudaStream_t st);
 }  // namespace rpt

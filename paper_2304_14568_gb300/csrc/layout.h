@@ -10,6 +10,8 @@
 #include <vector_types.h>
 
 #include <algorithm>
+#include <climits>
+#include <cstring>
 #include <vector>
 
 #include "chunk.h"
@@ -22,9 +24,9 @@ namespace layout {
 // lanes of different rows can hit the same spot column in the same shared-memory
 // atomic, which serialises; short rows (the dose periphery) often do.
 constexpr int kKeep = 8;   // entries per lane held in registers by the row-pass kernels
-inline int lanes_for(int len, int min_lanes) {
+inline int lanes_for(int len, int min_lanes, int keep = kKeep) {
   int g = min_lanes;
-  while (g < 32 && g * kKeep < len) g <<= 1;
+  while (g < 32 && g * keep < len) g <<= 1;
   return g;
 }
 
@@ -56,9 +58,10 @@ inline int stream_lanes(int len) { return kStreamLanes[stream_class(len)]; }
 // scenario s's chunks.  For the ring, returns false if a single row does not fit
 // a stage; the streaming path takes such a row as a chunk of its own.
 inline bool build_chunks(const RowLists& R, const std::vector<int64_t>& base, int N, int cmax, int rmax, bool stream,
-                         int min_lanes, std::vector<ChunkDesc>* chunks, std::vector<int>* scen_chunk) {
+                         int min_lanes, std::vector<ChunkDesc>* chunks, std::vector<int>* scen_chunk,
+                         int keep = kKeep) {
   scen_chunk->assign(N + 1, 0);
-  auto cls = [&](int len) { return stream ? stream_class(len) : lanes_for(len, min_lanes); };
+  auto cls = [&](int len) { return stream ? stream_class(len) : lanes_for(len, min_lanes, keep); };
   for (int s = 0; s < N; ++s) {
     (*scen_chunk)[s] = (int)chunks->size();
     const int4* r = &R.rec[R.rec_base[s]];
@@ -103,17 +106,17 @@ struct BankScratch {
   std::vector<float> v;
 };
 
-inline void bank_balance(int32_t* col, float* val, int len, int G, BankScratch& S) {
-  if (len <= 1) return;
+inline void bank_order(const int32_t* col, int len, int G, BankScratch& S) {
   int cnt[32] = {0}, start[33], cur[32];
   for (int i = 0; i < len; ++i) ++cnt[col[i] & 31];
   start[0] = 0;
   for (int b = 0; b < 32; ++b) start[b + 1] = start[b] + cnt[b];
+  S.order.clear();
+  if (len <= 0) return;
   S.idx.resize(len);
   for (int b = 0; b < 32; ++b) cur[b] = start[b];
   for (int i = 0; i < len; ++i) S.idx[cur[col[i] & 31]++] = i;   // entries by bank, stable
   for (int b = 0; b < 32; ++b) cur[b] = start[b];
-  S.order.clear();
   int banks[32];
   while ((int)S.order.size() < len) {
     // banks by entries left, largest first
@@ -136,6 +139,11 @@ inline void bank_balance(int32_t* col, float* val, int len, int G, BankScratch& 
       }
     }
   }
+}
+
+inline void bank_balance(int32_t* col, float* val, int len, int G, BankScratch& S) {
+  if (len <= 1) return;
+  bank_order(col, len, G, S);
   S.c.assign(col, col + len);
   S.v.assign(val, val + len);
   for (int i = 0; i < len; ++i) {
@@ -166,6 +174,124 @@ inline void interleave_row(const int32_t* col, const float* val, int plen, int G
         val_out[dst] = val[src];
       }
   }
+}
+
+
+// ---- row bundles (the bundled ring path) -------------------------------------
+// A scenario's non-empty rows, in the plan's kept-row order (neighbouring voxels
+// when the caller numbers voxels spatially), are grouped kBunRows at a time.
+// A bundle stores the sorted union of its rows' spot columns once, and for each
+// such "block column" the kBunRows values of its rows (zero where a row has no
+// entry there).  One index then serves several entries, and the row pass does
+// one gather from the spot vector and one scatter into the accumulator per
+// block column instead of one per entry.  The block columns of a bundle are
+// bank-balanced for the bundle's lanes; bundles are sorted by decreasing
+// block-column count so that chunks hold bundles of one lane class.
+constexpr int kBunRows = kBundleRows;   // rows per bundle
+constexpr int kBunKeep = kBundleKeep;   // block columns per lane held in registers by the bundled kernel
+constexpr int kBunMinLanes = 8;
+
+inline int bundle_lanes(int ncols) { return lanes_for(ncols, kBunMinLanes, kBunKeep); }
+
+// Input rows of one scenario (non-empty, kept order): kept index, the row's
+// entries (strictly increasing columns), c_s w_i and p_i as stored.
+struct BundleInRow {
+  int32_t kept;
+  const int32_t* col;
+  const float* val;
+  int32_t len;
+  float wc, p;
+};
+
+// One scenario's bundles.  rec: 4 int4 per bundle, in sorted order
+// {block-column offset, 0, 0, 0}, {c_s w_i of rows 0..3}, {p_i of rows 0..3},
+// {kept index of rows 0..3 (-1: no row)}, then 4 int4 holding the scenario's
+// block-column count.  col [nbc], val [nbc][kBunRows].  pos_of: sorted position
+// of the q-th bundle in creation (kept-row) order.
+struct BundleScen {
+  std::vector<int4> rec;
+  std::vector<int32_t> col;
+  std::vector<float> val;
+  std::vector<int32_t> pos_of;
+  int nb = 0;
+  int64_t nbc = 0;
+};
+
+inline int32_t f2i_bits(float f) {
+  int32_t i;
+  std::memcpy(&i, &f, 4);
+  return i;
+}
+
+inline void build_bundles(const std::vector<BundleInRow>& rows, BundleScen* out, BankScratch& S) {
+  const int nr = (int)rows.size();
+  const int nb = (nr + kBunRows - 1) / kBunRows;
+  // per bundle: union of columns by a kBunRows-way merge, values in place
+  std::vector<std::vector<int32_t>> bc(nb);
+  std::vector<std::vector<float>> bv(nb);
+  for (int q = 0; q < nb; ++q) {
+    const int r0 = q * kBunRows, rn = std::min(kBunRows, nr - r0);
+    int pos[kBunRows] = {0};
+    std::vector<int32_t>& C = bc[q];
+    std::vector<float>& V = bv[q];
+    for (;;) {
+      int32_t cmin = INT32_MAX;
+      for (int r = 0; r < rn; ++r)
+        if (pos[r] < rows[r0 + r].len) cmin = std::min(cmin, rows[r0 + r].col[pos[r]]);
+      if (cmin == INT32_MAX) break;
+      C.push_back(cmin);
+      for (int r = 0; r < kBunRows; ++r) {
+        float v = 0.f;
+        if (r < rn && pos[r] < rows[r0 + r].len && rows[r0 + r].col[pos[r]] == cmin) v = rows[r0 + r].val[pos[r]++];
+        V.push_back(v);
+      }
+    }
+    // bank-balanced block-column order for the bundle's lanes
+    const int len = (int)C.size();
+    if (len > 1) {
+      bank_order(C.data(), len, bundle_lanes(len), S);
+      std::vector<int32_t> c2(len);
+      std::vector<float> v2((size_t)len * kBunRows);
+      for (int i = 0; i < len; ++i) {
+        c2[i] = C[S.order[i]];
+        for (int r = 0; r < kBunRows; ++r) v2[(size_t)i * kBunRows + r] = V[(size_t)S.order[i] * kBunRows + r];
+      }
+      C.swap(c2);
+      V.swap(v2);
+    }
+  }
+  std::vector<int> ord(nb);
+  for (int q = 0; q < nb; ++q) ord[q] = q;
+  std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return bc[a].size() > bc[b].size(); });
+  out->nb = nb;
+  out->pos_of.assign(nb, 0);
+  out->rec.assign((size_t)4 * (nb + 1), int4{0, 0, 0, 0});
+  int64_t total = 0;
+  for (int q = 0; q < nb; ++q) total += (int64_t)bc[q].size();
+  out->nbc = total;
+  out->col.resize((size_t)total);
+  out->val.resize((size_t)total * kBunRows);
+  int64_t off = 0;
+  for (int k = 0; k < nb; ++k) {
+    const int q = ord[k];
+    out->pos_of[q] = k;
+    const int r0 = q * kBunRows, rn = std::min(kBunRows, nr - r0);
+    int4* R4 = &out->rec[(size_t)4 * k];
+    R4[0] = int4{(int)off, 0, 0, 0};
+    int wc[kBunRows] = {0}, pp[kBunRows] = {0}, kp[kBunRows] = {-1, -1, -1, -1};
+    for (int r = 0; r < rn; ++r) {
+      wc[r] = f2i_bits(rows[r0 + r].wc);
+      pp[r] = f2i_bits(rows[r0 + r].p);
+      kp[r] = rows[r0 + r].kept;
+    }
+    R4[1] = int4{wc[0], wc[1], wc[2], wc[3]};
+    R4[2] = int4{pp[0], pp[1], pp[2], pp[3]};
+    R4[3] = int4{kp[0], kp[1], kp[2], kp[3]};
+    std::copy(bc[q].begin(), bc[q].end(), out->col.begin() + off);
+    std::copy(bv[q].begin(), bv[q].end(), out->val.begin() + off * kBunRows);
+    off += (int64_t)bc[q].size();
+  }
+  out->rec[(size_t)4 * nb] = int4{(int)off, 0, 0, 0};
 }
 
 }  // namespace layout

@@ -78,7 +78,10 @@ k_noalloc_pass(int m, int n, int n_pad, const int32_t* __restrict__ rp, const in
   for (int j = tid; j < n_pad; j += kNaThreads) out[j] = acc[j];
 }
 
-// u[j] = sum over CTAs c of scratch[c][j] (fixed order, compensated) + (rho/2) v[j]
+// u[j] = sum over CTAs c of scratch[c][j] + (rho/2) v[j].  The sum over the CTAs
+// runs in a fixed order with compensation; the partial of each CTA comes from
+// shared-memory float atomics whose order varies between runs, so results are
+// not bitwise reproducible (they stay within the float32 bound of the sums).
 __global__ void k_noalloc_reduce(int n, int ctas, const float* __restrict__ scratch, const float* __restrict__ v,
                                  float half_rho, float* __restrict__ u) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -94,7 +97,10 @@ __global__ void k_noalloc_reduce(int n, int ctas, const float* __restrict__ scra
 }
 
 std::mutex g_na_mutex;
-float* g_na_ptr[64] = {nullptr};     // device address of the scratch array, per device ordinal
+// device address of the scratch array, per device ordinal; looked up by the first
+// call on a device and kept for the process (not valid across a cudaDeviceReset
+// of that device, which the rpt.h entry rules out)
+float* g_na_ptr[64] = {nullptr};
 
 }  // namespace
 }  // namespace rpt

@@ -13,7 +13,7 @@ namespace rpt {
 // the scalars of the iteration (written and read by the kernels).
 struct Ctl {
   // ADMM parameters
-  double rho, inv_rho, eps_abs, eps_rel, bb_kappa, cg_theta, cg_eta0, cg_floor, tol_obj;
+  double rho, inv_rho, eps_abs, eps_rel, bb_kappa, cg_theta, cg_eta0, cg_floor, tol_obj, f_goal;
   double const_term;
   int max_iter, cg_max, bb_mode, z_mode, use_obj, precond;
   // ADMM scalars
@@ -92,6 +92,13 @@ struct Plan {
   int admm_chol_exec_obj = -1;
 
   std::vector<int32_t> kept_rows; // original row index of each device row
+  // what rpt_plan_set_weights needs: scenario weights c_s, rows dropped at
+  // creation (empty in every scenario), per scenario the kept rows that are empty
+  // there, and per scenario max_j sum_i a_ij^2 (the scale of the diagonal sums)
+  std::vector<double> scen_c;
+  std::vector<int32_t> dropped_rows;
+  std::vector<std::vector<int32_t>> empty_kept;
+  std::vector<double> colsq_max;
   std::vector<int32_t> batch_col_off;  // batched plan: problem k owns spots [off[k], off[k+1]); else empty
   double lipschitz = 0.0;         // cached 2 lambda_max, 0 = not computed
   bool state_valid = false;

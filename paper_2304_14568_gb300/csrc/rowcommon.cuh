@@ -107,6 +107,41 @@ __device__ __forceinline__ void stage_vector(const DevPlan& P, const float* __re
   }
 }
 
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Bundled path: stage v_s (scaled like stage_vector), zero the 64-bit
+// accumulator, and return this thread's max |staged value| (+inf or NaN if the
+// vector is not finite, so that the caller sees it).
+template <bool kScatter>
+__device__ __forceinline__ float stage_vector_max(const DevPlan& P, const float* __restrict__ vin, int v_stride,
+                                                  int s, float* sv, unsigned long long* acc, int t0, int nt) {
+  const float4* v4 = reinterpret_cast<const float4*>(vin + (size_t)s * v_stride);
+  const float4* cs4 =
+      P.colscale ? reinterpret_cast<const float4*>(P.colscale + (size_t)s * P.n_pad) : nullptr;
+  float4* sv4 = reinterpret_cast<float4*>(sv);
+  float m = 0.f;
+  bool bad = false;
+  for (int k = t0; k < P.n_pad / 4; k += nt) {
+    float4 x = v4[k];
+    if (cs4) {
+      const float4 q = cs4[k];
+      x.x *= q.x; x.y *= q.y; x.z *= q.z; x.w *= q.w;
+    }
+    sv4[k] = x;
+    m = fmaxf(m, fmaxf(fmaxf(fabsf(x.x), fabsf(x.y)), fmaxf(fabsf(x.z), fabsf(x.w))));
+    bad |= !(isfinite(x.x) && isfinite(x.y) && isfinite(x.z) && isfinite(x.w));
+  }
+  if (kScatter) {
+    ulonglong2* a2 = reinterpret_cast<ulonglong2*>(acc);
+    for (int k = t0; k < P.n_pad / 2; k += nt) a2[k] = make_ulonglong2(0ull, 0ull);
+  }
+  return bad ? __int_as_float(0x7f800000) : m;
+}
+
 template <bool kScatter>
 __device__ __forceinline__ void flush_acc(const DevPlan& P, int s, const float* acc, float* __restrict__ out,
                                           int t0, int nt) {

@@ -37,6 +37,32 @@ __device__ __forceinline__ double clampd(double v, double lo, double hi) {
 // Compensated sum, in the slot list's fixed order, of scenario s's row-pass
 // partials at column j.
 __device__ __forceinline__ double sum_partials(const DevPlan& P, const float* __restrict__ part, int s, int j) {
+  if (P.acc64) {
+    // bundled path: 64-bit fixed-point partials, summed exactly (every partial
+    // and every sum stays below 2^62 in magnitude), then scaled by 2^-fexp[s]
+    // and by the column scale of quantised values
+    const long long* pl = reinterpret_cast<const long long*>(part);
+    const int cnt = __ldcg(&P.slot_count[s]);
+    const int* list = P.slot_list + (size_t)s * P.slot_cap;
+    long long sum = 0;
+    int k = 0;
+    for (; k + 8 <= cnt; k += 8) {
+      int idx[8];
+      long long v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) idx[u] = __ldcg(&list[k + u]);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = __ldcg(pl + (size_t)idx[u] * P.n_pad + j);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) sum += v[u];
+    }
+    for (; k < cnt; ++k) sum += __ldcg(pl + (size_t)__ldcg(&list[k]) * P.n_pad + j);
+    const int fe = __ldcg(&P.fexp[s]);
+    if (fe == kFexpNaN) return __longlong_as_double(0x7ff8000000000000ll);
+    double r = ldexp((double)sum, -fe);
+    if (P.colscale) r *= (double)P.colscale[(size_t)s * P.n_pad + j];
+    return r;
+  }
   float sum = 0.f, c = 0.f;
   const int cnt = __ldcg(&P.slot_count[s]);
   const int* list = P.slot_list + (size_t)s * P.slot_cap;
@@ -496,7 +522,7 @@ __global__ void k_admm_y(DevPlan P, Ctl* C, const double* __restrict__ x, double
 }
 
 // <<<1, 256>>>.  Objective of z (after a kObj row pass): optional relative-change test
-// AND-ed with Eq. 9 (Sec. 2.3).
+// AND-ed with Eq. 9 (Sec. 2.3), or, with an objective target, f(z) <= target alone.
 __global__ void k_admm_obj(DevPlan P, Ctl* C, unsigned long long hadmm, int use_cond) {
   if (threadIdx.x == 0) {
     const double f = objective_sum(P) + C->const_term;
@@ -504,7 +530,7 @@ __global__ void k_admm_obj(DevPlan P, Ctl* C, unsigned long long hadmm, int use_
     C->f_prev = f;
     C->f_cur = f;
     C->passes += 1;
-    C->status = C->status && conv_obj;
+    C->status = C->f_goal > 0.0 ? (f <= C->f_goal) : (C->status && conv_obj);
     C->stop = C->status || C->diverged || C->k >= C->max_iter;
     set_cond(hadmm, use_cond, !C->stop);
   }
@@ -1022,7 +1048,8 @@ int admm_solve_impl(Plan* P, const rpt_admm_params* prm, const double* z0, const
       prm->bb_per_scenario < 0 || prm->bb_per_scenario > 1 ||
       prm->cg_precond < 0 || prm->cg_precond > 1 || prm->subproblem < 0 || prm->subproblem > 1 ||
       !(prm->bb_kappa >= 1.0) || !(prm->cg_theta > 0) || !(prm->cg_eta0 > 0) ||
-      !(prm->cg_floor_rel >= 0) || std::isnan(prm->tol_obj)) {
+      !(prm->cg_floor_rel >= 0) || std::isnan(prm->tol_obj) || !(prm->f_target >= 0.0) ||
+      !std::isfinite(prm->f_target)) {
     set_error("invalid ADMM parameters");
     return RPT_EINVAL;
   }
@@ -1040,7 +1067,7 @@ int admm_solve_impl(Plan* P, const rpt_admm_params* prm, const double* z0, const
           return RPT_EINVAL;
         }
   }
-  const int use_obj = std::isfinite(prm->tol_obj) ? 1 : 0;
+  const int use_obj = (std::isfinite(prm->tol_obj) || prm->f_target > 0.0) ? 1 : 0;
   const bool chol = prm->subproblem == RPT_SUB_CHOL;
   cudaStream_t st = P->stream;
   cudaError_t e;
@@ -1070,6 +1097,7 @@ int admm_solve_impl(Plan* P, const rpt_admm_params* prm, const double* z0, const
   c.cg_eta0 = prm->cg_eta0;
   c.cg_floor = prm->cg_floor_rel;
   c.tol_obj = prm->tol_obj;
+  c.f_goal = prm->f_target;
   c.const_term = P->stats.const_term;
   c.max_iter = prm->max_iter;
   c.cg_max = prm->cg_max;
@@ -1433,9 +1461,18 @@ int profile_row_pass(Plan* P, int mode, int reps, double* ms, double* bytes) {
   if (int rc = check_err(P)) return rc;
   if (ms) *ms = (double)t / reps;
   if (bytes) {
-    const double per_row = 4.0 * (mode == kResid ? 2 : 1);   // weight (+ prescription)
-    *bytes = (double)P->stats.matrix_bytes + per_row * (double)dp.N * dp.m_act +
-             2.0 * 4.0 * (double)dp.N * dp.n;
+    if (dp.path == 3) {
+      // bundled: stored block columns (4 values + index) and the 64-byte bundle
+      // records the ring copies, plus the spot vectors in and out
+      const int bv = dp.value_format == RPT_F32 ? 4 : (dp.value_format == RPT_BF16 ? 2 : 1);
+      const int bi = dp.index_width == 16 ? 2 : 4;
+      *bytes = (double)P->stats.block_cols * (4.0 * bv + bi) + 64.0 * (double)(P->stats.bundles + dp.N) +
+               2.0 * 4.0 * (double)dp.N * dp.n;
+    } else {
+      const double per_row = 4.0 * (mode == kResid ? 2 : 1);   // weight (+ prescription)
+      *bytes = (double)P->stats.matrix_bytes + per_row * (double)dp.N * dp.m_act +
+               2.0 * 4.0 * (double)dp.N * dp.n;
+    }
   }
   return RPT_OK;
 }

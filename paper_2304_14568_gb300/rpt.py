@@ -27,7 +27,7 @@ EXPORTED = [
     "rpt_version", "rpt_mlp_train_params_default", "rpt_mlp_create", "rpt_mlp_destroy", "rpt_mlp_param_count",
     "rpt_mlp_get_params", "rpt_mlp_set_params", "rpt_mlp_loss_grad", "rpt_mlp_train", "rpt_mlp_predict",
     "rpt_admm_bb_solve_learned", "rpt_trace_get", "rpt_plans_create_batched", "rpt_plan_batch_query",
-    "rpt_admm_bb_solve_batched", "rpt_mlp_infer",
+    "rpt_admm_bb_solve_batched", "rpt_mlp_infer", "rpt_mlp_set_compute", "rpt_plan_set_weights",
 ]
 
 
@@ -55,7 +55,15 @@ class _Problem(C.Structure):
 
 class _DeviceOpts(C.Structure):
     _fields_ = [("device", C.c_int32), ("stream", C.c_void_p), ("ctas_per_sm", C.c_int32),
-                ("row_path", C.c_int32), ("autotune", C.c_int32)]
+                ("row_path", C.c_int32), ("autotune", C.c_int32), ("chunk_entries", C.c_int32),
+                ("chunk_rows", C.c_int32), ("stages", C.c_int32), ("min_lanes", C.c_int32),
+                ("inject_timeout", C.c_int32), ("device_mem_cap", C.c_int64)]
+
+
+def _device_opts(device=0, stream=None, ctas_per_sm=0, row_path=0, autotune=0, chunk_entries=0, chunk_rows=0,
+                 stages=0, min_lanes=0, inject_timeout=0, device_mem_cap=0):
+    return _DeviceOpts(device, stream, ctas_per_sm, row_path, autotune, chunk_entries, chunk_rows, stages,
+                       min_lanes, inject_timeout, device_mem_cap)
 
 
 class AdmmParams(C.Structure):
@@ -65,7 +73,7 @@ class AdmmParams(C.Structure):
                 ("cg_max", C.c_int32), ("cg_theta", C.c_double), ("cg_eta0", C.c_double),
                 ("cg_floor_rel", C.c_double), ("use_graph", C.c_int32), ("check_every", C.c_int32),
                 ("resume", C.c_int32), ("cg_precond", C.c_int32), ("subproblem", C.c_int32),
-                ("trace", C.c_int32), ("bb_per_scenario", C.c_int32)]
+                ("trace", C.c_int32), ("bb_per_scenario", C.c_int32), ("f_target", C.c_double)]
 
 
 class PgdParams(C.Structure):
@@ -92,7 +100,8 @@ class _Stats(C.Structure):
                 ("default_rho", C.c_double), ("const_term", C.c_double),
                 ("row_path", C.c_int32), ("min_lanes", C.c_int32), ("chunk_entries", C.c_int32),
                 ("chunk_rows", C.c_int32), ("stages", C.c_int32), ("autotuned", C.c_int32),
-                ("autotune_ms", C.c_double)]
+                ("autotune_ms", C.c_double), ("bundles", C.c_int64), ("block_cols", C.c_int64),
+                ("bundle_fill", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -167,6 +176,10 @@ def lib():
     L.rpt_mlp_predict.restype = C.c_int
     L.rpt_mlp_infer.argtypes = [C.c_void_p, fp, fp]
     L.rpt_mlp_infer.restype = C.c_int
+    L.rpt_mlp_set_compute.argtypes = [C.c_void_p, C.c_int32]
+    L.rpt_mlp_set_compute.restype = C.c_int
+    L.rpt_plan_set_weights.argtypes = [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double)]
+    L.rpt_plan_set_weights.restype = C.c_int
     L.rpt_admm_bb_solve_learned.argtypes = [C.c_void_p, C.c_void_p, fp, dp, C.POINTER(AdmmParams), dp,
                                             C.POINTER(_Info), C.POINTER(C.c_int32)]
     L.rpt_admm_bb_solve_learned.restype = C.c_int
@@ -268,13 +281,15 @@ class Plan:
     """A device-resident plan (rpt_plan_create / rpt_plan_destroy)."""
 
     def __init__(self, m, n, N, row_ptr, col_idx, val, voxel_w, presc, scen_weight=None,
-                 lb=None, ub=None, value_format=F32, index_width=32, device=0, stream=None,
-                 ctas_per_sm=0, row_path=0, autotune=0):
+                 lb=None, ub=None, value_format=F32, index_width=32, **device_opts):
+        """device_opts: the fields of rpt_device_opts (device, stream, ctas_per_sm,
+        row_path, autotune, chunk_entries, chunk_rows, stages, min_lanes,
+        inject_timeout, device_mem_cap)."""
         L = lib()
         m, n, N = int(m), int(n), int(N)
         pr, _keep = _problem_struct(m, n, N, row_ptr, col_idx, val, voxel_w, presc, scen_weight, lb, ub,
                                     value_format, index_width)
-        opts = _DeviceOpts(device, stream, ctas_per_sm, row_path, autotune)
+        opts = _device_opts(**device_opts)
         h = C.c_void_p()
         _check(L.rpt_plan_create(C.byref(pr), C.byref(opts), C.byref(h)))
         self._h = h
@@ -286,14 +301,13 @@ class Plan:
         return cls(*_problem_fields(prob), **kw)
 
     @classmethod
-    def batched(cls, problems, value_format=F32, index_width=32, device=0, stream=None, ctas_per_sm=0,
-                row_path=0, autotune=0):
+    def batched(cls, problems, value_format=F32, index_width=32, **device_opts):
         """One plan holding several problems side by side (rpt_plans_create_batched)."""
         L = lib()
         built = [_problem_struct(*_problem_fields(p), value_format=value_format, index_width=index_width)
                  for p in problems]
         arr = (C.POINTER(_Problem) * len(built))(*[C.pointer(pr) for pr, _ in built])
-        opts = _DeviceOpts(device, stream, ctas_per_sm, row_path, autotune)
+        opts = _device_opts(**device_opts)
         h = C.c_void_p()
         _check(L.rpt_plans_create_batched(len(built), arr, C.byref(opts), C.byref(h)))
         self = cls.__new__(cls)
@@ -301,6 +315,12 @@ class Plan:
         st = self.stats()
         self.m, self.n, self.N = st["m"], st["n"], st["N"]
         return self
+
+    def set_weights(self, voxel_w, presc):
+        """New voxel weights and prescription for the same matrices (rpt_plan_set_weights)."""
+        w = _vec(voxel_w, np.float64, self.m, "voxel_w")
+        p = _vec(presc, np.float64, self.m, "presc")
+        _check(lib().rpt_plan_set_weights(self._h, _dptr(w), _dptr(p)))
 
     def batch_offsets(self):
         """Spot ranges of the plan's problems: offsets [n_plans + 1] (rpt_plan_batch_query)."""
@@ -443,11 +463,14 @@ def mlp_train_params(**kw) -> MlpTrainParams:
 class Mlp:
     """Learned warm-start network (rpt_mlp_*)."""
 
-    def __init__(self, n_in, n_hidden, n_hidden_layers, n_out, seed=0, device=0):
+    def __init__(self, n_in, n_hidden, n_hidden_layers, n_out, seed=0, device=0, compute=None):
+        """compute: BF16 (tensor cores, the library default) or F32 (CUDA cores)."""
         h = C.c_void_p()
         _check(lib().rpt_mlp_create(int(n_in), int(n_hidden), int(n_hidden_layers), int(n_out), int(seed),
                                     int(device), C.byref(h)))
         self._h = h
+        if compute is not None:
+            _check(lib().rpt_mlp_set_compute(h, int(compute)))
         self.n_in, self.n_out = int(n_in), int(n_out)
 
     def close(self):

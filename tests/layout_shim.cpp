@@ -64,4 +64,35 @@ int shim_build_chunks(int N, const int* nrows, const int* plen, const int64_t* b
   return (int)chunks.size();
 }
 
+// Bundles of one scenario's rows (CSR rp [nrows+1], ci, va; row i has kept
+// index kept[i], weight wc[i] and prescription pr[i]).  Returns the block-column
+// count (or -2 when cap_bc / cap_b is too small) and writes col [nbc], val
+// [nbc][4], rec [(nb+1)*4][4] (int32 fields), pos_of [nb], *nb_out.
+int64_t shim_build_bundles(int nrows, const int32_t* rp, const int32_t* ci, const float* va, const int32_t* kept,
+                           const float* wc, const float* pr, int64_t cap_bc, int cap_b, int32_t* col, float* val,
+                           int32_t* rec, int32_t* pos_of, int* nb_out) {
+  std::vector<BundleInRow> rows(nrows);
+  for (int i = 0; i < nrows; ++i)
+    rows[i] = BundleInRow{kept[i], ci + rp[i], va + rp[i], rp[i + 1] - rp[i], wc[i], pr[i]};
+  BundleScen B;
+  BankScratch S;
+  build_bundles(rows, &B, S);
+  *nb_out = B.nb;
+  if (B.nbc > cap_bc || B.nb > cap_b) return -2;
+  for (int64_t k = 0; k < B.nbc; ++k) {
+    col[k] = B.col[k];
+    for (int r = 0; r < kBunRows; ++r) val[k * kBunRows + r] = B.val[k * kBunRows + r];
+  }
+  for (size_t k = 0; k < B.rec.size(); ++k) {
+    rec[4 * k] = B.rec[k].x;
+    rec[4 * k + 1] = B.rec[k].y;
+    rec[4 * k + 2] = B.rec[k].z;
+    rec[4 * k + 3] = B.rec[k].w;
+  }
+  for (int q = 0; q < B.nb; ++q) pos_of[q] = B.pos_of[q];
+  return B.nbc;
+}
+
+int shim_bundle_lanes(int ncols) { return bundle_lanes(ncols); }
+
 }  // extern "C"

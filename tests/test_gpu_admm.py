@@ -126,24 +126,43 @@ def test_iterates_match_oracle(rpt, bb, zm, per_scen):
             assert info["r_prim"] == pytest.approx(ref["r_prim"], rel=1e-3, abs=1e-5 * sz)
 
 
-@pytest.mark.parametrize("row_path", [0, 3])
-def test_converges_to_exact_optimum_tiny_plain(rpt, tiny_plain, row_path):
-    """Default parameters, tight tolerances: objective within 1e-6 of the exact
-    box-constrained optimum (lsq_linear), certificates near zero; default row
-    path and the streaming row path."""
-    prob, W, xs, fstar = tiny_plain
+@pytest.fixture(scope="module")
+def random_interior():
+    """A random problem whose optimum is interior in most coordinates (the box is
+    loose), so that the stacked dose is a sensitive check."""
+    prob = random_problem(29, m=700, n=60, N=4, mean_row=12.0, ub=1e3, scen_weight=True)
+    W = Weighted(prob)
+    xs = lsq_box(W)
+    return prob, W, xs, W.f(xs)
+
+
+@pytest.mark.parametrize("row_path", [0, 2, 3])
+@pytest.mark.parametrize("case", ["tiny", "random"])
+def test_objective_and_dose_parity_at_tight_tolerance(rpt, tiny_plain, random_interior, row_path, case):
+    """Default parameters at eps_abs = eps_rel = 1e-7 (the tightest decade the
+    float32 passes reach): objective within 1e-6 of the exact box-constrained
+    optimum (lsq_linear), and the stacked weighted dose D = [A~_1 z; ...; A~_N z]
+    within 1e-6 relative of D(z*), the stated tolerance of the float32 path
+    (measured: about 1e-7 on the tiny config, on every row path).  The
+    deterministic bundled path (0, the default) converges by Eq. 9; the float
+    atomics of the other paths may keep the residual just above eps while the
+    iterate already meets both tolerances, so their status is not asserted."""
+    prob, W, xs, fstar = tiny_plain if case == "tiny" else random_interior
     with plan_of(rpt, prob, row_path=row_path) as P:
         z, info = P.admm_bb_solve(eps_abs=1e-7, eps_rel=1e-7, max_iter=20000)
     f_gpu = W.f(z)
     assert np.all(z >= prob.lb) and np.all(z <= prob.ub)
     assert (f_gpu - fstar) / fstar <= 1e-6, ((f_gpu - fstar) / fstar, info)
     assert info["f"] == pytest.approx(f_gpu, rel=1e-6)
-    c = certificates(W, z)
-    assert c["pg"] < 1e-3
+    assert certificates(W, z)["pg"] < 1e-3
     Ds = W.stacked_weighted_dose(xs)
     Dg = W.stacked_weighted_dose(z)
     rel_dose = np.linalg.norm(Dg - Ds) / np.linalg.norm(Ds)
-    assert rel_dose <= 1e-3, rel_dose
+    print(f"{case} path {row_path}: status {info['status']} iterations {info['iterations']} "
+          f"objective gap {(f_gpu - fstar) / fstar:.2e} dose error {rel_dose:.2e}")
+    assert rel_dose <= 1e-6, rel_dose
+    if row_path == 0:
+        assert info["status"] == 0
 
 
 @pytest.mark.parametrize("sub", [0, 1])
@@ -257,7 +276,7 @@ def test_warm_start_and_dual_start(rpt):
     assert abs(W.f(z) - W.f(xs)) / W.f(xs) < 1e-6
 
 
-@pytest.mark.parametrize("row_path", [0, 3])
+@pytest.mark.parametrize("row_path", [0, 2, 3])
 def test_pgd_matches_oracle(rpt, tiny_plain, row_path):
     prob, W, xs, fstar = tiny_plain
     L = lipschitz(W)

@@ -34,7 +34,7 @@ def test_batched_operator_and_optimum_block_by_block(rpt):
         st = P.stats()
         U = P.apply_normal(V, 1.1)
         z, info = P.admm_bb_solve(eps_abs=1e-8, eps_rel=1e-8, max_iter=20000)
-    assert st["row_path"] == 2 and st["autotuned"] >= 2 and st["autotune_ms"] > 0
+    assert st["row_path"] == 4 and st["autotuned"] >= 2 and st["autotune_ms"] > 0
     for k, (r0, m, c0, n) in enumerate(big.meta["blocks"]):
         W = Weighted(probs[k])
         kb = fp32_op_bound(probs[k])
@@ -50,8 +50,8 @@ def test_batched_operator_and_optimum_block_by_block(rpt):
 
 
 def test_wide_plan_gets_a_ring_that_fits(rpt):
-    # 14,000 spots: the spot vector and the accumulator take 112 KB of shared
-    # memory, so the default 3 x 6144-entry ring does not fit beside them
+    # 14,000 spots: the spot vector and the 64-bit accumulator take 168 KB of
+    # shared memory, so the default 2 x 3072-block-column ring does not fit beside them
     prob = random_problem(34, m=600, n=14000, N=2, mean_row=30.0, long_rows=0)
     W = Weighted(prob)
     rng = np.random.default_rng(9)
@@ -59,7 +59,7 @@ def test_wide_plan_gets_a_ring_that_fits(rpt):
     with plan_of(rpt, prob) as P:
         st = P.stats()
         U = P.apply_normal(V, 0.0)
-    assert st["row_path"] == 2 and (st["chunk_entries"], st["stages"]) != (6144, 3)
+    assert st["row_path"] == 4 and (st["chunk_entries"], st["stages"]) != (3072, 2)
     k = fp32_op_bound(prob)
     for s in range(prob.N):
         ref = W.normal_apply(s, V[s], 0.0)

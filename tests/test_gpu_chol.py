@@ -22,7 +22,7 @@ def rpt():
     return gpu_lib()
 
 
-@pytest.mark.parametrize("path", [1, 2, 3])
+@pytest.mark.parametrize("path", [1, 2, 3, 4])
 def test_iterates_match_oracle_cholesky_admm(rpt, path):
     """Error budget of one x-update: the FP32 inverse of B_s (Cholesky, then
     L^{-T} L^{-1}) is accurate to about 4 n cond(B_s) eps32 relative, and B_s

@@ -37,7 +37,7 @@ def big(rpt):
 def test_plan_is_the_benchmarked_configuration(big):
     prob, W, P = big
     st = P.stats()
-    assert st["row_path"] == 2 and st["nnz"] == sum(int(v.size) for v in prob.val)
+    assert st["row_path"] == 4 and st["nnz"] == sum(int(v.size) for v in prob.val)
     assert st["m_active"] == 85495 and prob.n == 5000 and prob.N == 13
 
 

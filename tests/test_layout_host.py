@@ -31,6 +31,9 @@ def shim(tmp_path_factory):
     L.shim_interleave_row.argtypes = [i32p, f32p, C.c_int, C.c_int, i32p, f32p]
     L.shim_build_chunks.argtypes = [C.c_int, i32p, i32p, i64p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
                                     i64p, i32p, i32p, i32p, i32p, i32p, i32p, i32p]
+    L.shim_build_bundles.argtypes = [C.c_int, i32p, i32p, f32p, i32p, f32p, f32p, C.c_int64, C.c_int,
+                                     i32p, f32p, i32p, i32p, C.POINTER(C.c_int)]
+    L.shim_build_bundles.restype = C.c_int64
     return L
 
 
@@ -143,3 +146,66 @@ def test_ring_refuses_a_row_longer_than_a_stage(shim):
     assert n == -1
     n, *_ = _chunks(shim, [2], [4096, 8], [0], 2048, 64, True)          # the streaming path takes it alone
     assert n == 2
+
+
+def _bundles(shim, rp, ci, va, kept, wc, pr):
+    nr = rp.size - 1
+    cap_bc, cap_b = int(rp[-1]) + 8, nr // 4 + 2
+    col = np.zeros(cap_bc, np.int32)
+    val = np.zeros(cap_bc * 4, np.float32)
+    rec = np.zeros((cap_b + 1) * 16, np.int32)
+    pos = np.zeros(cap_b, np.int32)
+    nb = C.c_int()
+    nbc = shim.shim_build_bundles(nr, rp, ci, va, kept, wc, pr, cap_bc, cap_b, col, val, rec, pos, C.byref(nb))
+    assert nbc >= 0
+    return col[:nbc], val[:4 * nbc].reshape(-1, 4), rec[:(nb.value + 1) * 16].reshape(-1, 4, 4), pos[:nb.value]
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_bundles_store_every_entry_once(shim, seed):
+    """Row bundles (the bundled ring's layout): 4 consecutive rows per bundle;
+    every entry of the input appears exactly once, at its row slot and spot
+    column; absent entries are stored as 0; every bundle's columns are distinct;
+    bundles are sorted by decreasing width; pos_of is a permutation; records hold
+    the offsets, weights, prescriptions and kept indices (-1 for missing rows)."""
+    rng = np.random.default_rng(seed)
+    nr = int(rng.integers(1, 60))
+    n = int(rng.choice([5, 40, 300]))
+    lens = rng.integers(1, min(n, 50) + 1, size=nr)
+    rp = np.concatenate([[0], np.cumsum(lens)]).astype(np.int32)
+    ci = np.concatenate([np.sort(rng.choice(n, size=l, replace=False)) for l in lens]).astype(np.int32)
+    va = (rng.random(rp[-1]) + 0.01).astype(np.float32)
+    kept = np.sort(rng.choice(10 * nr, size=nr, replace=False)).astype(np.int32)
+    wc = rng.random(nr).astype(np.float32)
+    pr = rng.random(nr).astype(np.float32)
+    col, val, rec, pos = _bundles(shim, rp, ci, va, kept, wc, pr)
+    nb = (nr + 3) // 4
+    assert pos.size == nb and sorted(pos.tolist()) == list(range(nb))
+    widths = [rec[b + 1, 0, 0] - rec[b, 0, 0] for b in range(nb)]
+    assert all(w1 >= w2 for w1, w2 in zip(widths, widths[1:]))
+    assert rec[nb, 0, 0] == col.size
+    seen = np.zeros(rp[-1], bool)
+    for q in range(nb):
+        b = pos[q]
+        lo, hi = rec[b, 0, 0], rec[b + 1, 0, 0]
+        cols = col[lo:hi]
+        assert np.unique(cols).size == cols.size
+        assert shim.shim_bundle_lanes(int(hi - lo)) in (8, 16, 32)
+        for r in range(4):
+            i = 4 * q + r
+            if i >= nr:
+                assert rec[b, 3, r] == -1 and rec[b, 1, r] == 0 and np.all(val[lo:hi, r] == 0)
+                continue
+            assert rec[b, 3, r] == kept[i]
+            assert rec[b, 1, r] == wc[i:i + 1].view(np.int32)[0] and rec[b, 2, r] == pr[i:i + 1].view(np.int32)[0]
+            row = dict(zip(ci[rp[i]:rp[i + 1]].tolist(), range(rp[i], rp[i + 1])))
+            for k in range(lo, hi):
+                e = row.get(int(col[k]))
+                if e is None:
+                    assert val[k, r] == 0.0
+                else:
+                    assert val[k, r] == va[e] and not seen[e]
+                    seen[e] = True
+            # the union covers the row
+            assert set(row) <= set(cols.tolist())
+    assert seen.all()
