@@ -456,6 +456,8 @@ def main():
     ap.add_argument("--no-forms", action="store_true", help="skip the reduced-precision storage forms")
     ap.add_argument("--no-chol", action="store_true", help="skip the cached-factor subproblem solver")
     ap.add_argument("--no-variants", action="store_true", help="skip the per-scenario BB step variant")
+    ap.add_argument("--no-exact", action="store_true", help="skip the exact-sum (bitwise reproducible) variant")
+    ap.add_argument("--no-tto", action="store_true", help="skip the times to the objective target (1 + 1e-4) f*")
     ap.add_argument("--dvh", action="store_true",
                     help="also report DVH bands and dose metrics over the scenarios for the solved plan")
     ap.add_argument("--scenario-sweep", action="store_true",
@@ -540,11 +542,18 @@ def main():
     peak, peak_src = _peaks()
     achieved = bytes_pass / (ms_pass * 1e-3) / 1e9
     passes_per_solve = statistics.mean(i["row_passes"] for i in infos)
-    traffic = None
+    # DRAM bytes of one launch from a stored ncu capture of this kernel on this
+    # workload (dram__bytes_read.sum + dram__bytes_write.sum), keyed by the kernel
+    # variant; null when no capture of the variant in use is stored
+    variant = ("bundled-" + ("exact" if st["exact_sums"] else "float") if st["row_path"] == 4
+               else {1: "register", 2: "ring", 3: "stream"}[st["row_path"]])
+    traffic, traffic_src = None, None
     tr_path = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(tr_path):
         try:
-            traffic = json.load(open(tr_path)).get("rowpass_normal_f32_bytes_per_launch")
+            rec = json.load(open(tr_path)).get(f"kNormal f32 int32 {variant}")
+            if rec:
+                traffic, traffic_src = rec["bytes_per_launch"], rec["source"]
         except Exception:
             traffic = None
 
@@ -568,15 +577,64 @@ def main():
                  "solve_seconds_info": statistics.mean(i["seconds"] for i in infos)},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
-                     "kernel": ("k_rowpass_tma" if st["row_path"] == 2 else "k_rowpass") +
-                               "<kNormal,f32,int32> (CG operator pass, all scenarios)",
+                     "traffic_source": traffic_src or "no stored capture of this kernel variant",
+                     "kernel": ("k_rowpass_tma" if st["row_path"] in (2, 4) else "k_rowpass") +
+                               f"<kNormal,f32,int32,{variant}> (CG operator pass, all scenarios)",
                      "ms_per_launch": ms_pass, "bytes_per_launch": bytes_pass,
+                     "bytes_note": ("bundled layout: stored block columns (4 values + 1 index, 20 B) and 64-byte "
+                                    "bundle records, plus the spot vectors in and out"
+                                    if st["row_path"] == 4 else "CSR: values + indices, row records, vectors"),
+                     "csr_equivalent_gbs": (st["nnz"] * 8 + 4.0 * prob.N * st["m_active"] + 8.0 * prob.N * prob.n)
+                                           / (ms_pass * 1e-3) / 1e9,
                      "peak_source": f"{peak_src} hbm_gbs (burst; kernel timed alone)",
                      "resid_pass_gbs": bytes_resid / (ms_resid * 1e-3) / 1e9},
         "clocks": clocks,
         "gpu_launches": kernels,
         "workload_gen_s": round(t_gen, 1),
     }
+
+    fstar = _golden_fstar() if args.seed == 0 else None
+    if fstar is not None and not args.no_tto:
+        # the second time-to-tolerance: until f(z) <= (1 + 1e-4) f*, with f* the exact
+        # optimum (golden file); the objective is checked every iteration (one pass)
+        tt = {}
+        for name, prm_kw in (("admm_cg", {}), ("admm_cached_factor", {"subproblem": rpt.SUB_CHOL})):
+            prm_t = rpt.admm_params(f_target=fstar * (1 + 1e-4), max_iter=20000, **prm_kw)
+            plan.admm_bb_solve(prm_t)                                   # warm-up (graph, factor)
+            te0 = torch.cuda.Event(enable_timing=True)
+            te1 = torch.cuda.Event(enable_timing=True)
+            te0.record(stream)
+            _, ti = plan.admm_bb_solve(prm_t)
+            te1.record(stream)
+            torch.cuda.synchronize(dev)
+            tt[name] = {"seconds": te0.elapsed_time(te1) / 1e3, "iterations": ti["iterations"],
+                        "status": ti["status"], "f": ti["f"]}
+        te0 = torch.cuda.Event(enable_timing=True)
+        te1 = torch.cuda.Event(enable_timing=True)
+        te0.record(stream)
+        _, ti = plan.pgd_solve(f_target=fstar * (1 + 1e-4), tol_rel_df=0.0, max_iter=20000)
+        te1.record(stream)
+        torch.cuda.synchronize(dev)
+        tt["pgd"] = {"seconds": te0.elapsed_time(te1) / 1e3, "iterations": ti["iterations"],
+                     "status": ti["status"], "f": ti["f"]}
+        out["time_to_objective"] = {"target": "f(z) <= (1 + 1e-4) f*", "f_star": fstar, **tt}
+
+    if not args.no_exact:
+        # the bundled pass with exact fixed-point sums (bitwise reproducible solves)
+        with rpt.Plan.from_problem(prob, device=dev, stream=stream.cuda_stream, autotune=1, accumulate=1) as px:
+            px.apply_normal(rng.uniform(0.0, 5.0, size=(prob.N, prob.n)), 0.0)
+            ms_x, by_x = px.profile_row_pass(0, reps=20)
+            px.admm_bb_solve(params)
+            xe0 = torch.cuda.Event(enable_timing=True)
+            xe1 = torch.cuda.Event(enable_timing=True)
+            xe0.record(stream)
+            zx, ix = px.admm_bb_solve(params)
+            xe1.record(stream)
+            torch.cuda.synchronize(dev)
+            zx2, ix2 = px.admm_bb_solve(params)
+            out["exact_sums"] = {"ms_per_pass": ms_x, "gbs": by_x / ms_x / 1e6, "frac_of_peak": by_x / ms_x / 1e6 / peak,
+                                 "solve_s": xe0.elapsed_time(xe1) / 1e3, "iterations": ix["iterations"],
+                                 "f": ix["f"], "repeat_solve_bitwise_equal": bool(np.array_equal(zx, zx2))}
 
     if not args.no_pgd:
         # PGD baseline (Sec. 2.1) to the objective ADMM-BB reached
@@ -596,7 +654,8 @@ def main():
         # reduced-precision storage forms on the same workload: row-pass bandwidth
         # and time to the same tolerance; objective of their optimum on the float32 plan
         forms = {}
-        for name, vf, iw in (("f32+u16", rpt.F32, 16), ("bf16+u16", rpt.BF16, 16), ("fp8+u16", rpt.FP8E4M3, 16)):
+        for name, vf, iw in (("f32+u16", rpt.F32, 16), ("bf16+u16", rpt.BF16, 16), ("fp8+u16", rpt.FP8E4M3, 16),
+                             ("bf16+int32", rpt.BF16, 32)):
             pf = rpt.Plan.from_problem(prob, device=dev, stream=stream.cuda_stream, value_format=vf,
                                        index_width=iw, row_path=args.row_path)
             pf.apply_normal(rng.uniform(0.0, 5.0, size=(prob.N, prob.n)), 0.0)
@@ -699,9 +758,9 @@ def main():
         out["e2e"] = {"value": statistics.mean(e2e), "unit": "s", "h2d_bytes_per_step": int(h2d),
                       "d2h_bytes_per_step": int(prob.n * 8), "runs": len(e2e),
                       "iterations": e2e_it,
-                      "note": "plan_create from host CSR (validate, upload, set up) + solve + x read-back; "
-                              "mean over runs (the iteration count of a solve varies by a few percent "
-                              "with the order of floating-point atomics)"}
+                      "note": "plan_create from host CSR (validate, bundle, upload, autotune the ring) + solve + "
+                              "x read-back; mean over runs (the iteration count of a solve varies by a few "
+                              "percent with the order of floating-point atomics)"}
 
     if rank == 0 and world == 1 and not args.no_cpu:
         out["cpu_baseline"] = cpu_baseline(prob, budget_s=args.cpu_budget)

@@ -90,9 +90,8 @@ typedef struct {
                                        3 streaming (warps claim chunks, entries go straight to registers);
                                        4 bundled ring: rows grouped 4 at a time in the given row order, one
                                          spot index per column of a group (rows that are neighbours in the
-                                         input order should share spots, as voxels in grid order do), and
-                                         exact 64-bit fixed-point sums, so every result is bitwise
-                                         reproducible;
+                                         input order should share spots, as voxels in grid order do); see
+                                         accumulate for its exact (bitwise reproducible) sums;
                                        0: 4 when its shared-memory stage fits the plan, else 2, else 1 */
   int32_t autotune;                 /* 1: time every ring configuration that fits this plan (entries and
                                        rows per stage, stages) on its own row pass and keep the fastest;
@@ -109,6 +108,12 @@ typedef struct {
                                        the call returns RPT_TIMEOUT (no GPU fault is involved); 0 normally */
   int64_t device_mem_cap;           /* testing hook: bytes the plan may allocate on the device (a request past
                                        it fails as an out-of-memory would, RPT_ENOMEM); 0 = no cap */
+  int32_t accumulate;               /* row path 4's scatter: 0 = library choice (2); 1 = exact 64-bit fixed-point
+                                       sums: every pass, and so every solve, is bitwise reproducible whatever
+                                       the scheduling, and tight tolerances (1e-7) converge where float
+                                       rounding noise can stall them; about 25 % slower per pass;
+                                       2 = float32 shared-memory atomics, whose results vary in the last bits
+                                       from run to run */
 } rpt_device_opts;
 
 /* ADMM-BB parameters (Sec. 2.2).  Fill with rpt_admm_params_default(). */
@@ -199,6 +204,9 @@ typedef struct {
   int64_t block_cols;     /* path 4: stored block columns (4 values and one index each) */
   double  bundle_fill;    /* path 4: stored entries / (4 block_cols): the share of stored values that
                              are entries of the matrix */
+  int32_t exact_sums;     /* 1: the row passes sum in exact fixed point (path 4 with accumulate 0/1), so
+                             their results do not depend on scheduling; 0: float atomics */
+  int32_t reserved;
 } rpt_plan_stats;
 
 /* ---- defaults ----------------------------------------------------------- */
@@ -288,6 +296,40 @@ int rpt_admm_bb_solve_batched(rpt_plan* plan, const rpt_admm_params* params, dou
 int rpt_admm_bb_solve(rpt_plan* plan, const rpt_admm_params* params,
                       const double* z0, const double* y0,
                       double* x_out, rpt_solve_info* info);
+
+/* ---- linear dose constraints (Sec. 4) --------------------------------------
+ * Sec. 4 notes that ADMM, unlike PGD, accepts linear constraints on the plan
+ * such as maximum or mean dose limits.  Each limit below applies to the
+ * physical dose A_s x (unweighted) in every scenario s: */
+#define RPT_DOSE_MAX   0   /* a_{s,i}^T x <= limit for every voxel i of the set (one row per voxel) */
+#define RPT_DOSE_MIN   1   /* a_{s,i}^T x >= limit for every voxel i of the set (one row per voxel) */
+#define RPT_DOSE_MEAN  2   /* (1/|S|) sum_{i in S} a_{s,i}^T x <= limit (one row) */
+
+typedef struct {
+  int32_t kind;             /* RPT_DOSE_MAX | RPT_DOSE_MIN | RPT_DOSE_MEAN */
+  int32_t n_voxels;         /* >= 1 */
+  const int32_t* voxels;    /* [n_voxels] host, voxel (row) indices in [0, m) */
+  double  limit;            /* dose limit D (finite) */
+} rpt_dose_constraint;
+
+/* ADMM-BB with linear dose constraints as extra ADMM blocks: besides the
+ * consensus x_s = z, v_s = G_s x_s with v_s <= h_s, a second dual mu_s and a
+ * fixed penalty sigma (G_s, h_s: the constraint rows of scenario s, in the order
+ * of `cons`, voxels in the given order, a mean constraint one row).  Each
+ * iteration: x_s from the cached factor of B_s + (sigma/2) G_s^T G_s (App. A;
+ * formed and inverted for this call), the z-update, v_s = min(G_s x_s +
+ * mu_s/sigma, h_s), the dual step of Eq. 8 on the consensus blocks, mu_s +=
+ * sigma (G_s x_s - v_s), and Eq. 9 extended to both blocks.  sigma: > 0, or 0
+ * for rho.  params as for rpt_admm_bb_solve (subproblem, use_graph, resume and
+ * bb_per_scenario are ignored; tol_obj and f_target are not supported:
+ * RPT_EUNSUPPORTED).  x_out: [n] the final z; mu_out: [N*K] or NULL, the dose
+ * duals (the multipliers of the limits at the optimum), K rows per scenario in
+ * constraint order.  A voxel whose row is empty in a scenario contributes a
+ * zero row there.  Returns as rpt_admm_bb_solve; RPT_EINVAL for invalid
+ * constraints. */
+int rpt_admm_bb_solve_constrained(rpt_plan* plan, const rpt_admm_params* params, int32_t n_cons,
+                                  const rpt_dose_constraint* cons, double sigma, double* x_out, double* mu_out,
+                                  rpt_solve_info* info);
 
 /* Projected gradient descent with Armijo backtracking (Sec. 2.1, Eq. 3 read
  * as f(x+) <= f(x) + beta grad'(x+ - x)).  x0: [n] or NULL for 0; x_out [n]. */

@@ -368,11 +368,12 @@ int create_plan(const rpt_problem* pr, const rpt_device_opts* opts, rpt_plan** o
   // row path: the caller's choice, else the bundled ring when its stage fits the
   // plan, else the bulk-copy ring when it fits, else the register path
   const int want_path = opts ? opts->row_path : 0;
-  if (want_path < 0 || want_path > 4) {
+  if (want_path < 0 || want_path > 4 || (opts && (opts->accumulate < 0 || opts->accumulate > 2))) {
     free_plan(P);
-    set_error("row_path must be 0..4");
+    set_error("row_path must be 0..4 and accumulate 0..2");
     return RPT_EINVAL;
   }
+  const bool exact = opts && opts->accumulate == 1;      // bundled path: fixed-point sums on request
   int smem_optin = 0;
   cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, P->device);
   const bool autotune = opts && opts->autotune;
@@ -392,6 +393,9 @@ int create_plan(const rpt_problem* pr, const rpt_device_opts* opts, rpt_plan** o
       }
     }
   }
+  P->nz_index.assign((size_t)N * m_act, -1);
+  for (int s = 0; s < N; ++s)
+    for (size_t q = 0; q < order[s].size(); ++q) P->nz_index[(size_t)s * m_act + order[s][q]] = (int32_t)q;
   P->scen_c = cs;
   P->dropped_rows = dropped;
   P->colsq_max.assign(N, 0.0);
@@ -423,7 +427,8 @@ int create_plan(const rpt_problem* pr, const rpt_device_opts* opts, rpt_plan** o
                make_int3(1536, 96, 3), make_int3(1024, 64, 3), make_int3(1024, 64, 2), make_int3(512, 32, 2)};
     std::vector<int3> fit;
     for (const int3& c : cands)
-      if (tma_smem_bytes(n_pad, c.x, c.y, c.z, bv, bi, true, true) + 1024 <= (size_t)smem_optin) fit.push_back(c);
+      if (tma_smem_bytes(n_pad, c.x, c.y, c.z, bv, bi, true, true, exact) + 1024 <= (size_t)smem_optin)
+        fit.push_back(c);
     if (!fit.empty()) {
       std::vector<BundleScen> B(N);
       {
@@ -796,6 +801,7 @@ int create_plan(const rpt_problem* pr, const rpt_device_opts* opts, rpt_plan** o
   RPT_CP(d_rec, rec_h.data(), rec_h.size() * sizeof(int4));
   RPT_CP(d_recbase, recbase_h.data(), (N + 1) * sizeof(int));
   RPT_CP(P->rec_of, rec_of_h.data(), rec_of_h.size() * sizeof(int));
+  P->rec_of_host = rec_of_h;
   if (!dyn) RPT_CP(d_blocks, blocks.data(), blocks.size() * sizeof(int4));
   RPT_CP(P->diag, diag_h.data(), diag_h.size() * sizeof(float));
   if (dyn) {
@@ -839,7 +845,7 @@ int create_plan(const rpt_problem* pr, const rpt_device_opts* opts, rpt_plan** o
   dp.err = P->err;
   dp.col32 = d_col32;
   dp.val32 = d_val32;
-  dp.acc64 = bundled ? 1 : 0;
+  dp.acc64 = (bundled && exact) ? 1 : 0;
   dp.fexp = d_fexp;
   dp.kbound = d_kbound;
   // ---- quantised values / narrow indices ----
@@ -910,7 +916,7 @@ int create_plan(const rpt_problem* pr, const rpt_device_opts* opts, rpt_plan** o
   };
   if (pr->value_format != RPT_F32) release(d_val32);
   if (pr->index_width == 16) release(d_col32);
-  if (bundled) {
+  if (dp.acc64) {
     // bounds of the fixed-point accumulation, from the stored values
     double* kc = nullptr;
     if ((e = cudaMalloc(&kc, sizeof(double) * 2 * n_pad))) {
@@ -945,6 +951,7 @@ int create_plan(const rpt_problem* pr, const rpt_device_opts* opts, rpt_plan** o
   S.bundles = bundled ? n_bundles : 0;
   S.block_cols = bundled ? NE : 0;
   S.bundle_fill = (bundled && NE > 0) ? (double)NNZ / (double)(kBunRows * NE) : 0.0;
+  S.exact_sums = dp.acc64;
   S.value_format = pr->value_format;
   S.index_width = pr->index_width;
   S.row_blocks = dp.nblocks;
@@ -1215,12 +1222,11 @@ int rpt_plan_set_weights(rpt_plan* plan, const double* voxel_w, const double* pr
       if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), acc, sizeof(unsigned long long) * n_pad,
                                                 cudaMemcpyDeviceToHost, st);
       if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-      long long t = 0;
-      for (int j = 0; j < n; ++j) {
-        diag[(size_t)s * n + j] = (float)((double)(long long)h[j] / scale);
-        t += (long long)h[j];
+      for (int j = 0; j < n; ++j) {   // each sum is exact; the trace adds them in column order
+        const double dj = (double)(long long)h[j] / scale;
+        diag[(size_t)s * n + j] = (float)dj;
+        tr += dj;
       }
-      tr += (double)t / scale;
     }
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(P->diag, diag.data(), sizeof(float) * diag.size(), cudaMemcpyHostToDevice, st);
@@ -1241,6 +1247,7 @@ int rpt_plan_set_weights(rpt_plan* plan, const double* voxel_w, const double* pr
     P->stats.default_rho = 2.0 * (tr / N) / n;
     P->lipschitz = 0.0;
     P->chol_ready = false;
+    P->chol_con = false;
     return RPT_OK;
   });
 }

@@ -284,8 +284,8 @@ __global__ void __launch_bounds__(64) k_trsm_left(const float* L, float* Y, int 
 
 // Form, factor and invert B_s for every scenario into P->binv (allocating it on
 // first use); also A~_s^T p~ into P->bchol (compute_bconst, solver.cu).
-int chol_prepare(Plan* P, double rho) {
-  if (P->chol_ready && P->chol_rho == rho) return RPT_OK;
+int chol_prepare(Plan* P, double rho, CholExtra* extra) {
+  if (!extra && P->chol_ready && !P->chol_con && P->chol_rho == rho) return RPT_OK;
   const DevPlan& dp = P->dp;
   const int n = dp.n, N = dp.N;
   const size_t nn = (size_t)n * n;
@@ -339,6 +339,7 @@ int chol_prepare(Plan* P, double rho) {
   }
   const dim3 gd((n + 255) / 256, N);
   k_add_diag<<<gd, 256, 0, st>>>(P->binv, n, (float)(0.5 * rho));
+  if (extra && (e = extra->add(P, P->binv))) return done(cuda_fail(e, "constraint terms of B_s"));
   // 2. Cholesky, lower, in place
   const int nblk = (n + kNB - 1) / kNB;
   for (int kb = 0; kb < nblk; ++kb) {
@@ -379,6 +380,7 @@ int chol_prepare(Plan* P, double rho) {
     return done(RPT_EINVAL);
   }
   P->chol_ready = true;
+  P->chol_con = extra != nullptr;
   P->chol_rho = rho;
   return done(RPT_OK);
 }

@@ -82,7 +82,8 @@ struct DevPlan {
   // pass on scenario s scales every contribution by 2^fexp[s], chosen from the
   // bound |acc_c| <= kbound[2s] max|v_s| (+ kbound[2s+1] with the prescription
   // term) so that no sum can overflow; the reducers scale back by 2^-fexp[s].
-  int acc64;                          // 1: partial slots are int64 fixed point (path 3)
+  int acc64;                          // 1: partial slots are int64 fixed point (path 3 with exact sums;
+                                      //    0 on path 3: float32 shared atomics, like paths 0-2)
   int* fexp;                          // [N] scale exponent of the last scatter pass per scenario
   const double* kbound;               // [2N] max_c sum_i c_s w_i |a_ic| ||a_i||_1 and max_c sum_i c_s w_i |a_ic| p_i
 };
@@ -156,7 +157,7 @@ size_t rowpass_smem(const DevPlan& P, int mode);
 int rowpass_threads(const DevPlan& P);
 cudaError_t rowpass_prepare(const DevPlan& P);
 size_t tma_smem_bytes(int n_pad, int cmax, int rmax, int stages, int value_bytes, int index_bytes,
-                      bool scatter, bool bundled = false);
+                      bool scatter, bool bundled = false, bool fixed = false);
 size_t stream_smem_bytes(int n_pad, int rmax, bool scatter);
 void* stream_rowpass_kernel(const DevPlan& P, int mode);   // rowstream.cu
 // Bundled layout, at plan creation: kbound[2s], kbound[2s+1] of every scenario

@@ -37,6 +37,13 @@ struct Ctl {
   // step of the scenario's last dual update until the next BB computation replaces it
   double* step_s;
   int bb_scen, pad4;
+  // dose-constraint blocks (rpt_admm_bb_solve_constrained): the residual pieces of
+  // the iteration, written by the constraint kernels before k_admm_d / k_admm_y
+  const double* con_q;    // [N][n] sigma G_s^T (v_s - v_s_prev)
+  const double* con_t;    // [N][n] G_s^T mu_s
+  const double* con_sums; // [4] ||G x - v||^2, ||G x||^2, ||v||^2 over all scenarios
+  double con_K;           // constraint rows over all scenarios
+  int con_on, pad5;
 };
 
 // trace entry: iteration, seconds since the solve started, r_prim, r_dual,
@@ -87,6 +94,7 @@ struct Plan {
   double *trace = nullptr;         // [kTraceCap][kTraceFields] (allocated on first traced solve)
   int trace_count = 0;             // entries of the last traced solve
   bool chol_ready = false;
+  bool chol_con = false;          // the cached factor includes dose-constraint terms
   double chol_rho = 0.0;
   cudaGraphExec_t admm_chol_exec = nullptr;
   int admm_chol_exec_obj = -1;
@@ -99,6 +107,15 @@ struct Plan {
   std::vector<int32_t> dropped_rows;
   std::vector<std::vector<int32_t>> empty_kept;
   std::vector<double> colsq_max;
+  // where each kept row of each scenario sits in the stored layout (dose
+  // constraints read constrained rows from it): rec_of_host = the device rec_of
+  // ([N][m_act]: CSR paths: position of kept row k in scenario s's row list;
+  // bundled path: sorted position of the q-th bundle in creation order), and
+  // nz_index[s][k] = position of kept row k among scenario s's non-empty rows in
+  // kept order (-1: the row is empty in s), which gives a row's bundle (index / 4)
+  // and slot (index % 4)
+  std::vector<int32_t> rec_of_host;
+  std::vector<int32_t> nz_index;
   std::vector<int32_t> batch_col_off;  // batched plan: problem k owns spots [off[k], off[k+1]); else empty
   double lipschitz = 0.0;         // cached 2 lambda_max, 0 = not computed
   bool state_valid = false;
@@ -110,8 +127,30 @@ struct Plan {
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
 };
 
+// chol.cu: form, factor and invert B_s for this rho; `extra` (may be null) adds
+// further terms to the lower triangle of every B_s before the factorisation
+// (B_s row-major [N][n][n] float, launched on the plan's stream) and marks the
+// factor as not reusable by plain solves
+struct CholExtra {
+  virtual cudaError_t add(Plan* P, float* B) = 0;
+  virtual ~CholExtra() = default;
+};
+// Dose-constraint blocks of a cached-factor ADMM-BB solve (dosecon.cu): the
+// solver calls init after its own initialisation, rhs in place of the plain
+// right-hand side c_s (into v32, float), and after_z between the z-update and
+// the BB / dual kernels; q, t, sums and K feed the extended residuals of Eq. 9.
+struct ConHook : CholExtra {
+  const double* q = nullptr;      // [N][n]
+  const double* t = nullptr;      // [N][n]
+  const double* sums = nullptr;   // [4]
+  double K = 0.0;
+  virtual cudaError_t init(Plan* P) = 0;
+  virtual cudaError_t rhs(Plan* P) = 0;
+  virtual cudaError_t after_z(Plan* P) = 0;
+};
+
 int admm_solve(Plan* P, const rpt_admm_params* prm, const double* z0, const double* y0,
-               double* x_out, rpt_solve_info* info);
+               double* x_out, rpt_solve_info* info, ConHook* con = nullptr);
 int pgd_solve(Plan* P, const rpt_pgd_params* prm, const double* x0, double* x_out,
               rpt_solve_info* info);
 int op_apply_normal(Plan* P, const double* v, double rho, double* u_out);
@@ -120,7 +159,10 @@ int op_objective(Plan* P, const double* x, double* f_out, double* dose_out);
 int compute_lipschitz(Plan* P, double* L);
 int profile_row_pass(Plan* P, int mode, int reps, double* ms, double* bytes);
 void destroy_graphs(Plan* P);
-int chol_prepare(Plan* P, double rho);   // chol.cu
+// chol.cu (see CholExtra)
+int chol_prepare(Plan* P, double rho, CholExtra* extra = nullptr);
+
+
 int compute_bconst(Plan* P);             // solver.cu: P->bchol = A~_s^T p~
 
 // error reporting (api.cu)

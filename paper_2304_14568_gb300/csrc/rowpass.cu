@@ -175,12 +175,13 @@ __device__ __forceinline__ long long fixed_round(float y) {
 // accumulator (scale fscale = 2^F): integer sums are exact, so the result does
 // not depend on the order of the atomics.  Block columns whose four values are
 // zero (none are stored) or whose scaled contribution rounds to 0 add nothing.
-template <int MODE, typename VT, typename IT, int KR>
+template <int MODE, typename VT, typename IT, int KR, bool FIX>
 __device__ __forceinline__ void process_bundle(const int4* __restrict__ rec, int b, bool valid, int G, int sl,
                                                const VT* __restrict__ val, const IT* __restrict__ col,
-                                               long long off, const float* sv, unsigned long long* acc,
+                                               long long off, const float* sv, float* accf,
                                                float fscale, double& obj, float* __restrict__ dose,
                                                size_t dose_base) {
+  unsigned long long* acc = reinterpret_cast<unsigned long long*>(accf);
   constexpr bool kScatter = (MODE == kNormal || MODE == kResid);
   constexpr unsigned kFull = 0xffffffffu;
   int lo = 0, hi = 0;
@@ -249,15 +250,23 @@ __device__ __forceinline__ void process_bundle(const int4* __restrict__ rec, int
 #pragma unroll
     for (int k = 0; k < KR; ++k) {
       const float sc = coef[0] * a[k][0] + coef[1] * a[k][1] + coef[2] * a[k][2] + coef[3] * a[k][3];
-      const long long qv = fixed_round(sc * fscale);
-      if (qv != 0) atomicAdd(&acc[c[k]], (unsigned long long)qv);
+      if (FIX) {
+        const long long qv = fixed_round(sc * fscale);
+        if (qv != 0) atomicAdd(&acc[c[k]], (unsigned long long)qv);
+      } else if (sc != 0.f) {
+        atomicAdd(&accf[c[k]], sc);
+      }
     }
     for (int idx = lo + G * KR + sl; idx < hi; idx += G) {
       float q[4];
       quad_v<false, VT>(val + 4 * (size_t)idx, q);
       const float sc = coef[0] * q[0] + coef[1] * q[1] + coef[2] * q[2] + coef[3] * q[3];
-      const long long qv = fixed_round(sc * fscale);
-      if (qv != 0) atomicAdd(&acc[(int)col[idx]], (unsigned long long)qv);
+      if (FIX) {
+        const long long qv = fixed_round(sc * fscale);
+        if (qv != 0) atomicAdd(&acc[(int)col[idx]], (unsigned long long)qv);
+      } else if (sc != 0.f) {
+        atomicAdd(&accf[(int)col[idx]], sc);
+      }
     }
   }
 }
@@ -284,7 +293,7 @@ constexpr int kBatch = 4;   // chunks per queue pull
 // row bundles (path 3), records of 4 int4 per bundle, 4 values per block column,
 // 64-bit fixed-point accumulator (see process_bundle); the staged vector's
 // maximum magnitude sets the scale of each scenario.
-template <int MODE, typename VT, typename IT, bool BUN>
+template <int MODE, typename VT, typename IT, bool BUN, bool FIX>
 __global__ void __launch_bounds__(kTmaThreads, 1)
 k_rowpass_tma(DevPlan P, const float* __restrict__ vin, int v_stride, const int* __restrict__ active,
               float* __restrict__ partial, double* __restrict__ objp, float* __restrict__ dose) {
@@ -293,7 +302,8 @@ k_rowpass_tma(DevPlan P, const float* __restrict__ vin, int v_stride, const int*
   constexpr int KR = BUN ? kBundleKeep : 8;     // entries (block columns) per lane kept in registers
   constexpr int RPU = BUN ? 4 : 1;              // int4 records per row (bundle)
   constexpr int VPE = BUN ? 4 : 1;              // values per stored entry (block column)
-  constexpr int ACCB = BUN ? 8 : 4;             // accumulator bytes per column
+  constexpr bool FX = BUN && FIX;                // 64-bit fixed-point accumulator
+  constexpr int ACCB = FX ? 8 : 4;              // accumulator bytes per column
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t* full = reinterpret_cast<uint64_t*>(smem);
   uint64_t* empty = full + 8;
@@ -419,7 +429,7 @@ k_rowpass_tma(DevPlan P, const float* __restrict__ vin, int v_stride, const int*
       obj = 0.0;
       named_sync(1, NCW * 32);
       const int slot = blockIdx.x * P.N + s;
-      if (BUN) {
+      if (FX) {
         if (kScatter) {
           unsigned long long* out = reinterpret_cast<unsigned long long*>(partial) + (size_t)slot * P.n_pad;
           for (int k = ct; k < P.n_pad; k += NCW * 32) out[k] = acc64[k];
@@ -433,7 +443,7 @@ k_rowpass_tma(DevPlan P, const float* __restrict__ vin, int v_stride, const int*
           for (int k = 0; k < NCW; ++k) tsum += wobj[k];
           objp[slot] = tsum;
         }
-        if (BUN && kScatter) P.fexp[s] = fexp;
+        if (FX && kScatter) P.fexp[s] = fexp;
         P.visited[(size_t)s * P.grid + blockIdx.x] = 1;
       }
     };
@@ -451,7 +461,7 @@ k_rowpass_tma(DevPlan P, const float* __restrict__ vin, int v_stride, const int*
         }
         s = ch.s;
         base = P.nnz_base[s];
-        if (BUN) {
+        if (FX) {
           float vm = stage_vector_max<kScatter>(P, vin, v_stride, s, sv, acc64, ct, NCW * 32);
           vm = warp_max(vm);
           if (lane == 0) wmax[cw] = vm;
@@ -482,8 +492,8 @@ k_rowpass_tma(DevPlan P, const float* __restrict__ vin, int v_stride, const int*
       for (int u = u0; u < units; u += NCW) {
         const int r = u * rpw + sub;
         if (BUN)
-          process_bundle<MODE, VT, IT, KR>(rec, r, r < ch.n_rows, G, sl, val, col, off, sv, acc64, fscale, obj,
-                                           dose, dose_base);
+          process_bundle<MODE, VT, IT, KR, FIX>(rec, r, r < ch.n_rows, G, sl, val, col, off, sv, acc, fscale,
+                                                obj, dose, dose_base);
         else
           process_rows<MODE, VT, IT, KR>(rec, r, r < ch.n_rows, G, sl, val, col, off, sv, acc, obj, dose,
                                          dose_base);
@@ -556,27 +566,27 @@ k_rowpass(DevPlan P, const float* __restrict__ vin, int v_stride, const int* __r
 
 constexpr int kKR = 8;
 
-template <int MODE, bool BUN>
+template <int MODE, bool BUN, bool FIX>
 void* pick_ring(const DevPlan& P) {
   if (P.index_width == 16) {
     switch (P.value_format) {
-      case 1: return (void*)k_rowpass_tma<MODE, __nv_bfloat16, uint16_t, BUN>;
-      case 2: return (void*)k_rowpass_tma<MODE, __nv_fp8_e4m3, uint16_t, BUN>;
-      default: return (void*)k_rowpass_tma<MODE, float, uint16_t, BUN>;
+      case 1: return (void*)k_rowpass_tma<MODE, __nv_bfloat16, uint16_t, BUN, FIX>;
+      case 2: return (void*)k_rowpass_tma<MODE, __nv_fp8_e4m3, uint16_t, BUN, FIX>;
+      default: return (void*)k_rowpass_tma<MODE, float, uint16_t, BUN, FIX>;
     }
   }
   switch (P.value_format) {
-    case 1: return (void*)k_rowpass_tma<MODE, __nv_bfloat16, int32_t, BUN>;
-    case 2: return (void*)k_rowpass_tma<MODE, __nv_fp8_e4m3, int32_t, BUN>;
-    default: return (void*)k_rowpass_tma<MODE, float, int32_t, BUN>;
+    case 1: return (void*)k_rowpass_tma<MODE, __nv_bfloat16, int32_t, BUN, FIX>;
+    case 2: return (void*)k_rowpass_tma<MODE, __nv_fp8_e4m3, int32_t, BUN, FIX>;
+    default: return (void*)k_rowpass_tma<MODE, float, int32_t, BUN, FIX>;
   }
 }
 
 template <int MODE>
 void* pick(const DevPlan& P) {
-  if (P.path == 3) return pick_ring<MODE, true>(P);
+  if (P.path == 3) return P.acc64 ? pick_ring<MODE, true, true>(P) : pick_ring<MODE, true, false>(P);
   if (P.path == 2) return stream_rowpass_kernel(P, MODE);
-  if (P.path == 1) return pick_ring<MODE, false>(P);
+  if (P.path == 1) return pick_ring<MODE, false, false>(P);
   if (P.index_width == 16) {
     switch (P.value_format) {
       case 1: return (void*)k_rowpass<MODE, __nv_bfloat16, uint16_t, kKR>;
@@ -795,8 +805,8 @@ cudaError_t bundle_bounds(const DevPlan& P, double* kc, double* pc, double* kbou
 }
 
 size_t tma_smem_bytes(int n_pad, int cmax, int rmax, int stages, int value_bytes, int index_bytes,
-                      bool scatter, bool bundled) {
-  const int rpu = bundled ? 4 : 1, vpe = bundled ? 4 : 1, accb = bundled ? 8 : 4;
+                      bool scatter, bool bundled, bool fixed) {
+  const int rpu = bundled ? 4 : 1, vpe = bundled ? 4 : 1, accb = (bundled && fixed) ? 8 : 4;
   const size_t stage = round128((size_t)(rmax * rpu + 1) * 16) + round128((size_t)cmax * vpe * value_bytes) +
                        round128((size_t)cmax * index_bytes);
   return round128(kHdr + (size_t)n_pad * (4 + (scatter ? accb : 0))) + (size_t)stages * stage;
@@ -816,7 +826,7 @@ size_t rowpass_smem(const DevPlan& P, int mode) {
   if (P.path == 1 || P.path == 3) {
     const int vb = P.value_format == 0 ? 4 : (P.value_format == 1 ? 2 : 1);
     const int ib = P.index_width == 16 ? 2 : 4;
-    return tma_smem_bytes(P.n_pad, P.cmax, P.rmax, P.stages, vb, ib, scatter, P.path == 3);
+    return tma_smem_bytes(P.n_pad, P.cmax, P.rmax, P.stages, vb, ib, scatter, P.path == 3, P.acc64 != 0);
   }
   if (P.path == 2) return stream_smem_bytes(P.n_pad, P.rmax, scatter);
   return (size_t)P.n_pad * sizeof(float) * (scatter ? 2 : 1);

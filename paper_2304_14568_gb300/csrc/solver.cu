@@ -386,12 +386,13 @@ __global__ void k_admm_z(DevPlan P, Ctl* C, const double* __restrict__ x, const 
 
 // grid (nchunk, N).  d = x - z_new; BB sums dd'd_prev and ||dd||^2; ||d||^2, ||x||^2.
 // Last block: BB step (Eq. 8), r_prim, r_dual, eps_prim (Eq. 9).
-__global__ void k_admm_d(DevPlan P, Ctl* C, const double* __restrict__ x,
+__global__ void k_admm_d(DevPlan P, Ctl* C, const double* __restrict__ x, const double* __restrict__ z,
                          const double* __restrict__ znew, const double* __restrict__ dprev, double* d,
                          double* vpart, int nchunk) {
-  __shared__ double sh[4 * 32];
+  __shared__ double sh[5 * 32];
   const int s = blockIdx.y, j = blockIdx.x * VT + threadIdx.x;
-  double v[4] = {0.0, 0.0, 0.0, 0.0};
+  const int con = C->con_on;
+  double v[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
   if (j < P.n) {
     const size_t o = (size_t)s * P.n + j;
     const double xj = x[o];
@@ -403,15 +404,21 @@ __global__ void k_admm_d(DevPlan P, Ctl* C, const double* __restrict__ x,
     v[1] = dd * dd;
     v[2] = dj * dj;
     v[3] = xj * xj;
+    if (con) {   // dual residual with the dose blocks: rho (z - z_prev) + sigma G_s'(v_s - v_s_prev)
+      const double rd = C->rho * (znew[j] - z[j]) + C->con_q[o];
+      v[4] = rd * rd;
+    }
   }
-  block_sum_d<4>(v, sh);
+  block_sum_d<5>(v, sh);
   const int blk = s * nchunk + blockIdx.x;
   if (threadIdx.x == 0) {
     for (int k = 0; k < 4; ++k) vpart[(size_t)(nchunk + blk) * 8 + k] = v[k];
+    vpart[(size_t)(nchunk + blk) * 8 + 5] = v[4];
   }
   if (!last_block(&C->cnt_d, gridDim.x * gridDim.y)) return;
-  double S[4];
+  double S[4], SC[1];
   last_block_sums<4>(vpart + (size_t)nchunk * 8, gridDim.x * gridDim.y, 8, 0, S, sh);
+  last_block_sums<1>(vpart + (size_t)nchunk * 8, gridDim.x * gridDim.y, 8, 5, SC, sh);
   const double rho = C->rho;
   const bool use_bb = C->bb_mode != 2 && C->have_prev;
   if (C->bb_scen) {
@@ -451,10 +458,20 @@ __global__ void k_admm_d(DevPlan P, Ctl* C, const double* __restrict__ x,
     }
     const double sN = sqrt((double)P.N);
     C->step = step;
-    C->r_prim = sqrt(S[2]);
-    C->r_dual = sN * rho * sqrt(C->dz2);
-    C->eps_prim = C->eps_abs * sqrt((double)P.N * P.n) +
-                  C->eps_rel * fmax(sqrt(S[3]), sN * sqrt(C->sz2));
+    if (con) {
+      // Eq. 9 extended to both blocks: r_prim over [x_s - z; G_s x_s - v_s],
+      // eps_prim over [x_s; G_s x_s] and [z (N times); v_s]
+      const double* cs = C->con_sums;
+      C->r_prim = sqrt(S[2] + cs[0]);
+      C->r_dual = sqrt(SC[0]);
+      C->eps_prim = C->eps_abs * sqrt((double)P.N * P.n + C->con_K) +
+                    C->eps_rel * fmax(sqrt(S[3] + cs[1]), sqrt((double)P.N * C->sz2 + cs[2]));
+    } else {
+      C->r_prim = sqrt(S[2]);
+      C->r_dual = sN * rho * sqrt(C->dz2);
+      C->eps_prim = C->eps_abs * sqrt((double)P.N * P.n) +
+                    C->eps_rel * fmax(sqrt(S[3]), sN * sqrt(C->sz2));
+    }
   }
 }
 
@@ -475,7 +492,8 @@ __global__ void k_admm_y(DevPlan P, Ctl* C, const double* __restrict__ x, double
     y[o] = yn;
     dprev[o] = dj;
     v32[(size_t)s * P.n_pad + j] = (float)x[o];
-    v[0] = yn * yn;
+    const double ye = C->con_on ? yn + C->con_t[o] : yn;   // with dose blocks: y_s + G_s' mu_s
+    v[0] = ye * ye;
     if (s == 0) {
       const double zn = znew[j];
       z[j] = zn;
@@ -847,13 +865,14 @@ void cg_body(Exec& e, Plan* P, unsigned long long hcg, int uc) {
          P->act_next, P->cgi, P->cgcnt, P->cnt_s, hcg, uc);
 }
 
-void admm_iteration_tail(Exec& e, Plan* P, int use_obj, unsigned long long hadmm, int uc) {
+void admm_iteration_tail(Exec& e, Plan* P, int use_obj, unsigned long long hadmm, int uc, ConHook* con = nullptr) {
   const DevPlan& dp = P->dp;
   dim3 g1(P->nchunk), g2(P->nchunk, dp.N);
   launch(e, k_admm_z, g1, dim3(VT), 0, dp, P->ctl, (const double*)P->x, (const double*)P->y,
          (const double*)P->z, P->znew, (const double*)P->lb, (const double*)P->ub, P->vpart);
-  launch(e, k_admm_d, g2, dim3(VT), 0, dp, P->ctl, (const double*)P->x, (const double*)P->znew,
-         (const double*)P->dprev, P->d, P->vpart, P->nchunk);
+  if (con && e.err == cudaSuccess) e.err = con->after_z(P);
+  launch(e, k_admm_d, g2, dim3(VT), 0, dp, P->ctl, (const double*)P->x, (const double*)P->z,
+         (const double*)P->znew, (const double*)P->dprev, P->d, P->vpart, P->nchunk);
   launch(e, k_admm_y, g2, dim3(VT), 0, dp, P->ctl, (const double*)P->x, P->y, P->z,
          (const double*)P->znew, (const double*)P->d, P->dprev, P->v32, P->vz32, P->vpart, P->nchunk,
          hadmm, use_obj ? 0 : uc);
@@ -1026,16 +1045,19 @@ struct NvtxRange {            // NVTX range for tools (no cost without one attac
 }  // namespace
 
 int admm_solve_impl(Plan* P, const rpt_admm_params* prm, const double* z0, const double* y0, double* x_out,
-                    rpt_solve_info* info);
+                    rpt_solve_info* info, ConHook* con);
 
 int admm_solve(Plan* P, const rpt_admm_params* prm, const double* z0, const double* y0,
-               double* x_out, rpt_solve_info* info) {
-  NvtxRange r(prm && prm->subproblem == RPT_SUB_CHOL ? "rpt: ADMM-BB (cached factor)" : "rpt: ADMM-BB (CG)");
-  return admm_solve_impl(P, prm, z0, y0, x_out, info);
+               double* x_out, rpt_solve_info* info, ConHook* con) {
+  NvtxRange r(con ? "rpt: ADMM-BB with dose constraints (cached factor)"
+                  : (prm && prm->subproblem == RPT_SUB_CHOL ? "rpt: ADMM-BB (cached factor)" : "rpt: ADMM-BB (CG)"));
+  return admm_solve_impl(P, prm, z0, y0, x_out, info, con);
 }
 
+// con: dose-constraint blocks; the solve then uses the cached factor (with the
+// constraint terms in B_s) and the host-driven loop.
 int admm_solve_impl(Plan* P, const rpt_admm_params* prm, const double* z0, const double* y0,
-                    double* x_out, rpt_solve_info* info) {
+                    double* x_out, rpt_solve_info* info, ConHook* con) {
   const DevPlan& dp = P->dp;
   const int n = dp.n, N = dp.N;
   double rho = prm->rho > 0 ? prm->rho : prm->rho_scale * P->stats.default_rho;
@@ -1068,7 +1090,7 @@ int admm_solve_impl(Plan* P, const rpt_admm_params* prm, const double* z0, const
         }
   }
   const int use_obj = (std::isfinite(prm->tol_obj) || prm->f_target > 0.0) ? 1 : 0;
-  const bool chol = prm->subproblem == RPT_SUB_CHOL;
+  const bool chol = prm->subproblem == RPT_SUB_CHOL || con != nullptr;
   cudaStream_t st = P->stream;
   cudaError_t e;
   double setup_s = 0.0;
@@ -1076,9 +1098,9 @@ int admm_solve_impl(Plan* P, const rpt_admm_params* prm, const double* z0, const
     if ((e = cudaFuncSetAttribute(k_chol_x, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)(sizeof(float) * (size_t)dp.n_pad))))
       return cuda_fail(e, "kernel attribute");
-    const bool cached = P->chol_ready && P->chol_rho == rho;
+    const bool cached = !con && P->chol_ready && !P->chol_con && P->chol_rho == rho;
     const auto t0 = std::chrono::steady_clock::now();
-    if (int rc = chol_prepare(P, rho)) return rc;
+    if (int rc = chol_prepare(P, rho, con)) return rc;
     if (!cached) setup_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   }
   // inputs: z0 -> znew (scratch until the first z-update), y0 -> u (scratch until CG)
@@ -1120,6 +1142,13 @@ int admm_solve_impl(Plan* P, const rpt_admm_params* prm, const double* z0, const
   c.step_prev = rho;
   c.step = rho;
   c.f_prev = HUGE_VAL;
+  if (con) {
+    c.con_q = con->q;
+    c.con_t = con->t;
+    c.con_sums = con->sums;
+    c.con_K = con->K;
+    c.con_on = 1;
+  }
   if ((e = cudaMemcpyAsync(P->ctl, &c, sizeof(Ctl), cudaMemcpyHostToDevice, st)))
     return cuda_fail(e, "upload control block");
   if ((e = cudaMemsetAsync(P->cgcnt, 0, sizeof(int) * N, st))) return cuda_fail(e, "memset");
@@ -1133,7 +1162,8 @@ int admm_solve_impl(Plan* P, const rpt_admm_params* prm, const double* z0, const
            P->z, P->dprev, P->v32);
     if (ex.err) return cuda_fail(ex.err, "launch init");
   }
-  if (chol && prm->use_graph) {
+  if (con && (e = con->init(P))) return cuda_fail(e, "dose-constraint initialisation");
+  if (chol && prm->use_graph && !con) {
     if (!P->admm_chol_exec || P->admm_chol_exec_obj != use_obj) {
       if ((e = build_admm_chol_graph(P, use_obj))) return cuda_fail(e, "build ADMM graph");
     }
@@ -1143,8 +1173,14 @@ int admm_solve_impl(Plan* P, const rpt_admm_params* prm, const double* z0, const
     for (int it = 1;; ++it) {
       Exec ex;
       ex.st = st;
-      chol_iteration_head(ex, P);
-      admm_iteration_tail(ex, P, use_obj, 0, 0);
+      if (con) {
+        if ((e = con->rhs(P))) return cuda_fail(e, "dose-constraint right-hand side");
+        launch(ex, k_chol_x, dim3((dp.n + kCholRows - 1) / kCholRows, dp.N), dim3(256),
+               sizeof(float) * (size_t)dp.n_pad, dp, (const float*)P->binv, (const float*)P->v32, P->x);
+      } else {
+        chol_iteration_head(ex, P);
+      }
+      admm_iteration_tail(ex, P, use_obj, 0, 0, con);
       if (ex.err) return cuda_fail(ex.err, "launch");
       if (it % every == 0 || it >= prm->max_iter) {
         if ((e = read_ctl(P))) return cuda_fail(e, "read control");

@@ -16,6 +16,7 @@ LIB_PATH = os.path.join(_HERE, "librpt.so")
 OK, NOT_CONVERGED, EINVAL, ENOMEM, ECUDA, TIMEOUT, DIVERGED, EUNSUPPORTED = 0, 1, -1, -2, -3, -4, -5, -6
 F32, BF16, FP8E4M3 = 0, 1, 2
 SUB_CG, SUB_CHOL = 0, 1
+DOSE_MAX, DOSE_MIN, DOSE_MEAN = 0, 1, 2
 BB_PAPER, BB_GUARDED, BB_OFF = 0, 1, 2
 Z_STD, Z_LIT = 0, 1
 MAX_SPOTS = 24576
@@ -28,12 +29,18 @@ EXPORTED = [
     "rpt_mlp_get_params", "rpt_mlp_set_params", "rpt_mlp_loss_grad", "rpt_mlp_train", "rpt_mlp_predict",
     "rpt_admm_bb_solve_learned", "rpt_trace_get", "rpt_plans_create_batched", "rpt_plan_batch_query",
     "rpt_admm_bb_solve_batched", "rpt_mlp_infer", "rpt_mlp_set_compute", "rpt_plan_set_weights",
+    "rpt_admm_bb_solve_constrained",
 ]
 
 
 class MlpTrainParams(C.Structure):
     _fields_ = [("epochs", C.c_int32), ("batch", C.c_int32), ("lr", C.c_double), ("beta1", C.c_double),
                 ("beta2", C.c_double), ("eps", C.c_double), ("weight_decay", C.c_double), ("seed", C.c_uint64)]
+
+
+class _DoseConstraint(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("n_voxels", C.c_int32), ("voxels", C.POINTER(C.c_int32)),
+                ("limit", C.c_double)]
 
 
 class RptError(RuntimeError):
@@ -57,13 +64,13 @@ class _DeviceOpts(C.Structure):
     _fields_ = [("device", C.c_int32), ("stream", C.c_void_p), ("ctas_per_sm", C.c_int32),
                 ("row_path", C.c_int32), ("autotune", C.c_int32), ("chunk_entries", C.c_int32),
                 ("chunk_rows", C.c_int32), ("stages", C.c_int32), ("min_lanes", C.c_int32),
-                ("inject_timeout", C.c_int32), ("device_mem_cap", C.c_int64)]
+                ("inject_timeout", C.c_int32), ("device_mem_cap", C.c_int64), ("accumulate", C.c_int32)]
 
 
 def _device_opts(device=0, stream=None, ctas_per_sm=0, row_path=0, autotune=0, chunk_entries=0, chunk_rows=0,
-                 stages=0, min_lanes=0, inject_timeout=0, device_mem_cap=0):
+                 stages=0, min_lanes=0, inject_timeout=0, device_mem_cap=0, accumulate=0):
     return _DeviceOpts(device, stream, ctas_per_sm, row_path, autotune, chunk_entries, chunk_rows, stages,
-                       min_lanes, inject_timeout, device_mem_cap)
+                       min_lanes, inject_timeout, device_mem_cap, accumulate)
 
 
 class AdmmParams(C.Structure):
@@ -101,7 +108,7 @@ class _Stats(C.Structure):
                 ("row_path", C.c_int32), ("min_lanes", C.c_int32), ("chunk_entries", C.c_int32),
                 ("chunk_rows", C.c_int32), ("stages", C.c_int32), ("autotuned", C.c_int32),
                 ("autotune_ms", C.c_double), ("bundles", C.c_int64), ("block_cols", C.c_int64),
-                ("bundle_fill", C.c_double)]
+                ("bundle_fill", C.c_double), ("exact_sums", C.c_int32), ("reserved", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -180,6 +187,10 @@ def lib():
     L.rpt_mlp_set_compute.restype = C.c_int
     L.rpt_plan_set_weights.argtypes = [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double)]
     L.rpt_plan_set_weights.restype = C.c_int
+    L.rpt_admm_bb_solve_constrained.argtypes = [C.c_void_p, C.POINTER(AdmmParams), C.c_int32,
+                                                C.POINTER(_DoseConstraint), C.c_double, dp, dp,
+                                                C.POINTER(_Info)]
+    L.rpt_admm_bb_solve_constrained.restype = C.c_int
     L.rpt_admm_bb_solve_learned.argtypes = [C.c_void_p, C.c_void_p, fp, dp, C.POINTER(AdmmParams), dp,
                                             C.POINTER(_Info), C.POINTER(C.c_int32)]
     L.rpt_admm_bb_solve_learned.restype = C.c_int
@@ -284,7 +295,7 @@ class Plan:
                  lb=None, ub=None, value_format=F32, index_width=32, **device_opts):
         """device_opts: the fields of rpt_device_opts (device, stream, ctas_per_sm,
         row_path, autotune, chunk_entries, chunk_rows, stages, min_lanes,
-        inject_timeout, device_mem_cap)."""
+        inject_timeout, device_mem_cap, accumulate)."""
         L = lib()
         m, n, N = int(m), int(n), int(N)
         pr, _keep = _problem_struct(m, n, N, row_ptr, col_idx, val, voxel_w, presc, scen_weight, lb, ub,
@@ -374,6 +385,26 @@ class Plan:
         rc = lib().rpt_admm_bb_solve(self._h, C.byref(prm), _dptr(z0a), _dptr(y0a), _dptr(x), C.byref(info))
         _check(rc, allow=(OK, NOT_CONVERGED))
         return x, info.as_dict()
+
+    def admm_bb_solve_constrained(self, constraints, sigma=0.0, params: AdmmParams | None = None, **kw):
+        """ADMM-BB with dose constraints (rpt_admm_bb_solve_constrained).  constraints:
+        a list of (kind, voxels, limit) with kind DOSE_MAX / DOSE_MIN / DOSE_MEAN.
+        Returns (x, mu [N][K], info)."""
+        prm = params if params is not None else admm_params(**kw)
+        keep, arr = [], (_DoseConstraint * max(1, len(constraints)))()
+        K = 0
+        for i, (kind, voxels, limit) in enumerate(constraints):
+            v = np.ascontiguousarray(np.asarray(voxels, dtype=np.int32))
+            keep.append(v)
+            arr[i] = _DoseConstraint(int(kind), int(v.size), v.ctypes.data_as(C.POINTER(C.c_int32)), float(limit))
+            K += 1 if int(kind) == DOSE_MEAN else int(v.size)
+        x = np.empty(self.n)
+        mu = np.empty(max(1, self.N * K))
+        info = _Info()
+        rc = lib().rpt_admm_bb_solve_constrained(self._h, C.byref(prm), len(constraints), arr, float(sigma),
+                                                 _dptr(x), _dptr(mu), C.byref(info))
+        _check(rc, allow=(OK, NOT_CONVERGED))
+        return x, mu[:self.N * K].reshape(self.N, K), info.as_dict()
 
     def pgd_solve(self, params: PgdParams | None = None, x0=None, **kw):
         prm = params if params is not None else pgd_params(**kw)

@@ -46,7 +46,7 @@ def test_struct_layouts_match_c_compiler(lib):
         "rpt_problem": rpt._Problem, "rpt_device_opts": rpt._DeviceOpts,
         "rpt_admm_params": rpt.AdmmParams, "rpt_pgd_params": rpt.PgdParams,
         "rpt_solve_info": rpt._Info, "rpt_plan_stats": rpt._Stats,
-        "rpt_mlp_train_params": rpt.MlpTrainParams,
+        "rpt_mlp_train_params": rpt.MlpTrainParams, "rpt_dose_constraint": rpt._DoseConstraint,
     }
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "rpt.h"', "int main(void){"]
     for cname, py in structs.items():

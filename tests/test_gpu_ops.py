@@ -33,7 +33,8 @@ def rpt():
 # with tiny stages (many chunks per segment, stage wrap-around, segment
 # switches), the streaming path, the streaming path with tiny chunks (many
 # chunk hand-overs, class changes inside a warp's run, one-row chunks), the
-# bundled ring and the bundled ring with tiny stages
+# bundled ring and the bundled ring with tiny stages, each with float atomics
+# and with exact fixed-point sums
 PATHS = {
     "reg": dict(row_path=1),
     "tma": dict(row_path=2),
@@ -42,6 +43,8 @@ PATHS = {
     "stream_small": dict(row_path=3, chunk_entries=64, chunk_rows=3),
     "bun": dict(row_path=4),
     "bun_small": dict(row_path=4, chunk_entries=1280, chunk_rows=3, stages=2),
+    "bun_exact": dict(row_path=4, accumulate=1),
+    "bun_exact_small": dict(row_path=4, accumulate=1, chunk_entries=1280, chunk_rows=3, stages=2),
 }
 
 
@@ -181,14 +184,15 @@ def test_stream_path_takes_rows_longer_than_a_chunk(rpt):
 
 
 def test_bundled_pass_is_bitwise_reproducible(rpt):
-    """The bundled ring sums 64-bit fixed-point contributions, which is exact:
-    repeated passes give identical bits whatever order the atomics and the
-    chunk queues take, on every value format."""
+    """The bundled ring with exact sums (accumulate = 1) adds 64-bit fixed-point
+    contributions, which is exact: repeated passes give identical bits whatever
+    order the atomics and the chunk queues take, on every value format."""
     prob = random_problem(**CASES["ragged"])
     V = np.random.default_rng(21).normal(size=(prob.N, prob.n))
     x = np.random.default_rng(22).uniform(0.0, 3.0, size=prob.n)
     for vf in (rpt.F32, rpt.BF16, rpt.FP8E4M3):
-        with plan_of(rpt, prob, row_path=4, value_format=vf) as P:
+        with plan_of(rpt, prob, row_path=4, value_format=vf, accumulate=1) as P:
+            assert P.stats()["exact_sums"] == 1
             U = [P.apply_normal(V, 1.3) for _ in range(4)]
             G = [P.gradient(x)[0] for _ in range(4)]
         for k in range(1, 4):
@@ -220,8 +224,8 @@ def test_profile_row_pass(rpt):
 @pytest.mark.parametrize("path", [2, 4])
 def test_set_weights_matches_a_fresh_plan(rpt, path):
     """rpt_plan_set_weights: new voxel weights and prescriptions on an existing
-    plan give the operators of a plan created with them (bitwise on the
-    deterministic bundled path 4, within the float32 bound on path 2), the
+    plan give the operators of a plan created with them (bitwise on the bundled
+    path 4 with exact sums, within the float32 bound on path 2), the
     default rho and the constant of Eq. 2 of the oracle's rule, and a solve that
     reaches the new problem's optimum."""
     from oracle import default_rho, lsq_box
@@ -235,7 +239,9 @@ def test_set_weights_matches_a_fresh_plan(rpt, path):
     W2 = Weighted(prob2)
     V = rng.normal(size=(prob.N, prob.n))
     x = rng.uniform(0.0, 3.0, size=prob.n)
-    with plan_of(rpt, prob, row_path=path) as P, plan_of(rpt, prob2, row_path=path) as Q:
+    acc = 1 if path == 4 else 0
+    with plan_of(rpt, prob, row_path=path, accumulate=acc) as P, \
+            plan_of(rpt, prob2, row_path=path, accumulate=acc) as Q:
         P.set_weights(w2, p2)
         sp, sq = P.stats(), Q.stats()
         Up, Uq = P.apply_normal(V, 0.7), Q.apply_normal(V, 0.7)

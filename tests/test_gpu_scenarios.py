@@ -39,7 +39,10 @@ def test_first_k_scenarios_reach_their_own_optimum(rpt, tiny, k):
     assert ia["status"] == 0 and ip["status"] == 0
     assert np.all(z >= sub.lb) and np.all(z <= sub.ub)
     assert (W.f(z) - fs) / fs <= 1e-6, (k, (W.f(z) - fs) / fs)
-    assert (W.f(xp) - fs) / fs <= 2e-6, (k, (W.f(xp) - fs) / fs)
+    # PGD stops on the GPU's own objective, a sum of float32 row residuals squared
+    # (relative error up to about 2 (L + 8) eps32 of the sum of squared magnitudes,
+    # ~1e-5 here), so its target is met to that accuracy
+    assert (W.f(xp) - fs) / fs <= 3e-5, (k, (W.f(xp) - fs) / fs)
 
 
 def test_dvh_report_from_gpu_doses_matches_the_oracle(rpt, tiny):
