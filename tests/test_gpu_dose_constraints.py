@@ -7,7 +7,11 @@ the tiny phantom.
 Tolerances.  The GPU's x-update is the float32 cached inverse of
 B_s + (sigma/2) G_s'G_s (relative error about n cond(B_s) eps32 per solve, as for
 the plain cached-factor solver); the constraint rows and the dose-block updates
-are float64."""
+are float64.  That error sets a floor under the residuals of Eq. 9: at
+eps = 1e-8 the primal residual of these cases stalls above eps_prim (the oracle
+with its Cholesky solves replaced by a float32 inverse stalls the same way), and
+1e-7 is the tightest decade reached; there the float32-inverse iteration ends
+within 3e-7 of the optimum's objective and 4e-7 of each limit."""
 import json
 import os
 
@@ -43,7 +47,10 @@ def _case(kind_set, seed):
     dose = np.array([W.dose(s, x0) for s in range(W.N)])
     cons = []
     if "max" in kind_set:
-        cons.append(DoseConstraint("max", np.array([0, 1]), 0.8 * float(dose[:, [0, 1]].max())))
+        # with all three kinds one maximum voxel, so that the rows stay within the
+        # enumeration's limit of 8 (max 2 + mean 2 + min 4 over the 2 scenarios)
+        vox = np.array([0]) if len(kind_set) == 3 else np.array([0, 1])
+        cons.append(DoseConstraint("max", vox, 0.8 * float(dose[:, vox].max())))
     if "mean" in kind_set:
         cons.append(DoseConstraint("mean", np.arange(2, 7), 0.9 * float(dose[:, 2:7].mean(axis=1).max())))
     if "min" in kind_set:
@@ -110,7 +117,7 @@ def test_reaches_the_exact_constrained_optimum(rpt, kinds, seed):
     Ga, ha = sp.vstack(G).toarray(), np.concatenate(h)
     xb, lam = kkt_bruteforce_lin(W, Ga, ha)
     with plan_of(rpt, P) as Q:
-        z, mu, info = Q.admm_bb_solve_constrained(_lib_cons(cons), eps_abs=1e-8, eps_rel=1e-8, max_iter=100000)
+        z, mu, info = Q.admm_bb_solve_constrained(_lib_cons(cons), eps_abs=1e-7, eps_rel=1e-7, max_iter=100000)
     assert info["status"] == 0, info
     assert abs(W.f(z) - W.f(xb)) / W.f(xb) <= 1e-6
     assert np.all(Ga @ z <= ha + 1e-6 * (1 + np.abs(ha)))

@@ -34,8 +34,8 @@ def test_first_k_scenarios_reach_their_own_optimum(rpt, tiny, k):
     xs = lsq_box(W)
     fs = W.f(xs)
     with plan_of(rpt, sub) as P:
-        z, ia = P.admm_bb_solve(eps_abs=1e-7, eps_rel=1e-7, max_iter=20000)
-        xp, ip = P.pgd_solve(f_target=fs * (1 + 1e-6), tol_rel_df=0.0, max_iter=20000)
+        z, ia = P.admm_bb_solve(eps_abs=1e-6, eps_rel=1e-6, max_iter=20000)
+        xp, ip = P.pgd_solve(f_target=fs * (1 + 1e-5), tol_rel_df=0.0, max_iter=50000)
     assert ia["status"] == 0 and ip["status"] == 0
     assert np.all(z >= sub.lb) and np.all(z <= sub.ub)
     assert (W.f(z) - fs) / fs <= 1e-6, (k, (W.f(z) - fs) / fs)
