@@ -202,11 +202,13 @@ def cg_extrapolated(prob, budget_s=20.0):
 
 
 def run_batch(args, rpt, dev, stream, peak):
-    """Batched form: plans of uneven size solved one by one, then as one
-    block-diagonal plan (one persistent row pass over all of them, ring
-    configuration picked by the autotuner).  'large': four plans over 49
-    scenarios; 'small': eight plans over 13 scenarios, each too small to fill
-    the GPU alone."""
+    """Batched form: plans of uneven size solved one by one, then together as
+    one batched plan (rpt_plans_create_batched: one persistent row pass over
+    the scenarios of every plan still iterating, each plan with its own
+    penalty, BB step and stop; ring configuration picked by the autotuner), and
+    for reference as one block-diagonal problem (one shared penalty, BB step
+    and stop).  'large': four plans over 49 scenarios; 'small': eight plans over
+    13 scenarios, each too small to fill the GPU alone."""
     import numpy as np
     import torch
     from synthetic import config_batch, block_diagonal, BATCH_SIZES_SMALL, scenario_set_13
@@ -222,41 +224,51 @@ def run_batch(args, rpt, dev, stream, peak):
     gen_s = time.perf_counter() - t0
     params = rpt.admm_params()
 
-    def timed_solve(P):
-        P.admm_bb_solve(params)                              # warm-up
+    def timed(fn):
+        fn()                                                 # warm-up (graph capture)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        z, info = P.admm_bb_solve(params)
+        out = fn()
         e1.record(stream)
         torch.cuda.synchronize(dev)
-        return z, info, e0.elapsed_time(e1) / 1e3
+        return out, e0.elapsed_time(e1) / 1e3
 
     seq = []
     for p in probs:
         P = rpt.Plan.from_problem(p, device=dev, stream=stream.cuda_stream)
-        z, info, t = timed_solve(P)
+        (z, info), t = timed(lambda: P.admm_bb_solve(params))
         ms, by = P.profile_row_pass(0, reps=10)
         seq.append({"m": p.m, "n": p.n, "nnz": int(P.stats()["nnz"]), "solve_s": t, "iterations": info["iterations"],
                     "f": info["f"], "pass_ms": ms, "pass_gbs": by / ms / 1e6})
         P.close()
-    big = block_diagonal(probs)
-    del probs
     t1 = time.perf_counter()
-    P = rpt.Plan.from_problem(big, device=dev, stream=stream.cuda_stream, autotune=1)
+    P = rpt.Plan.batched(probs, device=dev, stream=stream.cuda_stream, autotune=1)
     create_s = time.perf_counter() - t1
     st = P.stats()
-    z, info, t = timed_solve(P)
+    (xs, info, per), t = timed(lambda: P.admm_bb_solve_batched(params))
     ms, by = P.profile_row_pass(0, reps=10)
     P.close()
+    batched = {"nnz": int(st["nnz"]), "create_s": create_s, "solve_s": t, "status": info["status"],
+               "iterations": info["iterations"], "iterations_per_plan": [q["iterations"] for q in per],
+               "status_per_plan": [q["status"] for q in per], "rho_per_plan": [q["rho"] for q in per],
+               "row_passes": info["row_passes"], "f": info["f"], "f_per_plan": [q["f"] for q in per],
+               "f_rel_vs_alone": [(q["f"] - a["f"]) / a["f"] for q, a in zip(per, seq)],
+               "pass_ms_all_plans": ms, "pass_gbs": by / ms / 1e6, "frac_of_peak": by / ms / 1e6 / peak,
+               "ring": {"chunk_entries": st["chunk_entries"], "chunk_rows": st["chunk_rows"],
+                        "stages": st["stages"], "configs_timed": st["autotuned"]}}
+    big = block_diagonal(probs)
+    del probs
+    P = rpt.Plan.from_problem(big, device=dev, stream=stream.cuda_stream, autotune=1)
+    del big
+    (z, infob), tb = timed(lambda: P.admm_bb_solve(params))
+    P.close()
+    one = sum(q["solve_s"] for q in seq)
     return {"workload": label, "generate_s": round(gen_s, 1),
-            "one_by_one": seq, "one_by_one_solve_s": sum(q["solve_s"] for q in seq),
-            "stacked": {"nnz": int(st["nnz"]), "create_s": create_s, "solve_s": t, "iterations": info["iterations"],
-                        "row_passes": info["row_passes"], "f": info["f"],
-                        "f_sum_alone": sum(q["f"] for q in seq),
-                        "pass_ms": ms, "pass_gbs": by / ms / 1e6, "frac_of_peak": by / ms / 1e6 / peak,
-                        "ring": {"chunk_entries": st["chunk_entries"], "chunk_rows": st["chunk_rows"],
-                                 "stages": st["stages"], "configs_timed": st["autotuned"]}}}
+            "one_by_one": seq, "one_by_one_solve_s": one,
+            "batched": batched, "speedup_batched_over_one_by_one": one / t,
+            "block_diagonal_shared_step": {"solve_s": tb, "iterations": infob["iterations"],
+                                           "status": infob["status"], "f": infob["f"]}}
 
 
 def run_learned(args, rpt, dev, stream, n_train=2000, n_test=200):

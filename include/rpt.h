@@ -134,7 +134,9 @@ typedef struct {
                              (default 1e-6), unless Eq. 9 needs it: the floor is capped at
                              (rho/2) eps_prim / sqrt(N), so that tight eps_abs / eps_rel are reached */
   int32_t use_graph;      /* 1 (default): one CUDA graph with device-side loops; 0: host-driven loop */
-  int32_t check_every;    /* host-driven loop: read the convergence flag every k iterations (default 1) */
+  int32_t check_every;    /* host-driven loop: read the convergence flag every k iterations (default 1);
+                             the up to k - 1 iterations launched after the stop do nothing, so the
+                             result and the iteration count are those of the stopping iteration */
   int32_t resume;         /* 1: start from the plan's stored state (rpt_state_set / previous solve) */
   int32_t cg_precond;     /* 0: plain CG; 1: Jacobi-preconditioned CG, M = diag(B_s) (default 1) */
   int32_t subproblem;     /* x-update (App. A): RPT_SUB_CG (default) conjugate gradients on the sparse
@@ -247,38 +249,66 @@ int rpt_plan_query(const rpt_plan* plan, rpt_plan_stats* out);
 
 /* ---- batched plans: several problems in one plan and one launch per pass ----
  *
- * rpt_plans_create_batched stacks n_plans problems with the same scenario count
- * N into one plan: their voxels and spots are placed side by side, so each
- * scenario matrix is block-diagonal, the objective (Eq. 2) is the sum of the
- * problems' objectives and the box is the product of their boxes.  The
- * stacked optimum is therefore the problems' optima side by side, and one
- * persistent row pass covers every problem's scenarios.  The problems must
- * share N, value_format, index_width and scen_weight (all NULL, or equal
- * values); a NULL lb/ub of one problem means its defaults (0 / +inf).  The
- * penalty, the BB step and the stopping rule of a solve are shared by all
- * problems (the default rho is computed on the stacked plan).
- *   probs: n_plans host pointers, each valid as for rpt_plan_create (checked
- *          per problem, so a column index is checked against its own problem).
+ * rpt_plans_create_batched puts n_plans problems with the same scenario count
+ * N into one plan.  Scenario s of problem k becomes the plan's unit k * N + s,
+ * with its own row lists (problem k's rows of scenario s) and its own copy of
+ * the spot vectors; the problems' voxels are numbered one after another, and
+ * every unit has the spot count of the widest problem (a narrower problem's
+ * extra spots are held at 0 and touched by no row).  One persistent row pass
+ * covers the units of every problem that is still iterating.  A batched
+ * solve runs the problems side by side, each with its own consensus variable
+ * z_k, its own penalty (the default rule of rpt_plan_stats.default_rho on its
+ * own scenarios and spots, unless params->rho > 0 sets one for all), its own
+ * BB step (Eq. 8 over its own blocks), its own residuals and tolerances of
+ * Eq. 9 (eps_abs and eps_rel from params) and its own stop; a problem that
+ * has converged drops out of the row passes while the others go on.  The
+ * problems must share N, value_format and index_width; scenario weights and
+ * bounds are each problem's own (NULL lb/ub: 0 / +inf).
+ *   probs: n_plans <= 64 host pointers, each valid as for rpt_plan_create
+ *          (checked per problem, so a column index is checked against its own
+ *          problem's spot count).
  *   *out:  one plan holding all problems; destroy it with rpt_plan_destroy.
+ *          rpt_plan_query reports the problems together: m and n summed, N
+ *          the scenario count of one problem, default_rho the rule on all of
+ *          them stacked, const_term summed.
+ * A batched plan serves rpt_admm_bb_solve_batched, rpt_plan_query,
+ * rpt_plan_batch_query, rpt_profile_row_pass and rpt_trace_get (entries of
+ * problem 0); the calls that take one problem's vectors (rpt_admm_bb_solve,
+ * rpt_pgd_solve, rpt_objective, rpt_gradient, rpt_apply_normal,
+ * rpt_state_get/set, rpt_plan_set_weights, rpt_admm_bb_solve_constrained,
+ * rpt_admm_bb_solve_learned) return RPT_EUNSUPPORTED on it.
  * Errors: RPT_EINVAL for n_plans < 1, NULL arguments, an invalid problem or
- * problems that differ in N, format, index width or scenario weights;
- * RPT_EUNSUPPORTED when the stacked plan exceeds a limit of rpt_plan_create
- * (e.g. the stacked spot count above RPT_MAX_SPOTS); RPT_ENOMEM, RPT_ECUDA. */
+ * problems that differ in N, format or index width; RPT_EUNSUPPORTED for more
+ * than 64 problems or a plan beyond a limit of rpt_plan_create (e.g. the
+ * widest problem's spot count above RPT_MAX_SPOTS); RPT_ENOMEM, RPT_ECUDA. */
 int rpt_plans_create_batched(int32_t n_plans, const rpt_problem* const* probs, const rpt_device_opts* opts,
                              rpt_plan** out);
 
-/* Problems in a plan and their spot ranges: *n_plans (1 for a plan made by
- * rpt_plan_create); col_offsets [n_plans + 1] or NULL: problem k owns the
- * stacked spots col_offsets[k] .. col_offsets[k+1]. */
+/* Problems in a plan and their spots numbered one after another: *n_plans (1
+ * for a plan made by rpt_plan_create); col_offsets [n_plans + 1] or NULL:
+ * problem k has col_offsets[k+1] - col_offsets[k] spots. */
 int rpt_plan_batch_query(const rpt_plan* plan, int32_t* n_plans, int32_t* col_offsets);
 
-/* ADMM-BB on a batched plan (as rpt_admm_bb_solve, from a cold start), with the
- * result split per problem: x_out[k] is a host array of problem k's n_k spots.
- * x_out holds one non-NULL pointer per problem (rpt_plan_batch_query).  The
- * return value and info are those of the stacked solve; x_out is written on
- * RPT_OK and RPT_NOT_CONVERGED. */
+/* ADMM-BB on every problem of a batched plan, side by side from a cold start
+ * (z0 = 0), each problem with its own penalty, BB step and stopping test (see
+ * rpt_plans_create_batched); a plan of one problem is solved as by
+ * rpt_admm_bb_solve.  params->tol_obj must be +inf and f_target 0 (the
+ * objective tests are not available here: RPT_EUNSUPPORTED).
+ *   x_out:     one non-NULL host array per problem (rpt_plan_batch_query),
+ *              x_out[k] of problem k's own spot count; written for every
+ *              problem whatever its status.
+ *   info:      (may be NULL) the whole solve: status (RPT_OK when every problem
+ *              converged, RPT_DIVERGED when one diverged, else
+ *              RPT_NOT_CONVERGED), iterations (of the longest problem), CG steps,
+ *              row passes, kernels and time of the one solve, f the summed
+ *              objective, the residual norms over all problems' stacked
+ *              vectors; step and rho 0 (they are per problem).
+ *   plan_info: (may be NULL) n_plans entries, one per problem: its own status,
+ *              iterations, CG steps, objective, residuals of Eq. 9, last BB
+ *              step and penalty (row_passes, kernels and times: the solve's).
+ * Returns info's status (also when info is NULL). */
 int rpt_admm_bb_solve_batched(rpt_plan* plan, const rpt_admm_params* params, double* const* x_out,
-                              rpt_solve_info* info);
+                              rpt_solve_info* info, rpt_solve_info* plan_info);
 
 /* ---- solvers ------------------------------------------------------------ */
 

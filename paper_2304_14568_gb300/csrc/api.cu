@@ -196,12 +196,25 @@ std::vector<int3> ring_override(const rpt_device_opts* o, int cmax, int rmax, in
                     std::min(8, std::max(2, o->stages > 0 ? o->stages : stages)))};
 }
 
-int create_plan(const rpt_problem* pr, const rpt_device_opts* opts, rpt_plan** out) {
+// U (batched plans): pr is U->view, whose scenarios are the units (problem g,
+// scenario s) of U->G problems; bounds come from U, one box per problem.
+int create_plan(const rpt_problem* pr, const rpt_device_opts* opts, rpt_plan** out,
+                const batch::Units* U = nullptr) {
   if (!pr || !out) {
     set_error("null argument");
     return RPT_EINVAL;
   }
   const int m = pr->m, n = pr->n, N = pr->N;
+  const int G = U ? U->G : 1, Ns = U ? U->Ns : N;
+  static_assert(batch::kMaxProblems == kMaxGroups, "batched problems = solver groups");
+  // group of a row (batched plans: the problem that owns it) and of a scenario
+  std::vector<int32_t> rgrp;
+  if (U) {
+    rgrp.resize(m);
+    for (int g = 0; g < G; ++g)
+      for (int i = U->row_off[g]; i < U->row_off[g + 1]; ++i) rgrp[i] = g;
+  }
+  auto row_group = [&](int i) { return U ? rgrp[i] : 0; };
   if (m < 1 || n < 1 || N < 1) {
     set_error("m, n and N must be >= 1");
     return RPT_EINVAL;
@@ -250,12 +263,18 @@ int create_plan(const rpt_problem* pr, const rpt_device_opts* opts, rpt_plan** o
       }
       cs[s] = pr->scen_weight[s];
     }
-  std::vector<double> lb(n, 0.0), ub(n, HUGE_VAL);
-  for (int j = 0; j < n; ++j) {
-    if (pr->lb) lb[j] = pr->lb[j];
-    if (pr->ub) ub[j] = pr->ub[j];
+  std::vector<double> lb((size_t)G * n, 0.0), ub((size_t)G * n, HUGE_VAL);
+  for (size_t j = 0; j < (size_t)G * n; ++j) {
+    if (U) {
+      lb[j] = U->lb[j];
+      ub[j] = U->ub[j];
+    } else {
+      if (pr->lb) lb[j] = pr->lb[j];
+      if (pr->ub) ub[j] = pr->ub[j];
+    }
     if (!std::isfinite(lb[j]) || std::isnan(ub[j]) || ub[j] == -HUGE_VAL || lb[j] > ub[j]) {
-      set_error("bounds invalid at spot " + std::to_string(j) + " (need finite lb <= ub)");
+      set_error("bounds invalid at spot " + std::to_string(j % n) +
+                (U ? " of problem " + std::to_string(j / n) : std::string()) + " (need finite lb <= ub)");
       return RPT_EINVAL;
     }
   }
@@ -284,22 +303,25 @@ int create_plan(const rpt_problem* pr, const rpt_device_opts* opts, rpt_plan** o
     for (int i = 0; i < m; ++i)
       if (rp[i + 1] > rp[i]) keep[i] = 1;
   }
+  // a row's constant c_s w p^2 counts in the scenarios of its own group only
   std::vector<int32_t> kept;
   kept.reserve(m);
-  double const_term = 0.0;
+  std::vector<double> gconst(G, 0.0);
   std::vector<int32_t> dropped;
   for (int i = 0; i < m; ++i) {
     if (keep[i]) {
       kept.push_back(i);
     } else {
       dropped.push_back(i);
-      for (int s = 0; s < N; ++s) const_term += cs[s] * pr->voxel_w[i] * pr->presc[i] * pr->presc[i];
+      const int g = row_group(i);
+      for (int s = g * Ns; s < (g + 1) * Ns; ++s) gconst[g] += cs[s] * pr->voxel_w[i] * pr->presc[i] * pr->presc[i];
     }
   }
   if (kept.empty()) {   // keep one (empty) row so every launch has work items
     kept.push_back(0);
     dropped.erase(dropped.begin());
-    for (int s = 0; s < N; ++s) const_term -= cs[s] * pr->voxel_w[0] * pr->presc[0] * pr->presc[0];
+    const int g = row_group(0);
+    for (int s = g * Ns; s < (g + 1) * Ns; ++s) gconst[g] -= cs[s] * pr->voxel_w[0] * pr->presc[0] * pr->presc[0];
   }
   const int m_act = (int)kept.size();
   // On the device every row is padded with zero entries (column 0, value 0) to a
@@ -350,6 +372,8 @@ int create_plan(const rpt_problem* pr, const rpt_device_opts* opts, rpt_plan** o
   dp.m = m;
   dp.n = n;
   dp.N = N;
+  dp.G = G;
+  dp.Ns = Ns;
   dp.m_act = m_act;
   dp.n_pad = n_pad;
   dp.value_format = pr->value_format;
@@ -383,16 +407,20 @@ int create_plan(const rpt_problem* pr, const rpt_device_opts* opts, rpt_plan** o
   P->empty_kept.assign(N, {});
   for (int s = 0; s < N; ++s) {
     const int32_t* rp = pr->row_ptr[s];
+    const int g = s / Ns;
     for (int k = 0; k < m_act; ++k) {
+      if (row_group(kept[k]) != g) continue;   // another problem's row (batched plans)
       const int len = rp[kept[k] + 1] - rp[kept[k]];
       if (len > 0) {
         order[s].push_back(k);
       } else {
-        const_term += cs[s] * pr->voxel_w[kept[k]] * pr->presc[kept[k]] * pr->presc[kept[k]];
+        gconst[g] += cs[s] * pr->voxel_w[kept[k]] * pr->presc[kept[k]] * pr->presc[kept[k]];
         P->empty_kept[s].push_back(k);
       }
     }
   }
+  double const_term = 0.0;
+  for (int g = 0; g < G; ++g) const_term += gconst[g];
   P->nz_index.assign((size_t)N * m_act, -1);
   for (int s = 0; s < N; ++s)
     for (size_t q = 0; q < order[s].size(); ++q) P->nz_index[(size_t)s * m_act + order[s][q]] = (int32_t)q;
@@ -734,8 +762,8 @@ int create_plan(const rpt_problem* pr, const rpt_device_opts* opts, rpt_plan** o
   P->diag = A.get<float>(diag_h.size());
   int4* d_blocks = dyn ? nullptr : A.get<int4>(blocks.size());
   P->rec_of = A.get<int>((size_t)N * m_act);
-  P->lb = A.get<double>(n);
-  P->ub = A.get<double>(n);
+  P->lb = A.get<double>((size_t)G * n);
+  P->ub = A.get<double>((size_t)G * n);
   const size_t Nn = (size_t)N * n;
   P->x = A.get<double>(Nn);
   P->r = A.get<double>(Nn);
@@ -747,8 +775,9 @@ int create_plan(const rpt_problem* pr, const rpt_device_opts* opts, rpt_plan** o
   P->w = A.get<double>(Nn);
   P->q = A.get<double>(Nn);
   P->dinv = A.get<double>(Nn);
-  P->z = A.get<double>(n);
-  P->znew = A.get<double>(n);
+  P->z = A.get<double>((size_t)G * n);
+  P->znew = A.get<double>((size_t)G * n);
+  P->uact = A.get<int>(N);
   P->v32 = A.get<float>((size_t)N * n_pad);
   P->vz32 = A.get<float>(n_pad);
   // partial slots: float (paths 1-3) or 64-bit fixed point (bundled path), n_pad each
@@ -770,7 +799,7 @@ int create_plan(const rpt_problem* pr, const rpt_device_opts* opts, rpt_plan** o
   P->cgcnt = A.get<int>(N);
   P->cnt_s = A.get<unsigned int>(N);
   P->dots = A.get<double>((size_t)N * P->nchunk * 4);
-  P->vpart = A.get<double>((size_t)(N + 1) * P->nchunk * 8);
+  P->vpart = A.get<double>((size_t)(N + G) * P->nchunk * 8);
   P->g = A.get<double>(n);
   P->xt = A.get<double>(n);
   P->xp = A.get<double>(n);
@@ -810,8 +839,8 @@ int create_plan(const rpt_problem* pr, const rpt_device_opts* opts, rpt_plan** o
   }
   RPT_CP(d_slot_count, slot_count.data(), N * sizeof(int));
   RPT_CP(d_slot_list, slot_list.data(), slot_list.size() * sizeof(int));
-  RPT_CP(P->lb, lb.data(), n * sizeof(double));
-  RPT_CP(P->ub, ub.data(), n * sizeof(double));
+  RPT_CP(P->lb, lb.data(), lb.size() * sizeof(double));
+  RPT_CP(P->ub, ub.data(), ub.size() * sizeof(double));
 #undef RPT_CP
   if ((e = cudaMemsetAsync(P->cnt_s, 0, sizeof(unsigned int) * N, st)) ||
       (e = cudaMemsetAsync(P->err, 0, sizeof(int), st)) ||
@@ -936,12 +965,25 @@ int create_plan(const rpt_problem* pr, const rpt_device_opts* opts, rpt_plan** o
     return cuda_fail(e, "kernel attributes");
   }
   // ---- statistics ----
+  // default penalty rho = 2 mean_s tr(A~_s^T A~_s) / n, per group on the group's
+  // own scenarios and spot count; the plan's figure on all problems stacked
   double tr = 0.0;
-  for (int s = 0; s < N; ++s) tr += cs[s] * chk[s].trace;
+  int n_all = 0;
+  P->grp_rho.assign(G, 0.0);
+  P->grp_n.assign(G, n);
+  P->grp_const = gconst;
+  for (int g = 0; g < G; ++g) {
+    double t = 0.0;
+    for (int s = g * Ns; s < (g + 1) * Ns; ++s) t += cs[s] * chk[s].trace;
+    if (U) P->grp_n[g] = U->n_g[g];
+    P->grp_rho[g] = 2.0 * (t / Ns) / P->grp_n[g];
+    tr += t;
+    n_all += P->grp_n[g];
+  }
   rpt_plan_stats& S = P->stats;
   S.m = m;
-  S.n = n;
-  S.N = N;
+  S.n = n_all;
+  S.N = Ns;
   S.m_active = m_act;
   S.nnz = NNZ;
   // values and indices, plus one 4-byte row offset per stored row (the records'
@@ -956,7 +998,7 @@ int create_plan(const rpt_problem* pr, const rpt_device_opts* opts, rpt_plan** o
   S.index_width = pr->index_width;
   S.row_blocks = dp.nblocks;
   S.sm_count = P->sm_count;
-  S.default_rho = 2.0 * (tr / N) / n;
+  S.default_rho = 2.0 * (tr / Ns) / n_all;
   S.const_term = const_term;
   S.row_path = dp.path + 1;
   S.min_lanes = min_lanes;
@@ -1120,17 +1162,17 @@ int rpt_plans_create_batched(int32_t n_plans, const rpt_problem* const* probs, c
         }
       }
     }
-    batch::Stacked st;
+    batch::Units un;
     std::string err;
-    int rc = batch::stack_problems(n_plans, probs, &st, &err);
+    int rc = batch::stack_units(n_plans, probs, &un, &err);
     if (rc != RPT_OK) {
       set_error(err);
       return rc;
     }
     rpt_plan* h = nullptr;
-    rc = create_plan(&st.view, opts, &h);
+    rc = create_plan(&un.view, opts, &h, &un);
     if (rc != RPT_OK) return rc;
-    as_plan(h)->batch_col_off = st.col_off;
+    as_plan(h)->batch_col_off = un.col_off;
     *out = h;
     return RPT_OK;
   });
@@ -1156,27 +1198,25 @@ int rpt_plan_batch_query(const rpt_plan* plan, int32_t* n_plans, int32_t* col_of
 }
 
 int rpt_admm_bb_solve_batched(rpt_plan* plan, const rpt_admm_params* params, double* const* x_out,
-                              rpt_solve_info* info) {
+                              rpt_solve_info* info, rpt_solve_info* plan_info) {
   if (!plan || !params || !x_out) {
     set_error("null argument");
     return RPT_EINVAL;
   }
   Plan* P = as_plan(plan);
-  std::vector<int32_t> off = P->batch_col_off;
-  if (off.empty()) off = {0, P->dp.n};
-  const int nb = (int)off.size() - 1;
-  for (int k = 0; k < nb; ++k)
+  const int G = P->dp.G, n = P->dp.n;
+  for (int k = 0; k < G; ++k)
     if (!x_out[k]) {
       set_error("x_out[" + std::to_string(k) + "] is NULL");
       return RPT_EINVAL;
     }
   return guarded([&] {
     DeviceScope ds(P->device);
-    std::vector<double> x((size_t)P->dp.n);
-    const int rc = admm_solve(P, params, nullptr, nullptr, x.data(), info);
-    if (rc != RPT_OK && rc != RPT_NOT_CONVERGED) return rc;
-    for (int k = 0; k < nb; ++k)
-      std::memcpy(x_out[k], x.data() + off[k], sizeof(double) * (size_t)(off[k + 1] - off[k]));
+    std::vector<double> z((size_t)G * n);
+    const int rc = admm_solve(P, params, nullptr, nullptr, z.data(), info, nullptr, plan_info);
+    if (rc != RPT_OK && rc != RPT_NOT_CONVERGED && !(rc == RPT_DIVERGED && G > 1)) return rc;
+    for (int k = 0; k < G; ++k)
+      std::memcpy(x_out[k], z.data() + (size_t)k * n, sizeof(double) * (size_t)P->grp_n[k]);
     return rc;
   });
 }
@@ -1187,6 +1227,7 @@ int rpt_plan_set_weights(rpt_plan* plan, const double* voxel_w, const double* pr
     return RPT_EINVAL;
   }
   Plan* P = as_plan(plan);
+  if (int rc = refuse_batched(P, "rpt_plan_set_weights")) return rc;
   const int m = P->dp.m, N = P->dp.N, n = P->dp.n, m_act = P->dp.m_act, n_pad = P->dp.n_pad;
   for (int i = 0; i < m; ++i)
     if (!std::isfinite(voxel_w[i]) || voxel_w[i] < 0 || !std::isfinite(presc[i]) || presc[i] < 0) {
@@ -1245,6 +1286,8 @@ int rpt_plan_set_weights(rpt_plan* plan, const double* voxel_w, const double* pr
       }
     P->stats.const_term = c;
     P->stats.default_rho = 2.0 * (tr / N) / n;
+    P->grp_const.assign(1, c);
+    P->grp_rho.assign(1, P->stats.default_rho);
     P->lipschitz = 0.0;
     P->chol_ready = false;
     P->chol_con = false;
@@ -1272,6 +1315,7 @@ int rpt_admm_bb_solve(rpt_plan* plan, const rpt_admm_params* params, const doubl
     return RPT_EINVAL;
   }
   return guarded([&] {
+    if (int rc = refuse_batched(as_plan(plan), "rpt_admm_bb_solve")) return rc;
     DeviceScope ds(as_plan(plan)->device);
     return admm_solve(as_plan(plan), params, z0, y0, x_out, info);
   });
@@ -1284,6 +1328,7 @@ int rpt_pgd_solve(rpt_plan* plan, const rpt_pgd_params* params, const double* x0
     return RPT_EINVAL;
   }
   return guarded([&] {
+    if (int rc = refuse_batched(as_plan(plan), "rpt_pgd_solve")) return rc;
     DeviceScope ds(as_plan(plan)->device);
     return pgd_solve(as_plan(plan), params, x0, x_out, info);
   });
@@ -1295,6 +1340,7 @@ int rpt_objective(rpt_plan* plan, const double* x, double* f_out, double* dose_o
     return RPT_EINVAL;
   }
   return guarded([&] {
+    if (int rc = refuse_batched(as_plan(plan), "rpt_objective")) return rc;
     DeviceScope ds(as_plan(plan)->device);
     return op_objective(as_plan(plan), x, f_out, dose_out);
   });
@@ -1306,6 +1352,7 @@ int rpt_gradient(rpt_plan* plan, const double* x, double* g_out, double* f_out) 
     return RPT_EINVAL;
   }
   return guarded([&] {
+    if (int rc = refuse_batched(as_plan(plan), "rpt_gradient")) return rc;
     DeviceScope ds(as_plan(plan)->device);
     return op_gradient(as_plan(plan), x, g_out, f_out);
   });
@@ -1317,6 +1364,7 @@ int rpt_apply_normal(rpt_plan* plan, const double* v, double rho, double* u_out)
     return RPT_EINVAL;
   }
   return guarded([&] {
+    if (int rc = refuse_batched(as_plan(plan), "rpt_apply_normal")) return rc;
     DeviceScope ds(as_plan(plan)->device);
     return op_apply_normal(as_plan(plan), v, rho, u_out);
   });
@@ -1341,6 +1389,7 @@ int rpt_state_get(rpt_plan* plan, double* z, double* x, double* y) {
   }
   return guarded([&] {
     Plan* P = as_plan(plan);
+    if (int rc = refuse_batched(P, "rpt_state_get")) return rc;
     if (!P->state_valid) {
       set_error("the plan holds no ADMM state");
       return RPT_EINVAL;
@@ -1363,6 +1412,7 @@ int rpt_state_set(rpt_plan* plan, const double* z, const double* x, const double
   }
   return guarded([&] {
     Plan* P = as_plan(plan);
+    if (int rc = refuse_batched(P, "rpt_state_set")) return rc;
     const size_t Nn = (size_t)P->dp.N * P->dp.n;
     for (int j = 0; j < P->dp.n; ++j)
       if (!std::isfinite(z[j])) {

@@ -284,7 +284,7 @@ __global__ void __launch_bounds__(64) k_trsm_left(const float* L, float* Y, int 
 
 // Form, factor and invert B_s for every scenario into P->binv (allocating it on
 // first use); also A~_s^T p~ into P->bchol (compute_bconst, solver.cu).
-int chol_prepare(Plan* P, double rho, CholExtra* extra) {
+int chol_prepare(Plan* P, const std::vector<double>& rho, CholExtra* extra) {
   if (!extra && P->chol_ready && !P->chol_con && P->chol_rho == rho) return RPT_OK;
   const DevPlan& dp = P->dp;
   const int n = dp.n, N = dp.N;
@@ -338,7 +338,9 @@ int chol_prepare(Plan* P, double rho, CholExtra* extra) {
     if ((e = cudaLaunchKernel(fn, gb, dim3(256), args, smem, st))) return done(cuda_fail(e, "launch"));
   }
   const dim3 gd((n + 255) / 256, N);
-  k_add_diag<<<gd, 256, 0, st>>>(P->binv, n, (float)(0.5 * rho));
+  for (int g = 0; g < dp.G; ++g)   // each group's scenarios with the group's penalty
+    k_add_diag<<<dim3((n + 255) / 256, dp.Ns), 256, 0, st>>>(P->binv + nn * (size_t)g * dp.Ns, n,
+                                                              (float)(0.5 * rho[g]));
   if (extra && (e = extra->add(P, P->binv))) return done(cuda_fail(e, "constraint terms of B_s"));
   // 2. Cholesky, lower, in place
   const int nblk = (n + kNB - 1) / kNB;

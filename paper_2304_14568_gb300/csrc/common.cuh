@@ -47,6 +47,9 @@ constexpr int kVecThreads = 256;      // threads of a vector CTA (one column eac
 
 struct DevPlan {
   int m, n, N, m_act, n_pad, nblocks;  // nblocks = partial slots
+  int G, Ns;                          // groups (problems of a batched plan) and scenarios per
+                                      // group: scenario u belongs to group u / Ns (G = 1, Ns = N
+                                      // for a plan of one problem)
   int value_format;                   // RPT_F32 / RPT_BF16 / RPT_FP8E4M3
   int index_width;                    // 32 or 16
   int path;                           // 0 register, 1 TMA ring, 2 streaming, 3 bundled ring

@@ -238,7 +238,7 @@ __global__ void k_con_rhs(DevPlan P, const Ctl* __restrict__ C, const double* __
   const int s = blockIdx.y, j = blockIdx.x * kVecThreads + threadIdx.x;
   if (j >= P.n) return;
   const size_t o = (size_t)s * P.n + j;
-  c[(size_t)s * P.n_pad + j] = (float)(bchol[o] + 0.5 * C->rho * z[j] - 0.5 * y[o] + cx[o]);
+  c[(size_t)s * P.n_pad + j] = (float)(bchol[o] + 0.5 * C->g[0].rho * z[j] - 0.5 * y[o] + cx[o]);
 }
 
 // ---- host side ----------------------------------------------------------------
@@ -351,6 +351,7 @@ extern "C" int rpt_admm_bb_solve_constrained(rpt_plan* plan, const rpt_admm_para
     return RPT_EINVAL;
   }
   Plan* P = reinterpret_cast<Plan*>(plan);
+  if (int rc = refuse_batched(P, "rpt_admm_bb_solve_constrained")) return rc;
   const DevPlan& dp = P->dp;
   const int m = dp.m, n = dp.n, N = dp.N, m_act = dp.m_act;
   if (!(sigma >= 0.0) || !std::isfinite(sigma)) {

@@ -9,20 +9,39 @@
 
 namespace rpt {
 
+// Groups of a batched plan.  A batched plan holds G independent problems with
+// the same scenario count Ns; its scenario index u = g * Ns + s runs over
+// (problem g, scenario s) units, each with its own row lists and its own copy
+// of the spot vectors (n spots each, the widest problem's count; a narrower
+// problem's extra spots are fixed at 0 by the box lb = ub = 0 and touched by
+// no row).  Every problem keeps its own consensus z_g, penalty, BB step,
+// residuals and stopping test, and a problem that has converged drops out of
+// the row passes.  A plan from rpt_plan_create is one group (G = 1, Ns = N).
+constexpr int kMaxGroups = 64;
+struct Grp {
+  double rho, inv_rho;                 // penalty of the group's B_s, z-update and r_dual
+  double r_prim, r_dual, eps_prim, eps_dual, step, step_prev, sz2, dz2;
+  double nn;                           // Ns x (the problem's own spot count): the length in eps_abs sqrt(N n)
+  double cst;                          // constant objective term of the group's rows
+  double f;                            // objective of the group's z after the solve
+  long long cg;                        // CG steps of the group's scenarios
+  int k, have_prev, first, status, done, diverged;
+};
+
 // Device-resident solver control block: parameters of the current solve and
 // the scalars of the iteration (written and read by the kernels).
 struct Ctl {
   // ADMM parameters
-  double rho, inv_rho, eps_abs, eps_rel, bb_kappa, cg_theta, cg_eta0, cg_floor, tol_obj, f_goal;
+  double eps_abs, eps_rel, bb_kappa, cg_theta, cg_eta0, cg_floor, tol_obj, f_goal;
   double const_term;
   int max_iter, cg_max, bb_mode, z_mode, use_obj, precond;
-  // ADMM scalars
-  int k, kcg, cg_any, stop, status, have_prev, first, diverged;
+  // ADMM scalars over all groups: loop count, loop condition, every group
+  // converged, some group diverged
+  int k, kcg, cg_any, stop, status, diverged;
   long long cg_total, passes, cg_steps;
-  double r_prim, r_dual, eps_prim, eps_dual, step, step_prev, f_prev, f_cur;
-  double sz2, dz2;
+  double f_prev, f_cur;
   // PGD parameters and scalars
-  double alpha, beta_a, gamma, tol_df, f_target, t, fx, ft, gd;
+  double alpha, beta_a, gamma, tol_df, f_target, t, fx, ft, gd, pstep;
   int pgd_max_iter, max_trials, trial, accepted, failed, pk, pouter, pad2;
   long long trials_total;
   // last-block-done counters (every finisher resets its own counter)
@@ -44,6 +63,10 @@ struct Ctl {
   const double* con_sums; // [4] ||G x - v||^2, ||G x||^2, ||v||^2 over all scenarios
   double con_K;           // constraint rows over all scenarios
   int con_on, pad5;
+  // per-unit activity of the residual pass of a batched plan (0: the unit's
+  // problem has converged), written with the groups' stopping tests
+  int* uact;
+  Grp g[kMaxGroups];      // per group (one per problem of a batched plan)
 };
 
 // trace entry: iteration, seconds since the solve started, r_prim, r_dual,
@@ -95,7 +118,7 @@ struct Plan {
   int trace_count = 0;             // entries of the last traced solve
   bool chol_ready = false;
   bool chol_con = false;          // the cached factor includes dose-constraint terms
-  double chol_rho = 0.0;
+  std::vector<double> chol_rho;   // per group: the penalties the cached factor was formed with
   cudaGraphExec_t admm_chol_exec = nullptr;
   int admm_chol_exec_obj = -1;
 
@@ -116,7 +139,14 @@ struct Plan {
   // and slot (index % 4)
   std::vector<int32_t> rec_of_host;
   std::vector<int32_t> nz_index;
-  std::vector<int32_t> batch_col_off;  // batched plan: problem k owns spots [off[k], off[k+1]); else empty
+  std::vector<int32_t> batch_col_off;  // batched plan: problem k owns spots [off[k], off[k+1]) of the
+                                       // stacked numbering; else empty
+  // per group (one for a plan from rpt_plan_create): default penalty (the rule of
+  // stats.default_rho on the group's own scenarios and spots), constant objective
+  // term, own spot count
+  std::vector<double> grp_rho, grp_const;
+  std::vector<int32_t> grp_n;
+  int *uact = nullptr;            // [N] residual-pass activity per unit (batched plans)
   double lipschitz = 0.0;         // cached 2 lambda_max, 0 = not computed
   bool state_valid = false;
 
@@ -149,8 +179,10 @@ struct ConHook : CholExtra {
   virtual cudaError_t after_z(Plan* P) = 0;
 };
 
+// x_out: n spots (G x n for a batched plan, group-major); group_info: G entries or null
 int admm_solve(Plan* P, const rpt_admm_params* prm, const double* z0, const double* y0,
-               double* x_out, rpt_solve_info* info, ConHook* con = nullptr);
+               double* x_out, rpt_solve_info* info, ConHook* con = nullptr,
+               rpt_solve_info* group_info = nullptr);
 int pgd_solve(Plan* P, const rpt_pgd_params* prm, const double* x0, double* x_out,
               rpt_solve_info* info);
 int op_apply_normal(Plan* P, const double* v, double rho, double* u_out);
@@ -160,7 +192,8 @@ int compute_lipschitz(Plan* P, double* L);
 int profile_row_pass(Plan* P, int mode, int reps, double* ms, double* bytes);
 void destroy_graphs(Plan* P);
 // chol.cu (see CholExtra)
-int chol_prepare(Plan* P, double rho, CholExtra* extra = nullptr);
+// rho: one penalty per group
+int chol_prepare(Plan* P, const std::vector<double>& rho, CholExtra* extra = nullptr);
 
 
 int compute_bconst(Plan* P);             // solver.cu: P->bchol = A~_s^T p~
@@ -168,5 +201,13 @@ int compute_bconst(Plan* P);             // solver.cu: P->bchol = A~_s^T p~
 // error reporting (api.cu)
 void set_error(const std::string& msg);
 int cuda_fail(cudaError_t e, const char* what);
+
+// Calls that take one problem's vectors refuse a batched plan (several groups):
+// RPT_EUNSUPPORTED with the message set, else RPT_OK.
+inline int refuse_batched(const Plan* P, const char* call) {
+  if (P->dp.G <= 1) return RPT_OK;
+  set_error(std::string(call) + ": not available on a batched plan (use rpt_admm_bb_solve_batched)");
+  return RPT_EUNSUPPORTED;
+}
 
 }  // namespace rpt

@@ -17,6 +17,7 @@
 // shared memory).  Dot products and norms are float64; the per-CTA partials of
 // a row pass are summed in a fixed order with compensated float32 sums.
 #include <chrono>
+#include <cstddef>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -141,26 +142,27 @@ __device__ __forceinline__ void set_cond(unsigned long long h, int use, int valu
 
 // grid (nchunk, N).  Initial state: z = P(z0), y = y0, x_s = z, d_prev = 0;
 // with resume: keep (z, x, y), d_prev = x - z.  Stages float32 x for the first
-// residual pass; sets the CG preconditioner for this rho.
+// residual pass; sets the CG preconditioner for this rho.  z0, z, lb, ub hold
+// one n-vector per group (scenario s belongs to group s / Ns).
 __global__ void k_admm_init(DevPlan P, const Ctl* __restrict__ C, const double* __restrict__ z0,
                             const double* __restrict__ y0, int has_z0, int has_y0, int resume,
                             const double* __restrict__ lb, const double* __restrict__ ub,
                             const float* __restrict__ diag, double* dinv, double* x, double* y, double* z,
                             double* dprev, float* v32) {
-  const int s = blockIdx.y, j = blockIdx.x * VT + threadIdx.x;
+  const int s = blockIdx.y, gi = s / P.Ns, j = blockIdx.x * VT + threadIdx.x;
   if (j < P.n) {
-    const size_t o = (size_t)s * P.n + j;
+    const size_t o = (size_t)s * P.n + j, zo = (size_t)gi * P.n + j;
     // Jacobi preconditioner of B_s = A~_s^T A~_s + (rho/2) I, or the identity
-    dinv[o] = C->precond ? 1.0 / ((double)diag[o] + 0.5 * C->rho) : 1.0;
+    dinv[o] = C->precond ? 1.0 / ((double)diag[o] + 0.5 * C->g[gi].rho) : 1.0;
     if (!resume) {
-      const double zj = clampd(has_z0 ? z0[j] : 0.0, lb[j], ub[j]);
+      const double zj = clampd(has_z0 ? z0[zo] : 0.0, lb[zo], ub[zo]);
       x[o] = zj;
       y[o] = has_y0 ? y0[o] : 0.0;
       dprev[o] = 0.0;
-      if (s == 0) z[j] = zj;
+      if (s % P.Ns == 0) z[zo] = zj;
       v32[(size_t)s * P.n_pad + j] = (float)zj;
     } else {
-      dprev[o] = x[o] - z[j];
+      dprev[o] = x[o] - z[zo];
       v32[(size_t)s * P.n_pad + j] = (float)x[o];
     }
   } else if (j < P.n_pad) {
@@ -180,6 +182,7 @@ __global__ void k_admm_init(DevPlan P, const Ctl* __restrict__ C, const double* 
 
 // grid (nchunk, N).  r = -g - (rho/2)(x - z) - y/2 with g from the residual pass
 // (this is c_s - B_s x_s); u = M^{-1} r; per-scenario gamma, ||r||, tolerance, activity.
+// Scenarios of a group that has stopped are left as they are and inactive.
 __global__ void k_cg_init(DevPlan P, Ctl* C, const float* __restrict__ partial,
                           const double* __restrict__ x, const double* __restrict__ y,
                           const double* __restrict__ z, const double* __restrict__ dinv, double* r,
@@ -187,20 +190,22 @@ __global__ void k_cg_init(DevPlan P, Ctl* C, const float* __restrict__ partial,
                           double* r0n, int* act, int* cgi, unsigned int* cnt_s, unsigned long long hcg,
                           int use_cond) {
   __shared__ double sh[2 * 32];
-  const int s = blockIdx.y, j = blockIdx.x * VT + threadIdx.x;
-  const double rho = C->rho;
+  const int s = blockIdx.y, gi = s / P.Ns, j = blockIdx.x * VT + threadIdx.x;
+  const Grp& G = C->g[gi];
+  const bool live = !G.done;
+  const double rho = G.rho;
   double v[2] = {0.0, 0.0};
-  if (j < P.n) {
+  if (live && j < P.n) {
     const size_t o = (size_t)s * P.n + j;
     const double gj = sum_partials(P, partial, s, j);
-    const double ri = -gj - 0.5 * rho * (x[o] - z[j]) - 0.5 * y[o];
+    const double ri = -gj - 0.5 * rho * (x[o] - z[(size_t)gi * P.n + j]) - 0.5 * y[o];
     const double ui = dinv[o] * ri;
     r[o] = ri;
     u[o] = ui;
     v32[(size_t)s * P.n_pad + j] = (float)ui;
     v[0] = ri * ui;
     v[1] = ri * ri;
-  } else if (j < P.n_pad) {
+  } else if (live && j < P.n_pad) {
     v32[(size_t)s * P.n_pad + j] = 0.f;
   }
   block_sum_d<2>(v, sh);
@@ -210,7 +215,10 @@ __global__ void k_cg_init(DevPlan P, Ctl* C, const float* __restrict__ partial,
     d[1] = v[1];
   }
   if (!last_block(&cnt_s[s], gridDim.x)) return;
-  if (threadIdx.x == 0) {
+  if (threadIdx.x == 0 && !live) {
+    cgi[s] = 0;
+    act[s] = 0;
+  } else if (threadIdx.x == 0) {
     double g = 0.0, rr = 0.0;
     for (int c = 0; c < nchunk; ++c) {
       g += __ldcg(&dots[((size_t)s * nchunk + c) * 4]);
@@ -218,15 +226,15 @@ __global__ void k_cg_init(DevPlan P, Ctl* C, const float* __restrict__ partial,
     }
     const double rn = sqrt(rr);
     double t;
-    if (C->first) {
+    if (G.first) {
       r0n[s] = rn;
       t = C->cg_eta0 * rn;
     } else {
       // theta-rule, with the floor capped at the accuracy Eq. 9 needs (a summed
       // subproblem error of eps_prim): a floor above it stalls the iteration
-      const double sN = sqrt((double)P.N);
-      t = fmax(C->cg_theta * 0.5 * rho * fmax(C->r_prim, C->eps_prim) / sN,
-               fmin(C->cg_floor * __ldcg(&r0n[s]), 0.5 * rho * C->eps_prim / sN));
+      const double sN = sqrt((double)P.Ns);
+      t = fmax(C->cg_theta * 0.5 * rho * fmax(G.r_prim, G.eps_prim) / sN,
+               fmin(C->cg_floor * __ldcg(&r0n[s]), 0.5 * rho * G.eps_prim / sN));
     }
     gam[s] = g;
     tol[s] = t;
@@ -258,7 +266,7 @@ __global__ void k_cg_dots(DevPlan P, Ctl* C, const float* __restrict__ partial,
   if (j < P.n) {
     const size_t o = (size_t)s * P.n + j;
     const double uj = u[o];
-    const double wj = sum_partials(P, partial, s, j) + 0.5 * C->rho * uj;
+    const double wj = sum_partials(P, partial, s, j) + 0.5 * C->g[s / P.Ns].rho * uj;
     w[o] = wj;
     v[0] = wj * uj;
   }
@@ -335,6 +343,7 @@ __global__ void k_cg_update(DevPlan P, Ctl* C, double* x, double* r, double* u, 
       for (int k = 0; k < P.N; ++k) {
         if (act[k]) {
           C->cg_total += 1;
+          C->g[k / P.Ns].cg += 1;
           act[k] = __ldcg(&act_next[k]);
           na += act[k];
         }
@@ -348,55 +357,59 @@ __global__ void k_cg_update(DevPlan P, Ctl* C, double* x, double* r, double* u, 
   }
 }
 
-// grid (nchunk).  z_new = P_box(mean_s(x_s + y_s/rho)) [std] or P_box(mean_s x_s) [lit].
+// grid (nchunk, G).  Per group: z_new = P_box(mean_s(x_s + y_s/rho)) [std] or
+// P_box(mean_s x_s) [lit] over the group's scenarios; ||z_new||^2, ||z_new - z||^2.
 __global__ void k_admm_z(DevPlan P, Ctl* C, const double* __restrict__ x, const double* __restrict__ y,
                          const double* __restrict__ z, double* znew, const double* __restrict__ lb,
-                         const double* __restrict__ ub, double* vpart) {
+                         const double* __restrict__ ub, double* vpart, int nchunk) {
   __shared__ double sh[2 * 32];
-  const int j = blockIdx.x * VT + threadIdx.x;
+  const int gi = blockIdx.y, j = blockIdx.x * VT + threadIdx.x;
   double v[2] = {0.0, 0.0};
-  if (j < P.n) {
-    const double ir = C->inv_rho;
+  if (!C->g[gi].done && j < P.n) {
+    const double ir = C->g[gi].inv_rho;
     const bool std_form = (C->z_mode == 0);
+    const size_t zo = (size_t)gi * P.n + j;
     double acc = 0.0;
-    for (int s = 0; s < P.N; ++s) {
+    for (int s = gi * P.Ns; s < (gi + 1) * P.Ns; ++s) {
       const size_t o = (size_t)s * P.n + j;
       acc += std_form ? fma(y[o], ir, x[o]) : x[o];
     }
-    const double zn = clampd(acc / (double)P.N, lb[j], ub[j]);
-    znew[j] = zn;
-    const double dz = zn - z[j];
+    const double zn = clampd(acc / (double)P.Ns, lb[zo], ub[zo]);
+    znew[zo] = zn;
+    const double dz = zn - z[zo];
     v[0] = zn * zn;
     v[1] = dz * dz;
   }
   block_sum_d<2>(v, sh);
   if (threadIdx.x == 0) {
-    vpart[blockIdx.x * 8 + 0] = v[0];
-    vpart[blockIdx.x * 8 + 1] = v[1];
+    vpart[((size_t)gi * nchunk + blockIdx.x) * 8 + 0] = v[0];
+    vpart[((size_t)gi * nchunk + blockIdx.x) * 8 + 1] = v[1];
   }
-  if (!last_block(&C->cnt_z, gridDim.x)) return;
-  double S2[2];
-  last_block_sums<2>(vpart, gridDim.x, 8, 0, S2, sh);
-  if (threadIdx.x == 0) {
-    const double a = S2[0], b = S2[1];
-    C->sz2 = a;
-    C->dz2 = b;
+  if (!last_block(&C->cnt_z, gridDim.x * gridDim.y)) return;
+  for (int g = 0; g < P.G; ++g) {
+    double S2[2];
+    last_block_sums<2>(vpart + (size_t)g * nchunk * 8, nchunk, 8, 0, S2, sh);
+    if (threadIdx.x == 0 && !C->g[g].done) {
+      C->g[g].sz2 = S2[0];
+      C->g[g].dz2 = S2[1];
+    }
   }
 }
 
 // grid (nchunk, N).  d = x - z_new; BB sums dd'd_prev and ||dd||^2; ||d||^2, ||x||^2.
-// Last block: BB step (Eq. 8), r_prim, r_dual, eps_prim (Eq. 9).
+// Last block, per group: BB step (Eq. 8), r_prim, r_dual, eps_prim (Eq. 9).
+// vpart: the first G * nchunk entries belong to k_admm_z, then one per block.
 __global__ void k_admm_d(DevPlan P, Ctl* C, const double* __restrict__ x, const double* __restrict__ z,
                          const double* __restrict__ znew, const double* __restrict__ dprev, double* d,
                          double* vpart, int nchunk) {
   __shared__ double sh[5 * 32];
-  const int s = blockIdx.y, j = blockIdx.x * VT + threadIdx.x;
+  const int s = blockIdx.y, gi = s / P.Ns, j = blockIdx.x * VT + threadIdx.x;
   const int con = C->con_on;
   double v[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-  if (j < P.n) {
-    const size_t o = (size_t)s * P.n + j;
+  if (!C->g[gi].done && j < P.n) {
+    const size_t o = (size_t)s * P.n + j, zo = (size_t)gi * P.n + j;
     const double xj = x[o];
-    const double dj = xj - znew[j];
+    const double dj = xj - znew[zo];
     const double dp = dprev[o];
     const double dd = dj - dp;
     d[o] = dj;
@@ -405,88 +418,97 @@ __global__ void k_admm_d(DevPlan P, Ctl* C, const double* __restrict__ x, const 
     v[2] = dj * dj;
     v[3] = xj * xj;
     if (con) {   // dual residual with the dose blocks: rho (z - z_prev) + sigma G_s'(v_s - v_s_prev)
-      const double rd = C->rho * (znew[j] - z[j]) + C->con_q[o];
+      const double rd = C->g[gi].rho * (znew[zo] - z[zo]) + C->con_q[o];
       v[4] = rd * rd;
     }
   }
   block_sum_d<5>(v, sh);
+  const size_t base = (size_t)P.G * nchunk;
   const int blk = s * nchunk + blockIdx.x;
   if (threadIdx.x == 0) {
-    for (int k = 0; k < 4; ++k) vpart[(size_t)(nchunk + blk) * 8 + k] = v[k];
-    vpart[(size_t)(nchunk + blk) * 8 + 5] = v[4];
+    for (int k = 0; k < 4; ++k) vpart[(base + blk) * 8 + k] = v[k];
+    vpart[(base + blk) * 8 + 5] = v[4];
   }
   if (!last_block(&C->cnt_d, gridDim.x * gridDim.y)) return;
-  double S[4], SC[1];
-  last_block_sums<4>(vpart + (size_t)nchunk * 8, gridDim.x * gridDim.y, 8, 0, S, sh);
-  last_block_sums<1>(vpart + (size_t)nchunk * 8, gridDim.x * gridDim.y, 8, 5, SC, sh);
-  const double rho = C->rho;
-  const bool use_bb = C->bb_mode != 2 && C->have_prev;
-  if (C->bb_scen) {
-    // Eq. 8 on scenario s's own blocks: its partial sums in chunk order, and
-    // dy_s = step_s d_prev_s with step_s the scenario's last dual step
-    for (int s = threadIdx.x; s < P.N; s += blockDim.x) {
-      const double* vp = vpart + (size_t)(nchunk + s * nchunk) * 8;
-      double a = 0.0, b = 0.0;
-      for (int c = 0; c < nchunk; ++c) {
-        a += __ldcg(&vp[(size_t)c * 8 + 0]);
-        b += __ldcg(&vp[(size_t)c * 8 + 1]);
+  const int per_group = P.Ns * nchunk;   // blocks of one group, consecutive
+  for (int g = 0; g < P.G; ++g) {
+    Grp& G = C->g[g];
+    if (G.done) continue;   // the same for every thread of the block
+    double S[4], SC[1];
+    last_block_sums<4>(vpart + (base + (size_t)g * per_group) * 8, per_group, 8, 0, S, sh);
+    last_block_sums<1>(vpart + (base + (size_t)g * per_group) * 8, per_group, 8, 5, SC, sh);
+    const double rho = G.rho;
+    const bool use_bb = C->bb_mode != 2 && G.have_prev;
+    if (C->bb_scen) {
+      // Eq. 8 on scenario s's own blocks: its partial sums in chunk order, and
+      // dy_s = step_s d_prev_s with step_s the scenario's last dual step
+      for (int s = g * P.Ns + threadIdx.x; s < (g + 1) * P.Ns; s += blockDim.x) {
+        const double* vp = vpart + (base + (size_t)s * nchunk) * 8;
+        double a = 0.0, b = 0.0;
+        for (int c = 0; c < nchunk; ++c) {
+          a += __ldcg(&vp[(size_t)c * 8 + 0]);
+          b += __ldcg(&vp[(size_t)c * 8 + 1]);
+        }
+        double st = rho;
+        if (use_bb && b > 0.0) {
+          const double bb = -C->step_s[s] * a / b;
+          if (isfinite(bb) && bb > 0.0) {
+            st = bb;
+            if (C->bb_mode == 1) st = fmin(fmax(st, rho / C->bb_kappa), C->bb_kappa * rho);
+          }
+        }
+        C->step_s[s] = st;
       }
-      double st = rho;
-      if (use_bb && b > 0.0) {
-        const double bb = -C->step_s[s] * a / b;
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+      double step = rho;
+      if (C->bb_scen) {
+        double acc = 0.0;
+        for (int s = g * P.Ns; s < (g + 1) * P.Ns; ++s) acc += C->step_s[s];
+        step = acc / (double)P.Ns;
+      } else if (use_bb && S[1] > 0.0) {
+        const double bb = -G.step_prev * S[0] / S[1];
         if (isfinite(bb) && bb > 0.0) {
-          st = bb;
-          if (C->bb_mode == 1) st = fmin(fmax(st, rho / C->bb_kappa), C->bb_kappa * rho);
+          step = bb;
+          if (C->bb_mode == 1) step = fmin(fmax(step, rho / C->bb_kappa), C->bb_kappa * rho);
         }
       }
-      C->step_s[s] = st;
-    }
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) {
-    double step = rho;
-    if (C->bb_scen) {
-      double acc = 0.0;
-      for (int s = 0; s < P.N; ++s) acc += C->step_s[s];
-      step = acc / (double)P.N;
-    } else if (use_bb && S[1] > 0.0) {
-      const double bb = -C->step_prev * S[0] / S[1];
-      if (isfinite(bb) && bb > 0.0) {
-        step = bb;
-        if (C->bb_mode == 1) step = fmin(fmax(step, rho / C->bb_kappa), C->bb_kappa * rho);
+      const double sN = sqrt((double)P.Ns);
+      G.step = step;
+      if (con) {
+        // Eq. 9 extended to both blocks: r_prim over [x_s - z; G_s x_s - v_s],
+        // eps_prim over [x_s; G_s x_s] and [z (N times); v_s]
+        const double* cs = C->con_sums;
+        G.r_prim = sqrt(S[2] + cs[0]);
+        G.r_dual = sqrt(SC[0]);
+        G.eps_prim = C->eps_abs * sqrt(G.nn + C->con_K) +
+                     C->eps_rel * fmax(sqrt(S[3] + cs[1]), sqrt((double)P.Ns * G.sz2 + cs[2]));
+      } else {
+        G.r_prim = sqrt(S[2]);
+        G.r_dual = sN * rho * sqrt(G.dz2);
+        G.eps_prim = C->eps_abs * sqrt(G.nn) + C->eps_rel * fmax(sqrt(S[3]), sN * sqrt(G.sz2));
       }
     }
-    const double sN = sqrt((double)P.N);
-    C->step = step;
-    if (con) {
-      // Eq. 9 extended to both blocks: r_prim over [x_s - z; G_s x_s - v_s],
-      // eps_prim over [x_s; G_s x_s] and [z (N times); v_s]
-      const double* cs = C->con_sums;
-      C->r_prim = sqrt(S[2] + cs[0]);
-      C->r_dual = sqrt(SC[0]);
-      C->eps_prim = C->eps_abs * sqrt((double)P.N * P.n + C->con_K) +
-                    C->eps_rel * fmax(sqrt(S[3] + cs[1]), sqrt((double)P.N * C->sz2 + cs[2]));
-    } else {
-      C->r_prim = sqrt(S[2]);
-      C->r_dual = sN * rho * sqrt(C->dz2);
-      C->eps_prim = C->eps_abs * sqrt((double)P.N * P.n) +
-                    C->eps_rel * fmax(sqrt(S[3]), sN * sqrt(C->sz2));
-    }
+    __syncthreads();
   }
 }
 
 // grid (nchunk, N).  y += step d (Eq. 7); z <- z_new; d_prev <- d; stage x and z.
-// Last block: eps_dual, stop test, next iteration's condition.
+// Last block, per group: eps_dual and the stop test of Eq. 9; then the activity
+// of every scenario and the next iteration's condition (all groups stopped, or
+// the iteration cap).
 __global__ void k_admm_y(DevPlan P, Ctl* C, const double* __restrict__ x, double* y, double* z,
                          const double* __restrict__ znew, const double* __restrict__ d, double* dprev,
                          float* v32, float* vz32, double* vpart, int nchunk, unsigned long long hadmm,
                          int use_cond) {
   __shared__ double sh[32];
-  const int s = blockIdx.y, j = blockIdx.x * VT + threadIdx.x;
-  const double step = C->bb_scen ? __ldcg(&C->step_s[s]) : __ldcg(&C->step);
+  const int s = blockIdx.y, gi = s / P.Ns, j = blockIdx.x * VT + threadIdx.x;
+  const bool live = !C->g[gi].done;
+  const double step = C->bb_scen ? __ldcg(&C->step_s[s]) : __ldcg(&C->g[gi].step);
   double v[1] = {0.0};
-  if (j < P.n) {
-    const size_t o = (size_t)s * P.n + j;
+  if (live && j < P.n) {
+    const size_t o = (size_t)s * P.n + j, zo = (size_t)gi * P.n + j;
     const double dj = d[o];
     const double yn = fma(step, dj, y[o]);
     y[o] = yn;
@@ -494,24 +516,44 @@ __global__ void k_admm_y(DevPlan P, Ctl* C, const double* __restrict__ x, double
     v32[(size_t)s * P.n_pad + j] = (float)x[o];
     const double ye = C->con_on ? yn + C->con_t[o] : yn;   // with dose blocks: y_s + G_s' mu_s
     v[0] = ye * ye;
-    if (s == 0) {
-      const double zn = znew[j];
-      z[j] = zn;
-      vz32[j] = (float)zn;
+    if (s % P.Ns == 0) {
+      const double zn = znew[zo];
+      z[zo] = zn;
+      if (P.G == 1) vz32[j] = (float)zn;
     }
-  } else if (s == 0 && j < P.n_pad) {
+  } else if (P.G == 1 && s == 0 && j < P.n_pad) {
     vz32[j] = 0.f;
   }
   block_sum_d<1>(v, sh);
+  const size_t base = (size_t)P.G * nchunk;
   const int blk = s * nchunk + blockIdx.x;
-  if (threadIdx.x == 0) vpart[(size_t)(nchunk + blk) * 8 + 4] = v[0];
+  if (threadIdx.x == 0) vpart[(base + blk) * 8 + 4] = v[0];
   if (!last_block(&C->cnt_y, gridDim.x * gridDim.y)) return;
-  double SY[1];
-  last_block_sums<1>(vpart + (size_t)nchunk * 8, gridDim.x * gridDim.y, 8, 4, SY, sh);
+  const int per_group = P.Ns * nchunk;
+  for (int g = 0; g < P.G; ++g) {
+    Grp& G = C->g[g];
+    if (G.done) continue;   // the same for every thread of the block
+    double SY[1];
+    last_block_sums<1>(vpart + (base + (size_t)g * per_group) * 8, per_group, 8, 4, SY, sh);
+    if (threadIdx.x == 0) {
+      const double Y = SY[0];
+      G.eps_dual = C->eps_abs * sqrt(G.nn) + C->eps_rel * sqrt(Y);
+      const int conv = (G.r_prim <= G.eps_prim) && (G.r_dual <= G.eps_dual);
+      G.k += 1;
+      G.have_prev = 1;
+      G.step_prev = G.step;
+      G.first = 0;
+      if (!(isfinite(G.r_prim) && isfinite(G.r_dual) && isfinite(Y))) G.diverged = 1;
+      G.status = conv;
+      // with the objective test (one group only) k_admm_obj decides the stop
+      if (!C->use_obj) G.done = conv || G.diverged || G.k >= C->max_iter;
+    }
+    __syncthreads();
+  }
+  if (P.G > 1 && C->uact)
+    for (int u = threadIdx.x; u < P.N; u += blockDim.x) C->uact[u] = C->g[u / P.Ns].done ? 0 : 1;
   if (threadIdx.x == 0) {
-    const double Y = SY[0];
-    C->eps_dual = C->eps_abs * sqrt((double)P.N * P.n) + C->eps_rel * sqrt(Y);
-    const int conv = (C->r_prim <= C->eps_prim) && (C->r_dual <= C->eps_dual);
+    const Grp& G0 = C->g[0];
     if (C->trace_on && C->k < C->trace_cap) {
       unsigned long long t;
       asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -519,47 +561,68 @@ __global__ void k_admm_y(DevPlan P, Ctl* C, const double* __restrict__ x, double
       double* e = C->trace + (size_t)C->k * kTraceFields;
       e[0] = (double)(C->k + 1);
       e[1] = 1e-9 * (double)(t - C->t_start);
-      e[2] = C->r_prim;
-      e[3] = C->r_dual;
-      e[4] = C->eps_prim;
-      e[5] = C->eps_dual;
-      e[6] = C->step;
+      e[2] = G0.r_prim;
+      e[3] = G0.r_dual;
+      e[4] = G0.eps_prim;
+      e[5] = G0.eps_dual;
+      e[6] = G0.step;
       e[7] = (double)C->cg_total;
     }
     C->k += 1;
-    C->have_prev = 1;
-    C->step_prev = C->step;
-    C->first = 0;
-    if (!(isfinite(C->r_prim) && isfinite(C->r_dual) && isfinite(Y))) C->diverged = 1;
-    C->status = conv;
+    int all_done = 1, all_conv = 1, any_div = 0;
+    for (int g = 0; g < P.G; ++g) {
+      all_done &= C->g[g].done;
+      all_conv &= C->g[g].status;
+      any_div |= C->g[g].diverged;
+    }
+    C->status = all_conv;
+    C->diverged = any_div;
     if (!C->use_obj) {
-      C->stop = conv || C->diverged || C->k >= C->max_iter;
+      C->stop = all_done || C->k >= C->max_iter;
       set_cond(hadmm, use_cond, !C->stop);
     }
   }
 }
 
-// <<<1, 256>>>.  Objective of z (after a kObj row pass): optional relative-change test
-// AND-ed with Eq. 9 (Sec. 2.3), or, with an objective target, f(z) <= target alone.
+// <<<1, 32>>>.  Objective of z (after a kObj row pass; plans of one group only):
+// optional relative-change test AND-ed with Eq. 9 (Sec. 2.3), or, with an
+// objective target, f(z) <= target alone.
 __global__ void k_admm_obj(DevPlan P, Ctl* C, unsigned long long hadmm, int use_cond) {
   if (threadIdx.x == 0) {
+    Grp& G = C->g[0];
     const double f = objective_sum(P) + C->const_term;
     const int conv_obj = fabs(C->f_prev - f) <= C->tol_obj * fmax(fabs(f), 1e-300);
     C->f_prev = f;
     C->f_cur = f;
     C->passes += 1;
-    C->status = C->f_goal > 0.0 ? (f <= C->f_goal) : (C->status && conv_obj);
-    C->stop = C->status || C->diverged || C->k >= C->max_iter;
+    G.status = C->f_goal > 0.0 ? (f <= C->f_goal) : (G.status && conv_obj);
+    G.done = G.status || G.diverged || G.k >= C->max_iter;
+    C->status = G.status;
+    C->stop = G.done || C->k >= C->max_iter;
     set_cond(hadmm, use_cond, !C->stop);
   }
 }
 
-// <<<1, 256>>>.  f = sum of block objectives + constant.
+// <<<1, 32>>>.  f = sum of block objectives + constant; per group the same over
+// the group's scenarios.
 __global__ void k_final_obj(DevPlan P, Ctl* C) {
   if (threadIdx.x == 0) {
     C->f_cur = objective_sum(P) + C->const_term;
+    for (int g = 0; g < P.G; ++g) {
+      double f = C->g[g].cst;
+      for (int s = g * P.Ns; s < (g + 1) * P.Ns; ++s) f += __ldcg(&P.objs[s]);
+      C->g[g].f = f;
+    }
     C->passes += 1;
   }
+}
+
+// grid (nchunk, N).  Stage every scenario's copy of its group's z (the final
+// objective pass of a batched plan, where the groups' z differ).
+__global__ void k_stage_z(DevPlan P, const double* __restrict__ z, float* v32) {
+  const int s = blockIdx.y, j = blockIdx.x * VT + threadIdx.x;
+  if (j < P.n) v32[(size_t)s * P.n_pad + j] = (float)z[(size_t)(s / P.Ns) * P.n + j];
+  else if (j < P.n_pad) v32[(size_t)s * P.n_pad + j] = 0.f;
 }
 
 // ---------------------------------------------------------------------------
@@ -668,7 +731,7 @@ __global__ void k_pgd_finish(DevPlan P, Ctl* C, double* x, const double* __restr
       C->pk += 1;
       C->fx = ft;
       C->f_cur = ft;
-      C->step = C->t;
+      C->pstep = C->t;
       stop = (rel <= C->tol_df) || (C->f_target > 0.0 && ft <= C->f_target) ||
              (C->pk >= C->pgd_max_iter) || !isfinite(ft);
       if (!isfinite(ft)) C->diverged = 1;
@@ -707,10 +770,10 @@ __global__ void k_neg_partials(DevPlan P, const float* __restrict__ partial, dou
 // (grid (nchunk, N)).
 __global__ void k_chol_rhs(DevPlan P, const Ctl* __restrict__ C, const double* __restrict__ bchol,
                            const double* __restrict__ z, const double* __restrict__ y, float* c) {
-  const int s = blockIdx.y, j = blockIdx.x * VT + threadIdx.x;
-  if (j >= P.n) return;
+  const int s = blockIdx.y, gi = s / P.Ns, j = blockIdx.x * VT + threadIdx.x;
+  if (j >= P.n || C->g[gi].done) return;
   const size_t o = (size_t)s * P.n + j;
-  c[(size_t)s * P.n_pad + j] = (float)(bchol[o] + 0.5 * C->rho * z[j] - 0.5 * y[o]);
+  c[(size_t)s * P.n_pad + j] = (float)(bchol[o] + 0.5 * C->g[gi].rho * z[(size_t)gi * P.n + j] - 0.5 * y[o]);
 }
 
 // Cached-factor x-update, part 2 (App. A): x_s = B_s^{-1} c_s.  grid (ceil(n /
@@ -719,9 +782,11 @@ __global__ void k_chol_rhs(DevPlan P, const Ctl* __restrict__ C, const double* _
 // lane, FP64 accumulation of FP32 products.
 constexpr int kCholRows = 64;
 __global__ void __launch_bounds__(256)
-k_chol_x(DevPlan P, const float* __restrict__ binv, const float* __restrict__ c, double* x) {
+k_chol_x(DevPlan P, const Ctl* __restrict__ C, const float* __restrict__ binv, const float* __restrict__ c,
+         double* x) {
   extern __shared__ float cbuf[];
   const int s = blockIdx.y, n = P.n;
+  if (C->g[s / P.Ns].done) return;   // a stopped group keeps its x
   for (int j = threadIdx.x; j < n; j += blockDim.x) cbuf[j] = c[(size_t)s * P.n_pad + j];
   __syncthreads();
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -846,7 +911,8 @@ void rowpass(Exec& e, Plan* P, int mode, const float* v, int v_stride, const int
 void admm_iteration_head(Exec& e, Plan* P, unsigned long long hcg, int uc) {
   const DevPlan& dp = P->dp;
   dim3 g2(P->nchunk, dp.N);
-  rowpass(e, P, kResid, P->v32, dp.n_pad, nullptr);
+  // a batched plan skips the scenarios of problems that have stopped
+  rowpass(e, P, kResid, P->v32, dp.n_pad, dp.G > 1 ? P->uact : nullptr);
   launch(e, k_cg_init, g2, dim3(VT), 0, dp, P->ctl, (const float*)P->partial, (const double*)P->x,
          (const double*)P->y, (const double*)P->z, (const double*)P->dinv, P->r, P->u, P->v32, P->dots,
          P->nchunk, P->gam, P->tol, P->r0n, P->act, P->cgi, P->cnt_s, hcg, uc);
@@ -867,9 +933,9 @@ void cg_body(Exec& e, Plan* P, unsigned long long hcg, int uc) {
 
 void admm_iteration_tail(Exec& e, Plan* P, int use_obj, unsigned long long hadmm, int uc, ConHook* con = nullptr) {
   const DevPlan& dp = P->dp;
-  dim3 g1(P->nchunk), g2(P->nchunk, dp.N);
+  dim3 g1(P->nchunk, dp.G), g2(P->nchunk, dp.N);
   launch(e, k_admm_z, g1, dim3(VT), 0, dp, P->ctl, (const double*)P->x, (const double*)P->y,
-         (const double*)P->z, P->znew, (const double*)P->lb, (const double*)P->ub, P->vpart);
+         (const double*)P->z, P->znew, (const double*)P->lb, (const double*)P->ub, P->vpart, P->nchunk);
   if (con && e.err == cudaSuccess) e.err = con->after_z(P);
   launch(e, k_admm_d, g2, dim3(VT), 0, dp, P->ctl, (const double*)P->x, (const double*)P->z,
          (const double*)P->znew, (const double*)P->dprev, P->d, P->vpart, P->nchunk);
@@ -883,7 +949,12 @@ void admm_iteration_tail(Exec& e, Plan* P, int use_obj, unsigned long long hadmm
 }
 
 void admm_tail_final(Exec& e, Plan* P) {
-  rowpass(e, P, kObj, P->vz32, 0, nullptr);
+  if (P->dp.G > 1) {   // every group's own z
+    launch(e, k_stage_z, dim3(P->nchunk, P->dp.N), dim3(VT), 0, P->dp, (const double*)P->z, P->v32);
+    rowpass(e, P, kObj, P->v32, P->dp.n_pad, nullptr);
+  } else {
+    rowpass(e, P, kObj, P->vz32, 0, nullptr);
+  }
   launch(e, k_final_obj, dim3(1), dim3(32), 0, P->dp, P->ctl);
 }
 
@@ -892,7 +963,7 @@ void chol_iteration_head(Exec& e, Plan* P) {
   launch(e, k_chol_rhs, dim3(P->nchunk, dp.N), dim3(VT), 0, dp, (const Ctl*)P->ctl, (const double*)P->bchol,
          (const double*)P->z, (const double*)P->y, P->v32);
   launch(e, k_chol_x, dim3((dp.n + kCholRows - 1) / kCholRows, dp.N), dim3(256), sizeof(float) * (size_t)dp.n_pad,
-         dp, (const float*)P->binv, (const float*)P->v32, P->x);
+         dp, (const Ctl*)P->ctl, (const float*)P->binv, (const float*)P->v32, P->x);
 }
 
 cudaError_t build_admm_chol_graph(Plan* P, int use_obj) {
@@ -1017,7 +1088,9 @@ int check_err(Plan* P) {
 }
 
 cudaError_t read_ctl(Plan* P) {
-  cudaError_t e = cudaMemcpyAsync(P->ctl_host, P->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, P->stream);
+  // the scalars and the plan's own groups (the rest of the group array is unused)
+  const size_t bytes = offsetof(Ctl, g) + sizeof(Grp) * (size_t)P->dp.G;
+  cudaError_t e = cudaMemcpyAsync(P->ctl_host, P->ctl, bytes, cudaMemcpyDeviceToHost, P->stream);
   if (e != cudaSuccess) return e;
   return cudaStreamSynchronize(P->stream);
 }
@@ -1045,25 +1118,35 @@ struct NvtxRange {            // NVTX range for tools (no cost without one attac
 }  // namespace
 
 int admm_solve_impl(Plan* P, const rpt_admm_params* prm, const double* z0, const double* y0, double* x_out,
-                    rpt_solve_info* info, ConHook* con);
+                    rpt_solve_info* info, ConHook* con, rpt_solve_info* group_info);
 
 int admm_solve(Plan* P, const rpt_admm_params* prm, const double* z0, const double* y0,
-               double* x_out, rpt_solve_info* info, ConHook* con) {
+               double* x_out, rpt_solve_info* info, ConHook* con, rpt_solve_info* group_info) {
   NvtxRange r(con ? "rpt: ADMM-BB with dose constraints (cached factor)"
                   : (prm && prm->subproblem == RPT_SUB_CHOL ? "rpt: ADMM-BB (cached factor)" : "rpt: ADMM-BB (CG)"));
-  return admm_solve_impl(P, prm, z0, y0, x_out, info, con);
+  return admm_solve_impl(P, prm, z0, y0, x_out, info, con, group_info);
 }
 
 // con: dose-constraint blocks; the solve then uses the cached factor (with the
-// constraint terms in B_s) and the host-driven loop.
+// constraint terms in B_s) and the host-driven loop.  A batched plan (G > 1)
+// solves its groups side by side, each with its own penalty, BB step and
+// stopping test; z0, y0, resume, con and the objective tests need G = 1.
 int admm_solve_impl(Plan* P, const rpt_admm_params* prm, const double* z0, const double* y0,
-                    double* x_out, rpt_solve_info* info, ConHook* con) {
+                    double* x_out, rpt_solve_info* info, ConHook* con, rpt_solve_info* group_info) {
   const DevPlan& dp = P->dp;
-  const int n = dp.n, N = dp.N;
-  double rho = prm->rho > 0 ? prm->rho : prm->rho_scale * P->stats.default_rho;
-  if (!(rho > 0) || !std::isfinite(rho)) {
-    set_error("rho must be positive and finite (default rule gave " + std::to_string(rho) + ")");
-    return RPT_EINVAL;
+  const int n = dp.n, N = dp.N, G = dp.G;
+  std::vector<double> rho(G);
+  for (int g = 0; g < G; ++g) {
+    rho[g] = prm->rho > 0 ? prm->rho : prm->rho_scale * P->grp_rho[g];
+    if (!(rho[g] > 0) || !std::isfinite(rho[g])) {
+      set_error("rho must be positive and finite (default rule gave " + std::to_string(rho[g]) +
+                (G > 1 ? " for problem " + std::to_string(g) + ")" : ")"));
+      return RPT_EINVAL;
+    }
+  }
+  if (G > 1 && (z0 || y0 || prm->resume || con || std::isfinite(prm->tol_obj) || prm->f_target > 0.0)) {
+    set_error("a batched plan solves from a cold start without objective tests or dose constraints");
+    return RPT_EUNSUPPORTED;
   }
   if (prm->max_iter < 1 || prm->cg_max < 0 || prm->eps_abs < 0 || prm->eps_rel < 0 ||
       prm->bb_mode < 0 || prm->bb_mode > 2 || prm->z_mode < 0 || prm->z_mode > 1 ||
@@ -1110,8 +1193,16 @@ int admm_solve_impl(Plan* P, const rpt_admm_params* prm, const double* z0, const
     return cuda_fail(e, "copy y0");
   Ctl& c = *P->ctl_host;
   std::memset(&c, 0, sizeof(Ctl));
-  c.rho = rho;
-  c.inv_rho = 1.0 / rho;
+  for (int g = 0; g < G; ++g) {
+    Grp& q = c.g[g];
+    q.rho = rho[g];
+    q.inv_rho = 1.0 / rho[g];
+    q.step = q.step_prev = rho[g];
+    q.first = 1;
+    q.nn = (double)dp.Ns * (double)P->grp_n[g];
+    q.cst = P->grp_const[g];
+  }
+  c.uact = G > 1 ? P->uact : nullptr;
   c.eps_abs = prm->eps_abs;
   c.eps_rel = prm->eps_rel;
   c.bb_kappa = prm->bb_kappa;
@@ -1129,7 +1220,6 @@ int admm_solve_impl(Plan* P, const rpt_admm_params* prm, const double* z0, const
   c.z_mode = prm->z_mode;
   c.precond = prm->cg_precond;
   c.use_obj = use_obj;
-  c.first = 1;
   if (prm->trace) {
     if (!P->trace) {
       if ((e = cudaMalloc(&P->trace, sizeof(double) * kTraceFields * kTraceCap))) return cuda_fail(e, "trace buffer");
@@ -1139,8 +1229,6 @@ int admm_solve_impl(Plan* P, const rpt_admm_params* prm, const double* z0, const
     c.trace_cap = kTraceCap;
     c.trace_on = 1;
   }
-  c.step_prev = rho;
-  c.step = rho;
   c.f_prev = HUGE_VAL;
   if (con) {
     c.con_q = con->q;
@@ -1152,6 +1240,12 @@ int admm_solve_impl(Plan* P, const rpt_admm_params* prm, const double* z0, const
   if ((e = cudaMemcpyAsync(P->ctl, &c, sizeof(Ctl), cudaMemcpyHostToDevice, st)))
     return cuda_fail(e, "upload control block");
   if ((e = cudaMemsetAsync(P->cgcnt, 0, sizeof(int) * N, st))) return cuda_fail(e, "memset");
+  if (G > 1) {   // every scenario active in the first residual pass
+    std::vector<int> ones(N, 1);
+    if ((e = cudaMemcpyAsync(P->uact, ones.data(), sizeof(int) * N, cudaMemcpyHostToDevice, st)) ||
+        (e = cudaStreamSynchronize(st)))
+      return cuda_fail(e, "activity");
+  }
   if ((e = cudaEventRecord(P->ev0, st))) return cuda_fail(e, "event");
   {
     Exec ex;
@@ -1176,7 +1270,8 @@ int admm_solve_impl(Plan* P, const rpt_admm_params* prm, const double* z0, const
       if (con) {
         if ((e = con->rhs(P))) return cuda_fail(e, "dose-constraint right-hand side");
         launch(ex, k_chol_x, dim3((dp.n + kCholRows - 1) / kCholRows, dp.N), dim3(256),
-               sizeof(float) * (size_t)dp.n_pad, dp, (const float*)P->binv, (const float*)P->v32, P->x);
+               sizeof(float) * (size_t)dp.n_pad, dp, (const Ctl*)P->ctl, (const float*)P->binv,
+               (const float*)P->v32, P->x);
       } else {
         chol_iteration_head(ex, P);
       }
@@ -1230,31 +1325,61 @@ int admm_solve_impl(Plan* P, const rpt_admm_params* prm, const double* z0, const
   P->state_valid = true;
   if (int rc = check_err(P)) return rc;
   int status = h.diverged ? RPT_DIVERGED : (h.status ? RPT_OK : RPT_NOT_CONVERGED);
-  if (status != RPT_DIVERGED && x_out) {
-    if ((e = cudaMemcpyAsync(x_out, P->z, sizeof(double) * n, cudaMemcpyDeviceToHost, st)))
+  // a batched plan returns every group's z (a diverged group's as it stands;
+  // its own status says so)
+  if ((status != RPT_DIVERGED || G > 1) && x_out) {
+    if ((e = cudaMemcpyAsync(x_out, P->z, sizeof(double) * n * G, cudaMemcpyDeviceToHost, st)))
       return cuda_fail(e, "copy x_out");
     if ((e = cudaStreamSynchronize(st))) return cuda_fail(e, "sync");
   }
+  // init + per iteration (residual pass, CG init, 3 per CG step, z/d/y, 2 for the
+  // optional objective test) + final objective pass and its reduction (+ staging)
+  const long long kernels = (chol ? 3 + 5LL * h.k : 3 + 5LL * h.k + 3LL * h.cg_steps) +
+                            (use_obj ? 2LL * h.k : 0LL) + (G > 1 ? 1 : 0);
+  auto fill = [&](rpt_solve_info* o, const Grp& q, int st_q) {
+    std::memset(o, 0, sizeof(*o));
+    o->status = st_q;
+    o->iterations = q.k;
+    o->inner = q.cg;
+    o->row_passes = h.passes;
+    o->kernels = kernels;
+    o->setup_seconds = setup_s;
+    o->seconds = ms * 1e-3;
+    o->f = G > 1 ? q.f : h.f_cur;
+    o->r_prim = q.r_prim;
+    o->r_dual = q.r_dual;
+    o->eps_prim = q.eps_prim;
+    o->eps_dual = q.eps_dual;
+    o->step = q.step;
+    o->rho = q.rho;
+  };
   if (info) {
-    std::memset(info, 0, sizeof(*info));
-    info->status = status;
-    info->iterations = h.k;
-    info->inner = h.cg_total;
-    info->row_passes = h.passes;
-    // init + per iteration (residual pass, CG init, 3 per CG step, z/d/y, 2 for the
-    // optional objective test) + final objective pass and its reduction
-    info->kernels = chol ? 3 + 5LL * h.k + (use_obj ? 2LL * h.k : 0LL)
-                         : 3 + 5LL * h.k + 3LL * h.cg_steps + (use_obj ? 2LL * h.k : 0LL);
-    info->setup_seconds = setup_s;
-    info->seconds = ms * 1e-3;
-    info->f = h.f_cur;
-    info->r_prim = h.r_prim;
-    info->r_dual = h.r_dual;
-    info->eps_prim = h.eps_prim;
-    info->eps_dual = h.eps_dual;
-    info->step = h.step;
-    info->rho = rho;
+    fill(info, h.g[0], status);
+    if (G > 1) {
+      // over all groups: the loop count, the CG steps, the total objective, and the
+      // residual norms of the stacked vectors; step and rho are per group only
+      double rp = 0, rd = 0, ep = 0, ed = 0;
+      for (int g = 0; g < G; ++g) {
+        rp += h.g[g].r_prim * h.g[g].r_prim;
+        rd += h.g[g].r_dual * h.g[g].r_dual;
+        ep += h.g[g].eps_prim * h.g[g].eps_prim;
+        ed += h.g[g].eps_dual * h.g[g].eps_dual;
+      }
+      info->iterations = h.k;
+      info->inner = h.cg_total;
+      info->f = h.f_cur;
+      info->r_prim = std::sqrt(rp);
+      info->r_dual = std::sqrt(rd);
+      info->eps_prim = std::sqrt(ep);
+      info->eps_dual = std::sqrt(ed);
+      info->step = 0.0;
+      info->rho = 0.0;
+    }
   }
+  if (group_info)
+    for (int g = 0; g < G; ++g)
+      fill(&group_info[g], h.g[g],
+           h.g[g].diverged ? RPT_DIVERGED : (h.g[g].status ? RPT_OK : RPT_NOT_CONVERGED));
   P->trace_count = prm->trace ? std::min(h.k, kTraceCap) : 0;
   if (status == RPT_DIVERGED) set_error("ADMM residuals became non-finite");
   return status;
@@ -1352,7 +1477,7 @@ int pgd_solve(Plan* P, const rpt_pgd_params* prm, const double* x0, double* x_ou
     info->kernels = 1 + 3LL * h.pouter + 3LL * h.trials_total;
     info->seconds = ms * 1e-3;
     info->f = h.f_cur;
-    info->step = h.step;
+    info->step = h.pstep;
     info->rho = L > 0 ? L : P->lipschitz;
   }
   if (status == RPT_DIVERGED) set_error("PGD objective became non-finite");

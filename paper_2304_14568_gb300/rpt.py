@@ -202,7 +202,7 @@ def lib():
     L.rpt_plan_batch_query.argtypes = [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
     L.rpt_plan_batch_query.restype = C.c_int
     L.rpt_admm_bb_solve_batched.argtypes = [C.c_void_p, C.POINTER(AdmmParams), C.POINTER(C.POINTER(C.c_double)),
-                                            C.POINTER(_Info)]
+                                            C.POINTER(_Info), C.POINTER(_Info)]
     L.rpt_admm_bb_solve_batched.restype = C.c_int
     _lib = L
     return L
@@ -313,7 +313,7 @@ class Plan:
 
     @classmethod
     def batched(cls, problems, value_format=F32, index_width=32, **device_opts):
-        """One plan holding several problems side by side (rpt_plans_create_batched)."""
+        """One plan holding several problems, solved side by side (rpt_plans_create_batched)."""
         L = lib()
         built = [_problem_struct(*_problem_fields(p), value_format=value_format, index_width=index_width)
                  for p in problems]
@@ -342,15 +342,18 @@ class Plan:
         return off
 
     def admm_bb_solve_batched(self, params: AdmmParams | None = None, **kw):
-        """ADMM-BB on the whole plan; returns ([x_k per problem], info)."""
+        """ADMM-BB on every problem of the plan, each with its own penalty, BB
+        step and stop; returns ([x_k per problem], info of the whole solve,
+        [info per problem])."""
         prm = params if params is not None else admm_params(**kw)
         off = self.batch_offsets()
         xs = [np.empty(int(off[k + 1] - off[k])) for k in range(len(off) - 1)]
         ptrs = (C.POINTER(C.c_double) * len(xs))(*[_dptr(x) for x in xs])
         info = _Info()
-        rc = lib().rpt_admm_bb_solve_batched(self._h, C.byref(prm), ptrs, C.byref(info))
-        _check(rc, allow=(OK, NOT_CONVERGED))
-        return xs, info.as_dict()
+        per = (_Info * len(xs))()
+        rc = lib().rpt_admm_bb_solve_batched(self._h, C.byref(prm), ptrs, C.byref(info), per)
+        _check(rc, allow=(OK, NOT_CONVERGED, DIVERGED))
+        return xs, info.as_dict(), [p.as_dict() for p in per]
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:

@@ -226,7 +226,10 @@ def test_graph_and_host_loop_agree(rpt):
     assert i1["status"] == 0 and i0["status"] == 0 and i2["status"] == 0
     assert abs(i1["iterations"] - i0["iterations"]) <= 0.2 * i0["iterations"] + 2
     assert abs(W.f(z1) - W.f(z0)) <= 1e-6 * W.f(z0)
-    assert i2["iterations"] % 5 == 0
+    # reading the flag every 5 iterations launches up to 4 more, which do nothing
+    # once the solve has stopped: the count and result are the stopping iteration's
+    assert abs(i2["iterations"] - i0["iterations"]) <= 0.2 * i0["iterations"] + 2
+    assert abs(W.f(z2) - W.f(z0)) <= 1e-6 * W.f(z0)
 
 
 def test_status_and_resume(rpt):
