@@ -468,6 +468,10 @@ def main():
     ap.add_argument("--no-forms", action="store_true", help="skip the reduced-precision storage forms")
     ap.add_argument("--no-chol", action="store_true", help="skip the cached-factor subproblem solver")
     ap.add_argument("--no-variants", action="store_true", help="skip the per-scenario BB step variant")
+    ap.add_argument("--ring", default=None,
+                    help="entries,rows,stages of the row-pass ring (default: the autotuner's choice)")
+    ap.add_argument("--ring-threads", type=int, default=0,
+                    help="threads of a bundled row-pass CTA: 1024, 768 or 640 (default: the autotuner's choice)")
     ap.add_argument("--no-exact", action="store_true", help="skip the exact-sum (bitwise reproducible) variant")
     ap.add_argument("--no-tto", action="store_true", help="skip the times to the objective target (1 + 1e-4) f*")
     ap.add_argument("--dvh", action="store_true",
@@ -510,7 +514,12 @@ def main():
     prob = _workload(args.seed, args.workers)
     t_gen = time.perf_counter() - t_gen
     stream = torch.cuda.Stream(device=dev)
-    plan = rpt.Plan.from_problem(prob, device=dev, stream=stream.cuda_stream, row_path=args.row_path, autotune=1)
+    ring_kw = dict(autotune=1)
+    if args.ring:
+        e_, r_, s_ = (int(v) for v in args.ring.split(","))
+        ring_kw = dict(chunk_entries=e_, chunk_rows=r_, stages=s_)
+    plan = rpt.Plan.from_problem(prob, device=dev, stream=stream.cuda_stream, row_path=args.row_path,
+                                 ring_threads=args.ring_threads, **ring_kw)
     st = plan.stats()
     params = rpt.admm_params()          # eps_abs = eps_rel = 1e-4, defaults of the library
     if args.max_iter > 0:
@@ -557,7 +566,8 @@ def main():
     # DRAM bytes of one launch from a stored ncu capture of this kernel on this
     # workload (dram__bytes_read.sum + dram__bytes_write.sum), keyed by the kernel
     # variant; null when no capture of the variant in use is stored
-    variant = ("bundled-" + ("exact" if st["exact_sums"] else "float") if st["row_path"] == 4
+    variant = ("bundled-" + ("exact" if st["exact_sums"] else "float") +
+               ("" if st["ring_threads"] in (0, 1024) else f"-{st['ring_threads']}t") if st["row_path"] == 4
                else {1: "register", 2: "ring", 3: "stream"}[st["row_path"]])
     traffic, traffic_src = None, None
     tr_path = os.path.join(ROOT, "profiles", "traffic.json")
@@ -580,7 +590,8 @@ def main():
                    "rho": infos[-1]["rho"], "l2": "inputs 1.02 GB > 129 MB L2, no flush",
                    "parallelism": "replicas" if world > 1 else "single GPU", "seed": args.seed,
                    "ring": {"chunk_entries": st["chunk_entries"], "chunk_rows": st["chunk_rows"],
-                            "stages": st["stages"], "configs_timed": st["autotuned"]}},
+                            "stages": st["stages"], "threads": st["ring_threads"],
+                            "configs_timed": st["autotuned"]}},
         "admm": {"f_rel_gap_vs_exact": (None if _golden_fstar() is None or args.seed != 0
                                         else (infos[-1]["f"] - _golden_fstar()) / _golden_fstar()),
                  "iterations": iters, "cg_iterations": statistics.mean(i["inner"] for i in infos),
@@ -654,7 +665,9 @@ def main():
             fe1.record(stream)
             torch.cuda.synchronize(dev)
             f_on_f32 = plan.objective(zf)
-            forms[name] = {"ms_per_pass": ms_f, "bytes_per_pass": by_f, "gbs": by_f / ms_f / 1e6,
+            sf = pf.stats()
+            forms[name] = {"ring": [sf["chunk_entries"], sf["stages"], sf["ring_threads"]],
+                           "ms_per_pass": ms_f, "bytes_per_pass": by_f, "gbs": by_f / ms_f / 1e6,
                            "frac_of_peak": by_f / ms_f / 1e6 / peak,
                            "solve_s": fe0.elapsed_time(fe1) / 1e3, "iterations": fi["iterations"],
                            "row_passes": fi["row_passes"],

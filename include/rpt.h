@@ -114,6 +114,11 @@ typedef struct {
                                        rounding noise can stall them; about 25 % slower per pass;
                                        2 = float32 shared-memory atomics, whose results vary in the last bits
                                        from run to run */
+  int32_t ring_threads;             /* row path 4: threads of a row-pass CTA, 1024 (31 consumer warps, 6 block
+                                       columns per lane held in registers), 768 (23 warps, 8) or 640 (19 warps,
+                                       10); fewer warps hide less latency, more registers re-read fewer block
+                                       columns of wide bundles.  0 = library choice (1024, or the autotuner's
+                                       pick among the three) */
 } rpt_device_opts;
 
 /* ADMM-BB parameters (Sec. 2.2).  Fill with rpt_admm_params_default(). */
@@ -206,9 +211,9 @@ typedef struct {
   int64_t block_cols;     /* path 4: stored block columns (4 values and one index each) */
   double  bundle_fill;    /* path 4: stored entries / (4 block_cols): the share of stored values that
                              are entries of the matrix */
-  int32_t exact_sums;     /* 1: the row passes sum in exact fixed point (path 4 with accumulate 0/1), so
+  int32_t exact_sums;     /* 1: the row passes sum in exact fixed point (path 4 with accumulate 1), so
                              their results do not depend on scheduling; 0: float atomics */
-  int32_t reserved;
+  int32_t ring_threads;   /* path 4: threads of a row-pass CTA (1024, 768 or 640); 0 otherwise */
 } rpt_plan_stats;
 
 /* ---- defaults ----------------------------------------------------------- */

@@ -182,6 +182,7 @@ using namespace layout;   // lanes per row, row lists, bank balance, chunks (lay
 // One bulk-copy ring configuration and its chunk lists.
 struct RingCfg {
   int cmax = 0, rmax = 0, stages = 0;
+  int thr = kTmaThreads;             // bundled path: threads of a row-pass CTA
   std::vector<ChunkDesc> chunks;
   std::vector<int> scen_chunk;
 };
@@ -392,9 +393,11 @@ int create_plan(const rpt_problem* pr, const rpt_device_opts* opts, rpt_plan** o
   // row path: the caller's choice, else the bundled ring when its stage fits the
   // plan, else the bulk-copy ring when it fits, else the register path
   const int want_path = opts ? opts->row_path : 0;
-  if (want_path < 0 || want_path > 4 || (opts && (opts->accumulate < 0 || opts->accumulate > 2))) {
+  const int want_thr = opts ? opts->ring_threads : 0;
+  if (want_path < 0 || want_path > 4 || (opts && (opts->accumulate < 0 || opts->accumulate > 2)) ||
+      (want_thr != 0 && want_thr != 1024 && want_thr != 768 && want_thr != 640)) {
     free_plan(P);
-    set_error("row_path must be 0..4 and accumulate 0..2");
+    set_error("row_path must be 0..4, accumulate 0..2 and ring_threads 0, 640, 768 or 1024");
     return RPT_EINVAL;
   }
   const bool exact = opts && opts->accumulate == 1;      // bundled path: fixed-point sums on request
@@ -451,8 +454,13 @@ int create_plan(const rpt_problem* pr, const rpt_device_opts* opts, rpt_plan** o
   if (want_path == 4 || want_path == 0) {
     std::vector<int3> cands = ring_override(opts, 3072, 192, 2);
     if (cands.empty())
-      cands = {make_int3(3072, 192, 2), make_int3(2048, 128, 3), make_int3(4096, 256, 2), make_int3(2048, 128, 2),
-               make_int3(1536, 96, 3), make_int3(1024, 64, 3), make_int3(1024, 64, 2), make_int3(512, 32, 2)};
+      // wide stages first: fewer, longer phases of the ring measured fastest (a
+      // stage holds at most 128 bundle records, enough for 4096 block columns of
+      // the average bundle); the list goes down to stages that fit wide plans
+      cands = {make_int3(4096, 128, 2), make_int3(2560, 128, 3), make_int3(3072, 192, 2), make_int3(2048, 128, 3),
+               make_int3(4096, 256, 2), make_int3(2048, 128, 2), make_int3(1536, 96, 3), make_int3(1024, 64, 3),
+               make_int3(1024, 64, 2), make_int3(512, 32, 2),
+               make_int3(6144, 384, 2), make_int3(4096, 256, 3)};   // these two fit narrow formats
     std::vector<int3> fit;
     for (const int3& c : cands)
       if (tma_smem_bytes(n_pad, c.x, c.y, c.z, bv, bi, true, true, exact) + 1024 <= (size_t)smem_optin)
@@ -508,16 +516,31 @@ int create_plan(const rpt_problem* pr, const rpt_device_opts* opts, rpt_plan** o
       for (int s = 0; s < N; ++s)
         for (int q = 0; q <= B[s].nb; ++q) RB.rec[RB.rec_base[s] + q] = B[s].rec[(size_t)4 * q];
       if (!too_many && recs < (int64_t)INT32_MAX) {
+        // CTA sizes: the caller's, else 1024 threads, or all three when autotuning.
+        // A bundle's lanes are chosen as for 1024 threads whatever the size (the
+        // larger register budgets of the smaller CTAs only shorten the tail), so
+        // that a lane's dot product runs in the same order on every CTA size and
+        // exact-sum passes give the same bits on all of them
+        std::vector<int> thr_list;
+        if (want_thr) thr_list = {want_thr};
+        else if (autotune) thr_list = {1024, 768, 640};
+        else thr_list = {1024};
+        auto keep_for = [](int) { return kBunKeep; };
+        bool found = false;
         for (const int3& c : fit) {
-          RingCfg rc;
-          rc.cmax = c.x;
-          rc.rmax = c.y;
-          rc.stages = c.z;
-          if (!build_chunks(RB, ebase, N, rc.cmax, rc.rmax, false, kBunMinLanes, &rc.chunks, &rc.scen_chunk,
-                            kBunKeep))
-            continue;
-          ring_cfgs.push_back(std::move(rc));
-          if (!autotune) break;
+          for (int t : thr_list) {
+            RingCfg rc;
+            rc.cmax = c.x;
+            rc.rmax = c.y;
+            rc.stages = c.z;
+            rc.thr = t;
+            if (!build_chunks(RB, ebase, N, rc.cmax, rc.rmax, false, kBunMinLanes, &rc.chunks, &rc.scen_chunk,
+                              keep_for(t)))
+              continue;
+            ring_cfgs.push_back(std::move(rc));
+            found = true;
+          }
+          if (found && !autotune) break;
         }
       }
       if (!ring_cfgs.empty()) {
@@ -538,6 +561,7 @@ int create_plan(const rpt_problem* pr, const rpt_device_opts* opts, rpt_plan** o
         }
         R = std::move(RB);
         ctas = 1;
+        dp.ring_threads = ring_cfgs[0].thr;
         dp.cmax = ring_cfgs[0].cmax;
         dp.rmax = ring_cfgs[0].rmax;
         dp.stages = ring_cfgs[0].stages;
@@ -994,6 +1018,7 @@ int create_plan(const rpt_problem* pr, const rpt_device_opts* opts, rpt_plan** o
   S.block_cols = bundled ? NE : 0;
   S.bundle_fill = (bundled && NE > 0) ? (double)NNZ / (double)(kBunRows * NE) : 0.0;
   S.exact_sums = dp.acc64;
+  S.ring_threads = bundled ? dp.ring_threads : 0;
   S.value_format = pr->value_format;
   S.index_width = pr->index_width;
   S.row_blocks = dp.nblocks;
@@ -1019,6 +1044,7 @@ int create_plan(const rpt_problem* pr, const rpt_device_opts* opts, rpt_plan** o
       P->dp.cmax = rc.cmax;
       P->dp.rmax = rc.rmax;
       P->dp.stages = rc.stages;
+      if (bundled) P->dp.ring_threads = rc.thr;
       if (ee == cudaSuccess) ee = rowpass_prepare(P->dp);
       return ee;
     };
@@ -1030,18 +1056,22 @@ int create_plan(const rpt_problem* pr, const rpt_device_opts* opts, rpt_plan** o
         return cuda_fail(e, "autotune");
       }
     }
-    for (size_t c = 0; c < ring_cfgs.size(); ++c) {
-      if ((e = apply(ring_cfgs[c]))) {
-        free_plan(P);
-        return cuda_fail(e, "autotune");
+    // two rounds over the configurations, 10 launches each, keeping each one's
+    // best: one short timing per configuration let clock and queue noise pick
+    // a slower ring
+    for (int round = 0; round < 2; ++round)
+      for (size_t c = 0; c < ring_cfgs.size(); ++c) {
+        if ((e = apply(ring_cfgs[c]))) {
+          free_plan(P);
+          return cuda_fail(e, "autotune");
+        }
+        double t = 0.0, by = 0.0;
+        if (int rc = profile_row_pass(P, kNormal, 10, &t, &by)) {
+          free_plan(P);
+          return rc;
+        }
+        ms[c] = std::min(ms[c], t);
       }
-      double t = 0.0, by = 0.0;
-      if (int rc = profile_row_pass(P, kNormal, 3, &t, &by)) {
-        free_plan(P);
-        return rc;
-      }
-      ms[c] = t;
-    }
     const size_t best = (size_t)(std::min_element(ms.begin(), ms.end()) - ms.begin());
     if ((e = apply(ring_cfgs[best]))) {
       free_plan(P);
@@ -1050,6 +1080,7 @@ int create_plan(const rpt_problem* pr, const rpt_device_opts* opts, rpt_plan** o
     S.chunk_entries = ring_cfgs[best].cmax;
     S.chunk_rows = ring_cfgs[best].rmax;
     S.stages = ring_cfgs[best].stages;
+    S.ring_threads = bundled ? ring_cfgs[best].thr : 0;
     S.autotuned = (int32_t)ring_cfgs.size();
     S.autotune_ms = ms[best];
   }

@@ -55,6 +55,7 @@ struct DevPlan {
   int path;                           // 0 register, 1 TMA ring, 2 streaming, 3 bundled ring
   int grid;                           // CTAs of one row pass
   int cmax, rmax, stages;             // TMA path: entries / rows per stage, ring depth
+  int ring_threads;                   // path 3: threads of a row-pass CTA (1024, 768, 640)
   int slot_cap;                       // capacity of each scenario's slot list
   const int64_t* nnz_base;            // [N]
   const int32_t* col32;               // [NNZ] (index_width 32)

@@ -293,13 +293,18 @@ constexpr int kBatch = 4;   // chunks per queue pull
 // row bundles (path 3), records of 4 int4 per bundle, 4 values per block column,
 // 64-bit fixed-point accumulator (see process_bundle); the staged vector's
 // maximum magnitude sets the scale of each scenario.
-template <int MODE, typename VT, typename IT, bool BUN, bool FIX>
-__global__ void __launch_bounds__(kTmaThreads, 1)
+// NT threads per CTA (one producer warp, NT / 32 - 1 consumer warps); the
+// bundled path trades warps for registers: 1024 threads keep 6 block columns
+// per lane in registers, 768 keep 8 and 640 keep 10 (so fewer block columns of
+// wide bundles are read twice).
+template <int MODE, typename VT, typename IT, bool BUN, bool FIX, int NT = kTmaThreads>
+__global__ void __launch_bounds__(NT, 1)
 k_rowpass_tma(DevPlan P, const float* __restrict__ vin, int v_stride, const int* __restrict__ active,
               float* __restrict__ partial, double* __restrict__ objp, float* __restrict__ dose) {
   constexpr bool kScatter = (MODE == kNormal || MODE == kResid);
-  constexpr int NCW = kTmaThreads / 32 - 1;     // consumer warps (wobj below holds up to 64)
-  constexpr int KR = BUN ? kBundleKeep : 8;     // entries (block columns) per lane kept in registers
+  constexpr int NCW = NT / 32 - 1;              // consumer warps (wobj below holds up to 64)
+  constexpr int KR = BUN ? (NT >= 1024 ? kBundleKeep : (NT >= 768 ? 8 : 10)) : 8;   // block columns (entries)
+                                                // per lane kept in registers
   constexpr int RPU = BUN ? 4 : 1;              // int4 records per row (bundle)
   constexpr int VPE = BUN ? 4 : 1;              // values per stored entry (block column)
   constexpr bool FX = BUN && FIX;                // 64-bit fixed-point accumulator
@@ -566,25 +571,32 @@ k_rowpass(DevPlan P, const float* __restrict__ vin, int v_stride, const int* __r
 
 constexpr int kKR = 8;
 
-template <int MODE, bool BUN, bool FIX>
+template <int MODE, bool BUN, bool FIX, int NT = kTmaThreads>
 void* pick_ring(const DevPlan& P) {
   if (P.index_width == 16) {
     switch (P.value_format) {
-      case 1: return (void*)k_rowpass_tma<MODE, __nv_bfloat16, uint16_t, BUN, FIX>;
-      case 2: return (void*)k_rowpass_tma<MODE, __nv_fp8_e4m3, uint16_t, BUN, FIX>;
-      default: return (void*)k_rowpass_tma<MODE, float, uint16_t, BUN, FIX>;
+      case 1: return (void*)k_rowpass_tma<MODE, __nv_bfloat16, uint16_t, BUN, FIX, NT>;
+      case 2: return (void*)k_rowpass_tma<MODE, __nv_fp8_e4m3, uint16_t, BUN, FIX, NT>;
+      default: return (void*)k_rowpass_tma<MODE, float, uint16_t, BUN, FIX, NT>;
     }
   }
   switch (P.value_format) {
-    case 1: return (void*)k_rowpass_tma<MODE, __nv_bfloat16, int32_t, BUN, FIX>;
-    case 2: return (void*)k_rowpass_tma<MODE, __nv_fp8_e4m3, int32_t, BUN, FIX>;
-    default: return (void*)k_rowpass_tma<MODE, float, int32_t, BUN, FIX>;
+    case 1: return (void*)k_rowpass_tma<MODE, __nv_bfloat16, int32_t, BUN, FIX, NT>;
+    case 2: return (void*)k_rowpass_tma<MODE, __nv_fp8_e4m3, int32_t, BUN, FIX, NT>;
+    default: return (void*)k_rowpass_tma<MODE, float, int32_t, BUN, FIX, NT>;
   }
+}
+
+template <int MODE, bool FIX>
+void* pick_bundled(const DevPlan& P) {
+  if (P.ring_threads == 768) return pick_ring<MODE, true, FIX, 768>(P);
+  if (P.ring_threads == 640) return pick_ring<MODE, true, FIX, 640>(P);
+  return pick_ring<MODE, true, FIX, kTmaThreads>(P);
 }
 
 template <int MODE>
 void* pick(const DevPlan& P) {
-  if (P.path == 3) return P.acc64 ? pick_ring<MODE, true, true>(P) : pick_ring<MODE, true, false>(P);
+  if (P.path == 3) return P.acc64 ? pick_bundled<MODE, true>(P) : pick_bundled<MODE, false>(P);
   if (P.path == 2) return stream_rowpass_kernel(P, MODE);
   if (P.path == 1) return pick_ring<MODE, false, false>(P);
   if (P.index_width == 16) {
@@ -833,7 +845,8 @@ size_t rowpass_smem(const DevPlan& P, int mode) {
 }
 
 int rowpass_threads(const DevPlan& P) {
-  return (P.path == 1 || P.path == 3) ? kTmaThreads : (P.path == 2 ? kStrThreads : kRowThreads);
+  if (P.path == 3) return (P.ring_threads == 768 || P.ring_threads == 640) ? P.ring_threads : kTmaThreads;
+  return P.path == 1 ? kTmaThreads : (P.path == 2 ? kStrThreads : kRowThreads);
 }
 
 // The dynamic shared-memory cap is a per-function, process-wide attribute, so

@@ -64,13 +64,14 @@ class _DeviceOpts(C.Structure):
     _fields_ = [("device", C.c_int32), ("stream", C.c_void_p), ("ctas_per_sm", C.c_int32),
                 ("row_path", C.c_int32), ("autotune", C.c_int32), ("chunk_entries", C.c_int32),
                 ("chunk_rows", C.c_int32), ("stages", C.c_int32), ("min_lanes", C.c_int32),
-                ("inject_timeout", C.c_int32), ("device_mem_cap", C.c_int64), ("accumulate", C.c_int32)]
+                ("inject_timeout", C.c_int32), ("device_mem_cap", C.c_int64), ("accumulate", C.c_int32),
+                ("ring_threads", C.c_int32)]
 
 
 def _device_opts(device=0, stream=None, ctas_per_sm=0, row_path=0, autotune=0, chunk_entries=0, chunk_rows=0,
-                 stages=0, min_lanes=0, inject_timeout=0, device_mem_cap=0, accumulate=0):
+                 stages=0, min_lanes=0, inject_timeout=0, device_mem_cap=0, accumulate=0, ring_threads=0):
     return _DeviceOpts(device, stream, ctas_per_sm, row_path, autotune, chunk_entries, chunk_rows, stages,
-                       min_lanes, inject_timeout, device_mem_cap, accumulate)
+                       min_lanes, inject_timeout, device_mem_cap, accumulate, ring_threads)
 
 
 class AdmmParams(C.Structure):
@@ -108,7 +109,7 @@ class _Stats(C.Structure):
                 ("row_path", C.c_int32), ("min_lanes", C.c_int32), ("chunk_entries", C.c_int32),
                 ("chunk_rows", C.c_int32), ("stages", C.c_int32), ("autotuned", C.c_int32),
                 ("autotune_ms", C.c_double), ("bundles", C.c_int64), ("block_cols", C.c_int64),
-                ("bundle_fill", C.c_double), ("exact_sums", C.c_int32), ("reserved", C.c_int32)]
+                ("bundle_fill", C.c_double), ("exact_sums", C.c_int32), ("ring_threads", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

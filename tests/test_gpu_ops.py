@@ -34,7 +34,8 @@ def rpt():
 # switches), the streaming path, the streaming path with tiny chunks (many
 # chunk hand-overs, class changes inside a warp's run, one-row chunks), the
 # bundled ring and the bundled ring with tiny stages, each with float atomics
-# and with exact fixed-point sums
+# and with exact fixed-point sums, and the bundled ring's smaller CTAs (768 and
+# 640 threads, 8 and 10 block columns per lane in registers)
 PATHS = {
     "reg": dict(row_path=1),
     "tma": dict(row_path=2),
@@ -45,6 +46,9 @@ PATHS = {
     "bun_small": dict(row_path=4, chunk_entries=1280, chunk_rows=3, stages=2),
     "bun_exact": dict(row_path=4, accumulate=1),
     "bun_exact_small": dict(row_path=4, accumulate=1, chunk_entries=1280, chunk_rows=3, stages=2),
+    "bun_768": dict(row_path=4, ring_threads=768),
+    "bun_640_small": dict(row_path=4, ring_threads=640, chunk_entries=1280, chunk_rows=3, stages=2),
+    "bun_640_exact": dict(row_path=4, ring_threads=640, accumulate=1),
 }
 
 
@@ -169,6 +173,9 @@ def test_row_path_selection(rpt):
         U = P.apply_normal(np.ones((prob.N, prob.n)), 1.0)
     W = Weighted(prob)
     np.testing.assert_allclose(U[0], W.normal_apply(0, np.ones(prob.n), 1.0), rtol=1e-4)
+    with pytest.raises(rpt.RptError) as e:                # CTA sizes of the bundled ring: 640, 768, 1024
+        plan_of(rpt, prob, ring_threads=512)
+    assert e.value.status == rpt.EINVAL
 
 
 def test_stream_path_takes_rows_longer_than_a_chunk(rpt):
@@ -186,17 +193,24 @@ def test_stream_path_takes_rows_longer_than_a_chunk(rpt):
 def test_bundled_pass_is_bitwise_reproducible(rpt):
     """The bundled ring with exact sums (accumulate = 1) adds 64-bit fixed-point
     contributions, which is exact: repeated passes give identical bits whatever
-    order the atomics and the chunk queues take, on every value format."""
+    order the atomics and the chunk queues take, on every value format, and the
+    same bits on every CTA size (a lane's dot product runs in the same order)."""
     prob = random_problem(**CASES["ragged"])
     V = np.random.default_rng(21).normal(size=(prob.N, prob.n))
     x = np.random.default_rng(22).uniform(0.0, 3.0, size=prob.n)
-    for vf in (rpt.F32, rpt.BF16, rpt.FP8E4M3):
-        with plan_of(rpt, prob, row_path=4, value_format=vf, accumulate=1) as P:
+    by_thr = {}
+    for vf, thr in ((rpt.F32, 0), (rpt.BF16, 0), (rpt.FP8E4M3, 0), (rpt.F32, 768), (rpt.F32, 640)):
+        with plan_of(rpt, prob, row_path=4, value_format=vf, accumulate=1, ring_threads=thr) as P:
             assert P.stats()["exact_sums"] == 1
+            assert P.stats()["ring_threads"] == (thr or 1024)
             U = [P.apply_normal(V, 1.3) for _ in range(4)]
             G = [P.gradient(x)[0] for _ in range(4)]
         for k in range(1, 4):
             assert np.array_equal(U[0], U[k]) and np.array_equal(G[0], G[k])
+        if vf == rpt.F32:
+            by_thr[thr] = (U[0], G[0])
+    for thr in (768, 640):
+        assert np.array_equal(by_thr[thr][0], by_thr[0][0]) and np.array_equal(by_thr[thr][1], by_thr[0][1])
 
 
 def test_profile_row_pass(rpt):
