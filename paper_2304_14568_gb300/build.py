@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "librpt.so")
 SOURCES = ["rowpass.cu", "rowstream.cu", "solver.cu", "api.cu", "noalloc.cu", "mlp.cu", "chol.cu", "dosecon.cu"]
-HEADERS = ["common.cuh", "rowcommon.cuh", "gemm.cuh", "gemm_bf16.cuh", "plan.h", "layout.h", "chunk.h", "batch.h", os.path.join("..", "..", "include", "rpt.h")]
+HEADERS = ["common.cuh", "rowcommon.cuh", "gemm.cuh", "gemm_bf16.cuh", "gemm_tf32.cuh", "plan.h", "layout.h", "chunk.h", "batch.h", os.path.join("..", "..", "include", "rpt.h")]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
          "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]

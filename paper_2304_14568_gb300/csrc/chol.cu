@@ -15,12 +15,13 @@
 // built in shared memory with the dense kRB x |U| block of A~, and every nonzero
 // pair sum over the block goes to the lower triangle of B_s with one global
 // atomic.  Factorisation and inversion are blocked (64) right-looking
-// algorithms: small diagonal-block kernels plus the FP32 GEMM of gemm.cuh for
-// the trailing updates, batched over scenarios.
+// algorithms: small diagonal-block kernels plus, for the trailing updates and
+// the products of the inverse, the FP32-accurate tensor-core GEMM of
+// gemm_tf32.cuh (error-compensated TF32), batched over scenarios.
 #include <cmath>
 #include <vector>
 
-#include "gemm.cuh"
+#include "gemm_tf32.cuh"
 #include "plan.h"
 #include "rowcommon.cuh"
 
@@ -351,8 +352,8 @@ int chol_prepare(Plan* P, const std::vector<double>& rho, CholExtra* extra) {
       k_trsm_panel<<<dim3((below + 63) / 64, N), 64, 0, st>>>(P->binv, n, kb);
       float* L21 = P->binv + (size_t)(kb + 1) * kNB * n + (size_t)kb * kNB;
       float* A22 = P->binv + (size_t)(kb + 1) * kNB * n + (size_t)(kb + 1) * kNB;
-      gemm<false, true>(st, below, below, kNB, L21, n, L21, n, A22, n, nullptr, false, -1.f, 1.f, N, (long long)nn,
-                        (long long)nn, (long long)nn, /*lower=*/true);
+      gemm_tf32x3<false, true>(st, below, below, kNB, L21, n, L21, n, A22, n, -1.f, 1.f, N, (long long)nn,
+                               (long long)nn, (long long)nn, /*lower=*/true);
     }
   }
   // 3. Y = L^{-1} (forward substitution on I, block row by block row)
@@ -360,15 +361,15 @@ int chol_prepare(Plan* P, const std::vector<double>& rho, CholExtra* extra) {
   for (int kb = 0; kb < nblk; ++kb) {
     const int r0 = kb * kNB, nb = std::min(kNB, n - r0);
     if (r0 > 0)
-      gemm<false, false>(st, nb, r0, r0, P->binv + (size_t)r0 * n, n, Y, n, Y + (size_t)r0 * n, n, nullptr, false,
-                         -1.f, 1.f, N, (long long)nn, (long long)nn, (long long)nn, false, /*kdiag=*/1);
+      gemm_tf32x3<false, false>(st, nb, r0, r0, P->binv + (size_t)r0 * n, n, Y, n, Y + (size_t)r0 * n, n, -1.f,
+                                1.f, N, (long long)nn, (long long)nn, (long long)nn, false, /*kdiag=*/1);
     const int cols = r0 + nb;
     k_trsm_left<<<dim3((cols + 63) / 64, N), 64, 0, st>>>(P->binv, Y, n, kb, cols);
   }
   // 4. B^{-1} = Y^T Y into binv (the factor is no longer needed): lower tiles, the
   //    sum starting at max(i, j) since Y is lower triangular; then mirrored
-  gemm<true, false>(st, n, n, n, Y, n, Y, n, P->binv, n, nullptr, false, 1.f, 0.f, N, (long long)nn, (long long)nn,
-                    (long long)nn, /*lower=*/true, /*kdiag=*/2);
+  gemm_tf32x3<true, false>(st, n, n, n, Y, n, Y, n, P->binv, n, 1.f, 0.f, N, (long long)nn, (long long)nn,
+                           (long long)nn, /*lower=*/true, /*kdiag=*/2);
   k_mirror_lower<<<dim3((n + 31) / 32, (n + 31) / 32, N), dim3(32, 8), 0, st>>>(P->binv, n);
   if ((e = cudaGetLastError())) return done(cuda_fail(e, "launch"));
   // 5. A~_s^T p~

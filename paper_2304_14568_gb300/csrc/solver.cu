@@ -132,6 +132,21 @@ __device__ __forceinline__ void last_block_sums(const double* buf, int count, in
   block_sum_d<K>(S, sh);
 }
 
+// In warp 0 of a block: the sums over c < count of buf[c * stride + off] and
+// buf[c * stride + off + 1], lane l taking c = l, l + 32, ... (independent loads
+// in flight instead of a serial chain) and a butterfly across the warp: a fixed
+// order for a given count.  Results valid in every lane of warp 0.
+__device__ __forceinline__ void warp_sums2(const double* buf, int count, int stride, int off, double& a, double& b) {
+  a = 0.0;
+  b = 0.0;
+  for (int c = threadIdx.x; c < count; c += 32) {
+    a += __ldcg(&buf[(size_t)c * stride + off]);
+    b += __ldcg(&buf[(size_t)c * stride + off + 1]);
+  }
+  a = warp_sum_d(a);
+  b = warp_sum_d(b);
+}
+
 __device__ __forceinline__ void set_cond(unsigned long long h, int use, int value) {
   if (use) cudaGraphSetConditional((cudaGraphConditionalHandle)h, value ? 1u : 0u);
 }
@@ -215,15 +230,12 @@ __global__ void k_cg_init(DevPlan P, Ctl* C, const float* __restrict__ partial,
     d[1] = v[1];
   }
   if (!last_block(&cnt_s[s], gridDim.x)) return;
+  double g = 0.0, rr = 0.0;
+  if (threadIdx.x < 32) warp_sums2(dots + (size_t)s * nchunk * 4, nchunk, 4, 0, g, rr);
   if (threadIdx.x == 0 && !live) {
     cgi[s] = 0;
     act[s] = 0;
   } else if (threadIdx.x == 0) {
-    double g = 0.0, rr = 0.0;
-    for (int c = 0; c < nchunk; ++c) {
-      g += __ldcg(&dots[((size_t)s * nchunk + c) * 4]);
-      rr += __ldcg(&dots[((size_t)s * nchunk + c) * 4 + 1]);
-    }
     const double rn = sqrt(rr);
     double t;
     if (G.first) {
@@ -242,9 +254,11 @@ __global__ void k_cg_init(DevPlan P, Ctl* C, const float* __restrict__ partial,
     act[s] = (rn > t && g > 0.0 && C->cg_max > 0) ? 1 : 0;
   }
   if (!last_block(&C->cnt_init, P.N)) return;
-  if (threadIdx.x == 0) {
+  if (threadIdx.x < 32) {
     int any = 0;
-    for (int k = 0; k < P.N; ++k) any += __ldcg(&act[k]);
+    for (int k = threadIdx.x; k < P.N; k += 32) any += __ldcg(&act[k]);
+    any = __reduce_add_sync(0xffffffffu, any);
+    if (threadIdx.x != 0) return;
     C->cg_any = any;
     C->kcg = 0;
     C->passes += 1;
@@ -272,10 +286,11 @@ __global__ void k_cg_dots(DevPlan P, Ctl* C, const float* __restrict__ partial,
   }
   block_sum_d<1>(v, sh);
   if (threadIdx.x == 0) dots[((size_t)s * nchunk + blockIdx.x) * 4 + 2] = v[0];
-  if (!last_block(&cnt_s[s], gridDim.x)) return;
+  if (!last_block(&cnt_s[s], gridDim.x) || threadIdx.x >= 32) return;
+  double delta = 0.0;
+  for (int c = threadIdx.x; c < nchunk; c += 32) delta += __ldcg(&dots[((size_t)s * nchunk + c) * 4 + 2]);
+  delta = warp_sum_d(delta);
   if (threadIdx.x == 0) {
-    double delta = 0.0;
-    for (int c = 0; c < nchunk; ++c) delta += __ldcg(&dots[((size_t)s * nchunk + c) * 4 + 2]);
     const double g = __ldcg(&gam[s]);
     const bool first = __ldcg(&cgi[s]) == 0;
     const double b = first ? 0.0 : g / __ldcg(&gprev[s]);
@@ -324,12 +339,9 @@ __global__ void k_cg_update(DevPlan P, Ctl* C, double* x, double* r, double* u, 
     d[1] = v[1];
   }
   if (last_block(&cnt_s[s], gridDim.x)) {
+    double g = 0.0, rr = 0.0;
+    if (threadIdx.x < 32) warp_sums2(dots + (size_t)s * nchunk * 4, nchunk, 4, 0, g, rr);
     if (threadIdx.x == 0) {
-      double g = 0.0, rr = 0.0;
-      for (int c = 0; c < nchunk; ++c) {
-        g += __ldcg(&dots[((size_t)s * nchunk + c) * 4]);
-        rr += __ldcg(&dots[((size_t)s * nchunk + c) * 4 + 1]);
-      }
       gprev[s] = __ldcg(&gam[s]);
       aprev[s] = a;
       gam[s] = g;
@@ -337,17 +349,23 @@ __global__ void k_cg_update(DevPlan P, Ctl* C, double* x, double* r, double* u, 
       cgcnt[s] += 1;
       act_next[s] = (a > 0.0 && g > 0.0 && sqrt(rr) > __ldcg(&tol[s])) ? 1 : 0;
     }
-    if (!last_block(&C->cnt_upd, (unsigned int)any)) return;
-    if (threadIdx.x == 0) {
-      int na = 0;
-      for (int k = 0; k < P.N; ++k) {
-        if (act[k]) {
-          C->cg_total += 1;
-          C->g[k / P.Ns].cg += 1;
-          act[k] = __ldcg(&act_next[k]);
-          na += act[k];
-        }
+    if (!last_block(&C->cnt_upd, (unsigned int)any) || threadIdx.x >= 32) return;
+    // warp 0: the scenarios of this step (lane l takes l, l + 32, ...) count one CG
+    // step each and take their next activity
+    int was = 0, na = 0;
+    for (int k = threadIdx.x; k < P.N; k += 32) {
+      if (__ldcg(&act[k])) {
+        ++was;
+        atomicAdd(reinterpret_cast<unsigned long long*>(&C->g[k / P.Ns].cg), 1ull);
+        const int nx = __ldcg(&act_next[k]);
+        act[k] = nx;
+        na += nx;
       }
+    }
+    was = __reduce_add_sync(0xffffffffu, was);
+    na = __reduce_add_sync(0xffffffffu, na);
+    if (threadIdx.x == 0) {
+      C->cg_total += was;
       C->cg_any = na;
       C->kcg += 1;
       C->cg_steps += 1;
