@@ -31,6 +31,7 @@ namespace {
 constexpr int kRB = 16;       // rows per outer-product block
 constexpr int kUMax = 1536;   // columns a block may touch (more: the per-row path)
 constexpr int kNB = 64;       // Cholesky / inverse block size
+constexpr int kPB = 4;        // blocks per panel: the trailing matrix is updated once per panel (rank 256)
 constexpr unsigned kFull = 0xffffffffu;
 
 // Lower triangle of B_s (row-major n x n, zero on entry) += sum over kept rows k
@@ -343,28 +344,52 @@ int chol_prepare(Plan* P, const std::vector<double>& rho, CholExtra* extra) {
     k_add_diag<<<dim3((n + 255) / 256, dp.Ns), 256, 0, st>>>(P->binv + nn * (size_t)g * dp.Ns, n,
                                                               (float)(0.5 * rho[g]));
   if (extra && (e = extra->add(P, P->binv))) return done(cuda_fail(e, "constraint terms of B_s"));
-  // 2. Cholesky, lower, in place
+  // 2. Cholesky, lower, in place, right-looking in panels of kPB blocks: inside a
+  //    panel each block is factored (diagonal block, then the rows below it) and
+  //    its rank-64 update goes to the rest of the panel's columns only; the
+  //    matrix right of the panel gets the panel's rank-256 update once
   const int nblk = (n + kNB - 1) / kNB;
-  for (int kb = 0; kb < nblk; ++kb) {
-    k_potrf_diag<<<N, 256, 0, st>>>(P->binv, n, kb, P->err);
-    const int below = n - (kb + 1) * kNB;
-    if (below > 0) {
-      k_trsm_panel<<<dim3((below + 63) / 64, N), 64, 0, st>>>(P->binv, n, kb);
-      float* L21 = P->binv + (size_t)(kb + 1) * kNB * n + (size_t)kb * kNB;
-      float* A22 = P->binv + (size_t)(kb + 1) * kNB * n + (size_t)(kb + 1) * kNB;
-      gemm_tf32x3<false, true>(st, below, below, kNB, L21, n, L21, n, A22, n, -1.f, 1.f, N, (long long)nn,
-                               (long long)nn, (long long)nn, /*lower=*/true);
+  const long long snn = (long long)nn;
+  for (int KB = 0; KB < nblk; KB += kPB) {
+    const int kend = std::min(KB + kPB, nblk);
+    for (int kb = KB; kb < kend; ++kb) {
+      k_potrf_diag<<<N, 256, 0, st>>>(P->binv, n, kb, P->err);
+      const int c0 = (kb + 1) * kNB;            // first row and column after block kb
+      if (c0 >= n) continue;
+      k_trsm_panel<<<dim3((n - c0 + 63) / 64, N), 64, 0, st>>>(P->binv, n, kb);
+      const int c1 = std::min(kend * kNB, n);   // the panel's remaining columns c0 .. c1
+      if (c1 > c0) {
+        const float* L21 = P->binv + (size_t)c0 * n + (size_t)kb * kNB;
+        gemm_tf32x3<false, true>(st, n - c0, c1 - c0, kNB, L21, n, L21, n, P->binv + (size_t)c0 * n + c0, n,
+                                 -1.f, 1.f, N, snn, snn, snn, /*lower=*/true);
+      }
+    }
+    const int t0 = kend * kNB;
+    if (t0 < n) {
+      const float* Lp = P->binv + (size_t)t0 * n + (size_t)KB * kNB;   // rows t0.., the panel's columns
+      gemm_tf32x3<false, true>(st, n - t0, n - t0, (kend - KB) * kNB, Lp, n, Lp, n, P->binv + (size_t)t0 * n + t0,
+                               n, -1.f, 1.f, N, snn, snn, snn, /*lower=*/true);
     }
   }
-  // 3. Y = L^{-1} (forward substitution on I, block row by block row)
+  // 3. Y = L^{-1} (forward substitution on I), in panels of kPB block rows: the
+  //    panel's rows first take -L Y over all earlier columns in one product
+  //    (Y is lower triangular, so the earlier rows of Y end at the panel), then
+  //    block row by block row the rest of the sum and the diagonal block's solve
   k_set_identity<<<gd, 256, 0, st>>>(Y, n);
-  for (int kb = 0; kb < nblk; ++kb) {
-    const int r0 = kb * kNB, nb = std::min(kNB, n - r0);
-    if (r0 > 0)
-      gemm_tf32x3<false, false>(st, nb, r0, r0, P->binv + (size_t)r0 * n, n, Y, n, Y + (size_t)r0 * n, n, -1.f,
-                                1.f, N, (long long)nn, (long long)nn, (long long)nn, false, /*kdiag=*/1);
-    const int cols = r0 + nb;
-    k_trsm_left<<<dim3((cols + 63) / 64, N), 64, 0, st>>>(P->binv, Y, n, kb, cols);
+  for (int KB = 0; KB < nblk; KB += kPB) {
+    const int kend = std::min(KB + kPB, nblk);
+    const int R0 = KB * kNB, R1 = std::min(kend * kNB, n);
+    if (R0 > 0)
+      gemm_tf32x3<false, false>(st, R1 - R0, R0, R0, P->binv + (size_t)R0 * n, n, Y, n, Y + (size_t)R0 * n, n,
+                                -1.f, 1.f, N, snn, snn, snn, false, /*kdiag=*/1);
+    for (int kb = KB; kb < kend; ++kb) {
+      const int r0 = kb * kNB, nb = std::min(kNB, n - r0);
+      if (r0 > R0)
+        gemm_tf32x3<false, false>(st, nb, r0, r0 - R0, P->binv + (size_t)r0 * n + R0, n, Y + (size_t)R0 * n, n,
+                                  Y + (size_t)r0 * n, n, -1.f, 1.f, N, snn, snn, snn);
+      const int cols = r0 + nb;
+      k_trsm_left<<<dim3((cols + 63) / 64, N), 64, 0, st>>>(P->binv, Y, n, kb, cols);
+    }
   }
   // 4. B^{-1} = Y^T Y into binv (the factor is no longer needed): lower tiles, the
   //    sum starting at max(i, j) since Y is lower triangular; then mirrored
