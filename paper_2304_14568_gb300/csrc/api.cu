@@ -1056,21 +1056,28 @@ int create_plan(const rpt_problem* pr, const rpt_device_opts* opts, rpt_plan** o
         return cuda_fail(e, "autotune");
       }
     }
-    // two rounds over the configurations, 10 launches each, keeping each one's
-    // best: one short timing per configuration let clock and queue noise pick
-    // a slower ring
-    for (int round = 0; round < 2; ++round)
-      for (size_t c = 0; c < ring_cfgs.size(); ++c) {
-        if ((e = apply(ring_cfgs[c]))) {
-          free_plan(P);
-          return cuda_fail(e, "autotune");
-        }
-        double t = 0.0, by = 0.0;
-        if (int rc = profile_row_pass(P, kNormal, 10, &t, &by)) {
-          free_plan(P);
-          return rc;
-        }
-        ms[c] = std::min(ms[c], t);
+    // every configuration timed over 4 launches, then the four fastest again over
+    // 10 launches each, keeping each one's best (one short timing per
+    // configuration let clock and queue noise pick a slower ring)
+    auto time_cfg = [&](size_t c, int reps) -> int {
+      if ((e = apply(ring_cfgs[c]))) return cuda_fail(e, "autotune");
+      double t = 0.0, by = 0.0;
+      if (int rc = profile_row_pass(P, kNormal, reps, &t, &by)) return rc;
+      ms[c] = std::min(ms[c], t);
+      return RPT_OK;
+    };
+    for (size_t c = 0; c < ring_cfgs.size(); ++c)
+      if (int rc = time_cfg(c, 4)) {
+        free_plan(P);
+        return rc;
+      }
+    std::vector<size_t> order(ring_cfgs.size());
+    for (size_t c = 0; c < order.size(); ++c) order[c] = c;
+    std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return ms[a] < ms[b]; });
+    for (size_t k = 0; k < std::min<size_t>(4, order.size()); ++k)
+      if (int rc = time_cfg(order[k], 10)) {
+        free_plan(P);
+        return rc;
       }
     const size_t best = (size_t)(std::min_element(ms.begin(), ms.end()) - ms.begin());
     if ((e = apply(ring_cfgs[best]))) {
