@@ -223,7 +223,7 @@ __device__ __forceinline__ void process_bundle(const int4* __restrict__ rec, int
   const float u1 = k1 + __shfl_xor_sync(kFull, g1, h);
   float tw = (up2 ? u1 : u0) + __shfl_xor_sync(kFull, up2 ? u0 : u1, qd);
   for (int o = qd >> 1; o > 0; o >>= 1) tw += __shfl_xor_sync(kFull, tw, o);
-  const int rho = sl / qd;                       // the row whose whole dot this lane holds
+  const int rho = sl >> (__ffs(qd) - 1);         // the row whose whole dot this lane holds (qd a power of 2)
   float wc = 0.f, pr = 0.f;
   int kept = -1;
   if (valid) {
@@ -487,10 +487,11 @@ k_rowpass_tma(DevPlan P, const float* __restrict__ vin, int v_stride, const int*
       const IT* col = reinterpret_cast<const IT*>(sp + rec_bytes + val_bytes);
       const long long off = base - ch.g_al;
       const int G = ch.group;                // lanes per row (bundle)
-      const int rpw = 32 / G;                // rows (bundles) per warp step
-      const int sl = lane & (G - 1), sub = lane / G;
+      const int lg = __ffs(G) - 1;           // G is a power of two: shifts, not divisions
+      const int rpw = 32 >> lg;              // rows (bundles) per warp step
+      const int sl = lane & (G - 1), sub = lane >> lg;
       const size_t dose_base = (size_t)s * P.m_act;
-      const int units = (ch.n_rows + rpw - 1) / rpw;
+      const int units = (ch.n_rows + rpw - 1) >> (5 - lg);
       int u0 = cw - rot;
       if (u0 < 0) u0 += NCW;
       rot = (rot + units) % NCW;
@@ -541,8 +542,8 @@ k_rowpass(DevPlan P, const float* __restrict__ vin, int v_stride, const int* __r
     const int4* __restrict__ rec = P.rowrec + P.rec_base[s];
     const VT* __restrict__ val = vals<VT>(P) + P.nnz_base[s];
     const IT* __restrict__ col = cols<IT>(P) + P.nnz_base[s];
-    const int G = blk.w, rpw = 32 / G;
-    const int sl = lane & (G - 1), sub = lane / G;
+    const int G = blk.w, lg = __ffs(G) - 1, rpw = 32 >> lg;   // G a power of two
+    const int sl = lane & (G - 1), sub = lane >> lg;
     const size_t dose_base = (size_t)s * P.m_act;
     double obj = 0.0;
     for (;;) {
