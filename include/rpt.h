@@ -300,8 +300,9 @@ int rpt_plan_batch_query(const rpt_plan* plan, int32_t* n_plans, int32_t* col_of
  * rpt_admm_bb_solve.  params->tol_obj must be +inf and f_target 0 (the
  * objective tests are not available here: RPT_EUNSUPPORTED).
  *   x_out:     one non-NULL host array per problem (rpt_plan_batch_query),
- *              x_out[k] of problem k's own spot count; written for every
- *              problem whatever its status.
+ *              x_out[k] of problem k's own spot count; for a batched plan
+ *              written for every problem whatever its status (see plan_info);
+ *              for a plan of one problem on RPT_OK and RPT_NOT_CONVERGED.
  *   info:      (may be NULL) the whole solve: status (RPT_OK when every problem
  *              converged, RPT_DIVERGED when one diverged, else
  *              RPT_NOT_CONVERGED), iterations (of the longest problem), CG steps,
