@@ -111,7 +111,7 @@ typedef struct {
   int32_t accumulate;               /* row path 4's scatter: 0 = library choice (2); 1 = exact 64-bit fixed-point
                                        sums: every pass, and so every solve, is bitwise reproducible whatever
                                        the scheduling, and tight tolerances (1e-7) converge where float
-                                       rounding noise can stall them; about 25 % slower per pass;
+                                       rounding noise can stall them; about 40 % slower per pass;
                                        2 = float32 shared-memory atomics, whose results vary in the last bits
                                        from run to run */
   int32_t ring_threads;             /* row path 4: threads of a row-pass CTA, 1024 (31 consumer warps, 6 block
