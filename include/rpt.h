@@ -273,6 +273,9 @@ int rpt_plan_query(const rpt_plan* plan, rpt_plan_stats* out);
  *          (checked per problem, so a column index is checked against its own
  *          problem's spot count).
  *   *out:  one plan holding all problems; destroy it with rpt_plan_destroy.
+ *          Creation builds, on the host, one row-pointer array over all the
+ *          problems' voxels per unit (4 bytes x total voxels x n_plans x N,
+ *          released when the call returns).
  *          rpt_plan_query reports the problems together: m and n summed, N
  *          the scenario count of one problem, default_rho the rule on all of
  *          them stacked, const_term summed.
