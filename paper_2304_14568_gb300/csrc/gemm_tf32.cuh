@@ -19,7 +19,9 @@
 // A CTA computes a 64 x 64 tile with 4 warps of 32 x 32 (2 x 4 mma tiles each);
 // K advances in steps of 32 staged in shared memory as [row][k] for op(A) and
 // [column][k] for op(B) (a row stride of 36 floats keeps the fragment loads of a
-// warp on 32 distinct banks).  beta == 0 never reads C.
+// warp on 32 distinct banks).  The next K step's tiles are loaded from global
+// memory into registers while the tensor cores work on the current one.
+// beta == 0 never reads C.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -73,23 +75,40 @@ k_gemm_tf32x3(int M, int N, int K, const float* __restrict__ A, int lda, long lo
 #pragma unroll
       for (int c = 0; c < 4; ++c) acc[a][b][c] = 0.f;
   const int kfirst = kdiag == 2 ? max(i0, j0) : (kdiag == 1 ? j0 : 0);
-  for (int k0 = (kfirst / kT3BK) * kT3BK; k0 < K; k0 += kT3BK) {
-    // loads run along each operand's contiguous dimension
-    for (int e = tid; e < kT3BM * kT3BK; e += kT3Threads) {
+  constexpr int kPer = kT3BM * kT3BK / kT3Threads;   // tile elements per thread and operand (16)
+  float ra[kPer], rb[kPer];
+  // loads run along each operand's contiguous dimension
+  auto load = [&](int k0) {
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+      const int e = tid + q * kT3Threads;
       const int ii = TA ? e % kT3BM : e / kT3BK, kk = TA ? e / kT3BM : e % kT3BK;
       const int i = i0 + ii, k = k0 + kk;
-      float v = 0.f;
-      if (i < M && k < K) v = TA ? A[(size_t)k * lda + i] : A[(size_t)i * lda + k];
-      As[ii][kk] = v;
+      ra[q] = (i < M && k < K) ? (TA ? A[(size_t)k * lda + i] : A[(size_t)i * lda + k]) : 0.f;
+      const int jj = TB ? e / kT3BK : e % kT3BN, kb = TB ? e % kT3BK : e / kT3BN;
+      const int j = j0 + jj, kj = k0 + kb;
+      rb[q] = (j < N && kj < K) ? (TB ? B[(size_t)j * ldb + kj] : B[(size_t)kj * ldb + j]) : 0.f;
     }
-    for (int e = tid; e < kT3BN * kT3BK; e += kT3Threads) {
-      const int jj = TB ? e / kT3BK : e % kT3BN, kk = TB ? e % kT3BK : e / kT3BN;
-      const int j = j0 + jj, k = k0 + kk;
-      float v = 0.f;
-      if (j < N && k < K) v = TB ? B[(size_t)j * ldb + k] : B[(size_t)k * ldb + j];
-      Bs[jj][kk] = v;
+  };
+  auto store = [&]() {
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+      const int e = tid + q * kT3Threads;
+      const int ii = TA ? e % kT3BM : e / kT3BK, kk = TA ? e / kT3BM : e % kT3BK;
+      As[ii][kk] = ra[q];
+      const int jj = TB ? e / kT3BK : e % kT3BN, kb = TB ? e % kT3BK : e / kT3BN;
+      Bs[jj][kb] = rb[q];
     }
-    __syncthreads();
+  };
+  int k0 = (kfirst / kT3BK) * kT3BK;
+  if (k0 < K) {
+    load(k0);
+    store();
+  }
+  __syncthreads();
+  for (; k0 < K; k0 += kT3BK) {
+    const bool more = k0 + kT3BK < K;
+    if (more) load(k0 + kT3BK);   // in flight during the products below
     float part[2][4][4];
 #pragma unroll
     for (int a = 0; a < 2; ++a)
@@ -131,6 +150,8 @@ k_gemm_tf32x3(int M, int N, int K, const float* __restrict__ A, int lda, long lo
       for (int b = 0; b < 4; ++b)
 #pragma unroll
         for (int c = 0; c < 4; ++c) acc[a][b][c] += part[a][b][c];
+    __syncthreads();   // every warp is done with the current tiles
+    if (more) store();
     __syncthreads();
   }
   // accumulator layout: regs 0,1 at (row g, cols 2t, 2t+1), regs 2,3 at row g + 8
