@@ -236,6 +236,12 @@ int create_plan(const rpt_problem* pr, const rpt_device_opts* opts, rpt_plan** o
     set_error("index_width 16 needs n <= 65535");
     return RPT_EINVAL;
   }
+  if (opts && (opts->row_path < 0 || opts->row_path > 4 || opts->accumulate < 0 || opts->accumulate > 2 ||
+               (opts->ring_threads != 0 && opts->ring_threads != 1024 && opts->ring_threads != 768 &&
+                opts->ring_threads != 640))) {
+    set_error("row_path must be 0..4, accumulate 0..2 and ring_threads 0, 640, 768 or 1024");
+    return RPT_EINVAL;
+  }
   if (!pr->row_ptr || !pr->col_idx || !pr->val || !pr->voxel_w || !pr->presc) {
     set_error("null array in rpt_problem");
     return RPT_EINVAL;
@@ -393,13 +399,7 @@ int create_plan(const rpt_problem* pr, const rpt_device_opts* opts, rpt_plan** o
   // row path: the caller's choice, else the bundled ring when its stage fits the
   // plan, else the bulk-copy ring when it fits, else the register path
   const int want_path = opts ? opts->row_path : 0;
-  const int want_thr = opts ? opts->ring_threads : 0;
-  if (want_path < 0 || want_path > 4 || (opts && (opts->accumulate < 0 || opts->accumulate > 2)) ||
-      (want_thr != 0 && want_thr != 1024 && want_thr != 768 && want_thr != 640)) {
-    free_plan(P);
-    set_error("row_path must be 0..4, accumulate 0..2 and ring_threads 0, 640, 768 or 1024");
-    return RPT_EINVAL;
-  }
+  const int want_thr = opts ? opts->ring_threads : 0;   // checked on entry
   const bool exact = opts && opts->accumulate == 1;      // bundled path: fixed-point sums on request
   int smem_optin = 0;
   cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, P->device);

@@ -111,6 +111,14 @@ def test_plan_create_rejects_bad_input_without_touching_the_device(lib, mutate, 
     assert lib.rpt_last_error()
 
 
+@pytest.mark.parametrize("opt", [dict(row_path=5), dict(accumulate=3), dict(ring_threads=512)])
+def test_plan_create_rejects_bad_options_without_touching_the_device(lib, opt):
+    with pytest.raises(rpt.RptError) as ei:
+        rpt.Plan(**_tiny(), **opt)
+    assert ei.value.status == rpt.EINVAL
+    assert b"ring_threads" in lib.rpt_last_error()
+
+
 def test_null_arguments_are_errors(lib):
     assert lib.rpt_plan_create(None, None, None) == rpt.EINVAL
     assert lib.rpt_admm_bb_solve(None, None, None, None, None, None) == rpt.EINVAL
