@@ -796,7 +796,6 @@ int create_plan(const rpt_problem* pr, const rpt_device_opts* opts, rpt_plan** o
   P->y = A.get<double>(Nn);
   P->d = A.get<double>(Nn);
   P->dprev = A.get<double>(Nn);
-  P->w = A.get<double>(Nn);
   P->q = A.get<double>(Nn);
   P->dinv = A.get<double>(Nn);
   P->z = A.get<double>((size_t)G * n);

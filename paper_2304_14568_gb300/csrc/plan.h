@@ -94,7 +94,7 @@ struct Plan {
   float *vz32 = nullptr;          // [n_pad] staged shared vector
   float *partial = nullptr;       // [nblocks][n_pad]
   double *objp = nullptr;         // [nblocks]
-  double *w = nullptr, *q = nullptr, *dinv = nullptr;   // CG: B u, B p, M^{-1}
+  double *q = nullptr, *dinv = nullptr;   // CG: B p, M^{-1}
   float *diag = nullptr;          // [N][n] diag(A~_s^T A~_s)
   double *gam = nullptr, *tol = nullptr, *r0n = nullptr, *alpha = nullptr, *beta = nullptr;
   double *bb_step = nullptr;      // [N] per-scenario ADMM dual steps

@@ -4,7 +4,7 @@
 //   a. residual pass   g_s = A~_s^T (A~_s x_s - p~)              (row pass, kResid)
 //      r_s = c_s - B_s x_s = -g_s - (rho/2)(x_s - z) - y_s/2     (App. A: B_s, c_s)
 //   b. CG on B_s x_s = c_s for all scenarios at once, warm-started from x_s
-//      (each CG step: one row pass kNormal + two vector kernels)
+//      (each CG step: one row pass kNormal + one vector kernel)
 //   c. z = P_box(mean_s(x_s + y_s/rho))                          (z-update)
 //   d. d = x - 1(x)z; BB step from dd = d - d_prev and dy = step_prev d_prev (Eq. 8)
 //   e. y_s += step d_s (Eq. 7); residuals and tolerances of Eq. 9; stop test.
@@ -22,6 +22,7 @@
 #include <cstring>
 #include <vector>
 
+#include <cooperative_groups.h>
 #include <nvtx3/nvToolsExt.h>
 
 #include "plan.h"
@@ -29,6 +30,7 @@
 namespace rpt {
 namespace {
 
+namespace cg = cooperative_groups;
 constexpr int VT = kVecThreads;
 
 __device__ __forceinline__ double clampd(double v, double lo, double hi) {
@@ -266,112 +268,148 @@ __global__ void k_cg_init(DevPlan P, Ctl* C, const float* __restrict__ partial,
   }
 }
 
-// grid (nchunk, N).  w = B u = (row-pass partials) + (rho/2) u; delta = (w, u);
-// per scenario: beta and alpha of the step.
-__global__ void k_cg_dots(DevPlan P, Ctl* C, const float* __restrict__ partial,
-                          const double* __restrict__ u, double* w, double* dots, int nchunk,
-                          const double* __restrict__ gam, const double* __restrict__ gprev,
-                          const double* __restrict__ aprev, double* alpha, double* beta,
-                          const int* __restrict__ act, const int* __restrict__ cgi, unsigned int* cnt_s) {
-  __shared__ double sh[32];
-  const int s = blockIdx.y, j = blockIdx.x * VT + threadIdx.x;
-  if (__ldcg(&act[s]) == 0) return;
-  double v[1] = {0.0};
-  if (j < P.n) {
-    const size_t o = (size_t)s * P.n + j;
-    const double uj = u[o];
-    const double wj = sum_partials(P, partial, s, j) + 0.5 * C->g[s / P.Ns].rho * uj;
-    w[o] = wj;
-    v[0] = wj * uj;
+// grid (kCgCluster, N) in clusters of kCgCluster CTAs along x; the cluster of
+// scenario s makes one whole CG step after the operator pass:
+//   w = B u = (row-pass partials) + (rho/2) u;  delta = (w, u);  beta and alpha;
+//   p = u + beta p;  q = w + beta q;  x += alpha p;  r -= alpha q;  u = M^{-1} r (staged);
+//   gamma = (r, u), ||r||; activity; loop condition.
+// A CTA has kCgSub rows of kVecThreads threads; column chunk c (kVecThreads
+// columns) belongs to the cluster's CTA c mod kCgCluster, to its thread row
+// (c / kCgCluster) mod kCgSub and to its round c / (kCgCluster kCgSub), column
+// j to thread j mod kVecThreads of that row, and a thread takes its rounds in
+// increasing order; each CTA's sums are block reductions and the cluster's the
+// CTAs' sums added in rank order through distributed shared memory.  The order
+// depends on the column index only, not on n: the wider spot range of a
+// batched plan adds exact zeros.  w and u stay in registers between the two
+// halves; the cluster barriers are hardware barriers.
+constexpr int kCgCluster = 8;
+constexpr int kCgSub = 4;
+constexpr int kCgThreads = kCgSub * kVecThreads;
+constexpr int kCgChunks = (RPT_MAX_SPOTS + kCgThreads * kCgCluster - 1) / (kCgThreads * kCgCluster);
+constexpr int kErrCgCluster = 16;   // error word: the CG step ran without its cluster
+
+__global__ void __cluster_dims__(kCgCluster, 1, 1) __launch_bounds__(kCgThreads, 1)
+k_cg_step(DevPlan P, Ctl* C, double* x, double* r, double* u, double* p, double* q,
+          const float* __restrict__ partial, const double* __restrict__ dinv, float* v32, double* gam,
+          double* gprev, double* aprev, const double* __restrict__ tol, int* act, int* act_next, int* cgi,
+          int* cgcnt, unsigned long long hcg, int use_cond) {
+  __shared__ double sh[2 * 32];
+  __shared__ double cl_part[3];   // this CTA's parts of delta, gamma and ||r||^2 (read by the cluster)
+  __shared__ double ab[2];
+  cg::cluster_group cl = cg::this_cluster();
+  if (cl.num_blocks() != kCgCluster) {   // never expected: report it and touch nothing
+    if (threadIdx.x == 0) atomicExch(P.err, kErrCgCluster);
+    return;
   }
-  block_sum_d<1>(v, sh);
-  if (threadIdx.x == 0) dots[((size_t)s * nchunk + blockIdx.x) * 4 + 2] = v[0];
-  if (!last_block(&cnt_s[s], gridDim.x) || threadIdx.x >= 32) return;
-  double delta = 0.0;
-  for (int c = threadIdx.x; c < nchunk; c += 32) delta += __ldcg(&dots[((size_t)s * nchunk + c) * 4 + 2]);
-  delta = warp_sum_d(delta);
+  const int s = blockIdx.y, rank = (int)cl.block_rank();
+  const int sub = threadIdx.x / VT, col = threadIdx.x % VT;
+  if (__ldcg(&act[s]) == 0) return;      // the same answer in every CTA of the cluster
+  const int any = __ldcg(&C->cg_any);
+  const bool first = __ldcg(&cgi[s]) == 0;
+  const double hr = 0.5 * C->g[s / P.Ns].rho;
+  double uv[kCgChunks], wv[kCgChunks];
+  double dl[1] = {0.0};
+#pragma unroll
+  for (int t = 0; t < kCgChunks; ++t) {
+    const int j = ((t * kCgSub + sub) * kCgCluster + rank) * VT + col;
+    uv[t] = 0.0;
+    wv[t] = 0.0;
+    if (j < P.n) {
+      const size_t o = (size_t)s * P.n + j;
+      uv[t] = u[o];
+      wv[t] = sum_partials(P, partial, s, j) + hr * uv[t];
+      dl[0] += wv[t] * uv[t];
+    }
+  }
+  block_sum_d<1>(dl, sh);
+  if (threadIdx.x == 0) cl_part[0] = dl[0];
+  cl.sync();
   if (threadIdx.x == 0) {
+    double parts[kCgCluster];
+#pragma unroll
+    for (int k = 0; k < kCgCluster; ++k) parts[k] = *cl.map_shared_rank(&cl_part[0], k);
+    double delta = 0.0;
+#pragma unroll
+    for (int k = 0; k < kCgCluster; ++k) delta += parts[k];
     const double g = __ldcg(&gam[s]);
-    const bool first = __ldcg(&cgi[s]) == 0;
     const double b = first ? 0.0 : g / __ldcg(&gprev[s]);
     const double den = first ? delta : delta - b * g / __ldcg(&aprev[s]);
-    const double a = (den > 0.0 && isfinite(den) && isfinite(b)) ? g / den : 0.0;
-    alpha[s] = a;
-    beta[s] = b;
+    ab[0] = (den > 0.0 && isfinite(den) && isfinite(b)) ? g / den : 0.0;
+    ab[1] = b;
   }
-}
-
-// grid (nchunk, N).  p = u + beta p; q = w + beta q; x += alpha p; r -= alpha q;
-// u = M^{-1} r (staged); gamma = (r, u), ||r||; activity; loop condition.
-__global__ void k_cg_update(DevPlan P, Ctl* C, double* x, double* r, double* u, const double* __restrict__ w,
-                            double* p, double* q, const double* __restrict__ dinv, float* v32,
-                            double* dots, int nchunk, const double* __restrict__ alpha,
-                            const double* __restrict__ beta, double* gam, double* gprev, double* aprev,
-                            const double* __restrict__ tol, int* act, int* act_next, int* cgi, int* cgcnt,
-                            unsigned int* cnt_s, unsigned long long hcg, int use_cond) {
-  __shared__ double sh[2 * 32];
-  const int s = blockIdx.y, j = blockIdx.x * VT + threadIdx.x;
-  const int any = __ldcg(&C->cg_any);
-  if (__ldcg(&act[s]) == 0) return;
-  const double a = __ldcg(&alpha[s]);
-  const bool first = __ldcg(&cgi[s]) == 0;
+  __syncthreads();
+  const double a = ab[0], b = ab[1];
   double v[2] = {0.0, 0.0};
-  if (j < P.n) {
-    const size_t o = (size_t)s * P.n + j;
-    const double b = __ldcg(&beta[s]);
-    const double pj = first ? u[o] : fma(b, p[o], u[o]);
-    const double qj = first ? w[o] : fma(b, q[o], w[o]);
-    p[o] = pj;
-    q[o] = qj;
-    x[o] = fma(a, pj, x[o]);
-    const double rj = fma(-a, qj, r[o]);
-    const double uj = dinv[o] * rj;
-    r[o] = rj;
-    u[o] = uj;
-    v32[(size_t)s * P.n_pad + j] = (float)uj;
-    v[0] = rj * uj;
-    v[1] = rj * rj;
+#pragma unroll
+  for (int t = 0; t < kCgChunks; ++t) {
+    const int j = ((t * kCgSub + sub) * kCgCluster + rank) * VT + col;
+    if (j < P.n) {
+      const size_t o = (size_t)s * P.n + j;
+      const double pj = first ? uv[t] : fma(b, p[o], uv[t]);
+      const double qj = first ? wv[t] : fma(b, q[o], wv[t]);
+      p[o] = pj;
+      q[o] = qj;
+      x[o] = fma(a, pj, x[o]);
+      const double rj = fma(-a, qj, r[o]);
+      const double uj = dinv[o] * rj;
+      r[o] = rj;
+      u[o] = uj;
+      v32[(size_t)s * P.n_pad + j] = (float)uj;
+      v[0] += rj * uj;
+      v[1] += rj * rj;
+    }
   }
   block_sum_d<2>(v, sh);
   if (threadIdx.x == 0) {
-    double* d = &dots[((size_t)s * nchunk + blockIdx.x) * 4];
-    d[0] = v[0];
-    d[1] = v[1];
+    cl_part[1] = v[0];
+    cl_part[2] = v[1];
   }
-  if (last_block(&cnt_s[s], gridDim.x)) {
+  cl.sync();
+  if (rank == 0 && threadIdx.x == 0) {
+    double pg[kCgCluster], pr[kCgCluster];
+#pragma unroll
+    for (int k = 0; k < kCgCluster; ++k) {
+      pg[k] = *cl.map_shared_rank(&cl_part[1], k);
+      pr[k] = *cl.map_shared_rank(&cl_part[2], k);
+    }
     double g = 0.0, rr = 0.0;
-    if (threadIdx.x < 32) warp_sums2(dots + (size_t)s * nchunk * 4, nchunk, 4, 0, g, rr);
-    if (threadIdx.x == 0) {
-      gprev[s] = __ldcg(&gam[s]);
-      aprev[s] = a;
-      gam[s] = g;
-      cgi[s] += 1;
-      cgcnt[s] += 1;
-      act_next[s] = (a > 0.0 && g > 0.0 && sqrt(rr) > __ldcg(&tol[s])) ? 1 : 0;
+#pragma unroll
+    for (int k = 0; k < kCgCluster; ++k) {
+      g += pg[k];
+      rr += pr[k];
     }
-    if (!last_block(&C->cnt_upd, (unsigned int)any) || threadIdx.x >= 32) return;
-    // warp 0: the scenarios of this step (lane l takes l, l + 32, ...) count one CG
-    // step each and take their next activity
-    int was = 0, na = 0;
-    for (int k = threadIdx.x; k < P.N; k += 32) {
-      if (__ldcg(&act[k])) {
-        ++was;
-        atomicAdd(reinterpret_cast<unsigned long long*>(&C->g[k / P.Ns].cg), 1ull);
-        const int nx = __ldcg(&act_next[k]);
-        act[k] = nx;
-        na += nx;
-      }
+    gprev[s] = __ldcg(&gam[s]);
+    aprev[s] = a;
+    gam[s] = g;
+    cgi[s] += 1;
+    cgcnt[s] += 1;
+    act_next[s] = (a > 0.0 && g > 0.0 && sqrt(rr) > __ldcg(&tol[s])) ? 1 : 0;
+  }
+  cl.sync();   // every CTA's shared memory stays until rank 0 has read it
+  if (rank != 0) return;
+  // rank 0 of every stepping scenario; the last to arrive ends the step
+  if (!last_block(&C->cnt_upd, (unsigned int)any) || threadIdx.x >= 32) return;
+  // warp 0: the scenarios of this step (lane l takes l, l + 32, ...) count one CG
+  // step each and take their next activity
+  int was = 0, na = 0;
+  for (int k = threadIdx.x; k < P.N; k += 32) {
+    if (__ldcg(&act[k])) {
+      ++was;
+      atomicAdd(reinterpret_cast<unsigned long long*>(&C->g[k / P.Ns].cg), 1ull);
+      const int nx = __ldcg(&act_next[k]);
+      act[k] = nx;
+      na += nx;
     }
-    was = __reduce_add_sync(0xffffffffu, was);
-    na = __reduce_add_sync(0xffffffffu, na);
-    if (threadIdx.x == 0) {
-      C->cg_total += was;
-      C->cg_any = na;
-      C->kcg += 1;
-      C->cg_steps += 1;
-      C->passes += 1;
-      set_cond(hcg, use_cond, na > 0 && C->kcg < C->cg_max);
-    }
+  }
+  was = __reduce_add_sync(0xffffffffu, was);
+  na = __reduce_add_sync(0xffffffffu, na);
+  if (threadIdx.x == 0) {
+    C->cg_total += was;
+    C->cg_any = na;
+    C->kcg += 1;
+    C->cg_steps += 1;
+    C->passes += 1;
+    set_cond(hcg, use_cond, na > 0 && C->kcg < C->cg_max);
   }
 }
 
@@ -938,15 +976,10 @@ void admm_iteration_head(Exec& e, Plan* P, unsigned long long hcg, int uc) {
 
 void cg_body(Exec& e, Plan* P, unsigned long long hcg, int uc) {
   const DevPlan& dp = P->dp;
-  dim3 g2(P->nchunk, dp.N);
   rowpass(e, P, kNormal, P->v32, dp.n_pad, P->act);
-  launch(e, k_cg_dots, g2, dim3(VT), 0, dp, P->ctl, (const float*)P->partial, (const double*)P->u,
-         P->w, P->dots, P->nchunk, (const double*)P->gam, (const double*)P->gprev,
-         (const double*)P->aprev, P->alpha, P->beta, (const int*)P->act, (const int*)P->cgi, P->cnt_s);
-  launch(e, k_cg_update, g2, dim3(VT), 0, dp, P->ctl, P->x, P->r, P->u, (const double*)P->w, P->p,
-         P->q, (const double*)P->dinv, P->v32, P->dots, P->nchunk, (const double*)P->alpha,
-         (const double*)P->beta, P->gam, P->gprev, P->aprev, (const double*)P->tol, P->act,
-         P->act_next, P->cgi, P->cgcnt, P->cnt_s, hcg, uc);
+  launch(e, k_cg_step, dim3(kCgCluster, dp.N), dim3(kCgThreads), 0, dp, P->ctl, P->x, P->r, P->u, P->p, P->q,
+         (const float*)P->partial, (const double*)P->dinv, P->v32, P->gam, P->gprev, P->aprev,
+         (const double*)P->tol, P->act, P->act_next, P->cgi, P->cgcnt, hcg, uc);
 }
 
 void admm_iteration_tail(Exec& e, Plan* P, int use_obj, unsigned long long hadmm, int uc, ConHook* con = nullptr) {
@@ -1099,6 +1132,10 @@ int check_err(Plan* P) {
   if (e != cudaSuccess) return cuda_fail(e, "read error word");
   if (h != 0) {
     cudaMemsetAsync(P->err, 0, sizeof(int), P->stream);
+    if (h == kErrCgCluster) {
+      set_error("the CG step kernel ran without its thread-block cluster");
+      return RPT_ECUDA;
+    }
     set_error("a row-pass pipeline wait ran out (code " + std::to_string(h) + ")");
     return RPT_TIMEOUT;
   }
@@ -1350,9 +1387,9 @@ int admm_solve_impl(Plan* P, const rpt_admm_params* prm, const double* z0, const
       return cuda_fail(e, "copy x_out");
     if ((e = cudaStreamSynchronize(st))) return cuda_fail(e, "sync");
   }
-  // init + per iteration (residual pass, CG init, 3 per CG step, z/d/y, 2 for the
+  // init + per iteration (residual pass, CG init, 2 per CG step, z/d/y, 2 for the
   // optional objective test) + final objective pass and its reduction (+ staging)
-  const long long kernels = (chol ? 3 + 5LL * h.k : 3 + 5LL * h.k + 3LL * h.cg_steps) +
+  const long long kernels = (chol ? 3 + 5LL * h.k : 3 + 5LL * h.k + 2LL * h.cg_steps) +
                             (use_obj ? 2LL * h.k : 0LL) + (G > 1 ? 1 : 0);
   auto fill = [&](rpt_solve_info* o, const Grp& q, int st_q) {
     std::memset(o, 0, sizeof(*o));
