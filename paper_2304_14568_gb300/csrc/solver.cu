@@ -38,28 +38,28 @@ __device__ __forceinline__ double clampd(double v, double lo, double hi) {
 }
 
 // Compensated sum, in the slot list's fixed order, of scenario s's row-pass
-// partials at column j.
-__device__ __forceinline__ double sum_partials(const DevPlan& P, const float* __restrict__ part, int s, int j) {
+// partials at column j; list holds the cnt slots of scenario s (in global or
+// shared memory, written before this kernel started).  Sixteen slots at a
+// time: all loads of a batch are issued before the (order-preserving) sums
+// consume them.
+__device__ __forceinline__ double sum_partials_of(const DevPlan& P, const float* __restrict__ part, int s, int j,
+                                                  const int* list, int cnt) {
+  constexpr int kB = 16;
   if (P.acc64) {
     // bundled path: 64-bit fixed-point partials, summed exactly (every partial
     // and every sum stays below 2^62 in magnitude), then scaled by 2^-fexp[s]
     // and by the column scale of quantised values
     const long long* pl = reinterpret_cast<const long long*>(part);
-    const int cnt = __ldcg(&P.slot_count[s]);
-    const int* list = P.slot_list + (size_t)s * P.slot_cap;
     long long sum = 0;
     int k = 0;
-    for (; k + 8 <= cnt; k += 8) {
-      int idx[8];
-      long long v[8];
+    for (; k + kB <= cnt; k += kB) {
+      long long v[kB];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) idx[u] = __ldcg(&list[k + u]);
+      for (int u = 0; u < kB; ++u) v[u] = __ldcg(pl + (size_t)list[k + u] * P.n_pad + j);
 #pragma unroll
-      for (int u = 0; u < 8; ++u) v[u] = __ldcg(pl + (size_t)idx[u] * P.n_pad + j);
-#pragma unroll
-      for (int u = 0; u < 8; ++u) sum += v[u];
+      for (int u = 0; u < kB; ++u) sum += v[u];
     }
-    for (; k < cnt; ++k) sum += __ldcg(pl + (size_t)__ldcg(&list[k]) * P.n_pad + j);
+    for (; k < cnt; ++k) sum += __ldcg(pl + (size_t)list[k] * P.n_pad + j);
     const int fe = __ldcg(&P.fexp[s]);
     if (fe == kFexpNaN) return __longlong_as_double(0x7ff8000000000000ll);
     double r = ldexp((double)sum, -fe);
@@ -67,20 +67,13 @@ __device__ __forceinline__ double sum_partials(const DevPlan& P, const float* __
     return r;
   }
   float sum = 0.f, c = 0.f;
-  const int cnt = __ldcg(&P.slot_count[s]);
-  const int* list = P.slot_list + (size_t)s * P.slot_cap;
-  // eight slots at a time: all loads of a batch are issued before the
-  // (order-preserving) compensated sums consume them
   int k = 0;
-  for (; k + 8 <= cnt; k += 8) {
-    int idx[8];
-    float v[8];
+  for (; k + kB <= cnt; k += kB) {
+    float v[kB];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) idx[u] = __ldcg(&list[k + u]);
+    for (int u = 0; u < kB; ++u) v[u] = __ldcg(part + (size_t)list[k + u] * P.n_pad + j);
 #pragma unroll
-    for (int u = 0; u < 8; ++u) v[u] = __ldcg(part + (size_t)idx[u] * P.n_pad + j);
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
+    for (int u = 0; u < kB; ++u) {
       float t, e;
       two_sum(sum, v[u], t, e);
       sum = t;
@@ -88,13 +81,17 @@ __device__ __forceinline__ double sum_partials(const DevPlan& P, const float* __
     }
   }
   for (; k < cnt; ++k) {
-    const float v = __ldcg(part + (size_t)__ldcg(&list[k]) * P.n_pad + j);
+    const float v = __ldcg(part + (size_t)list[k] * P.n_pad + j);
     float t, e;
     two_sum(sum, v, t, e);
     sum = t;
     c += e;
   }
   return (double)sum + (double)c;
+}
+
+__device__ __forceinline__ double sum_partials(const DevPlan& P, const float* __restrict__ part, int s, int j) {
+  return sum_partials_of(P, part, s, j, P.slot_list + (size_t)s * P.slot_cap, __ldcg(&P.slot_count[s]));
 }
 
 // Objective of the last objective pass: sum over scenarios (fixed order).
@@ -287,6 +284,7 @@ constexpr int kCgSub = 4;
 constexpr int kCgThreads = kCgSub * kVecThreads;
 constexpr int kCgChunks = (RPT_MAX_SPOTS + kCgThreads * kCgCluster - 1) / (kCgThreads * kCgCluster);
 constexpr int kErrCgCluster = 16;   // error word: the CG step ran without its cluster
+constexpr int kCgListCap = 2048;    // slot lists up to this length are read from shared memory
 
 __global__ void __cluster_dims__(kCgCluster, 1, 1) __launch_bounds__(kCgThreads, 1)
 k_cg_step(DevPlan P, Ctl* C, double* x, double* r, double* u, double* p, double* q,
@@ -296,6 +294,7 @@ k_cg_step(DevPlan P, Ctl* C, double* x, double* r, double* u, double* p, double*
   __shared__ double sh[2 * 32];
   __shared__ double cl_part[3];   // this CTA's parts of delta, gamma and ||r||^2 (read by the cluster)
   __shared__ double ab[2];
+  __shared__ int s_list[kCgListCap];
   cg::cluster_group cl = cg::this_cluster();
   if (cl.num_blocks() != kCgCluster) {   // never expected: report it and touch nothing
     if (threadIdx.x == 0) atomicExch(P.err, kErrCgCluster);
@@ -307,7 +306,34 @@ k_cg_step(DevPlan P, Ctl* C, double* x, double* r, double* u, double* p, double*
   const int any = __ldcg(&C->cg_any);
   const bool first = __ldcg(&cgi[s]) == 0;
   const double hr = 0.5 * C->g[s / P.Ns].rho;
+  // the scenario's slot list into shared memory, and the step's scalars, all
+  // loads in flight together (this kernel's rank 0 rewrites the scalars only
+  // after every CTA of the cluster has passed its second barrier)
+  const int cnt = __ldcg(&P.slot_count[s]);
+  const int* glist = P.slot_list + (size_t)s * P.slot_cap;
+  const int* list = cnt <= kCgListCap ? s_list : glist;
+  if (cnt <= kCgListCap)
+    for (int k = threadIdx.x; k < cnt; k += blockDim.x) s_list[k] = __ldcg(&glist[k]);
+  double g_s = 0.0, gp_s = 0.0, ap_s = 0.0, tol_s = 0.0;
+  if (threadIdx.x == 0) {
+    g_s = __ldcg(&gam[s]);
+    gp_s = __ldcg(&gprev[s]);
+    ap_s = __ldcg(&aprev[s]);
+    tol_s = __ldcg(&tol[s]);
+  }
+  __syncthreads();
   double uv[kCgChunks], wv[kCgChunks];
+  // the second half's operands of the first round are loaded now, so that
+  // their latency overlaps the first half's sums and barriers
+  const int j0 = (sub * kCgCluster + rank) * VT + col;
+  const size_t o0 = (size_t)s * P.n + j0;
+  double p0 = 0.0, q0 = 0.0, r0 = 0.0, d0 = 0.0;
+  if (j0 < P.n) {
+    p0 = p[o0];
+    q0 = q[o0];
+    r0 = r[o0];
+    d0 = dinv[o0];
+  }
   double dl[1] = {0.0};
 #pragma unroll
   for (int t = 0; t < kCgChunks; ++t) {
@@ -317,7 +343,7 @@ k_cg_step(DevPlan P, Ctl* C, double* x, double* r, double* u, double* p, double*
     if (j < P.n) {
       const size_t o = (size_t)s * P.n + j;
       uv[t] = u[o];
-      wv[t] = sum_partials(P, partial, s, j) + hr * uv[t];
+      wv[t] = sum_partials_of(P, partial, s, j, list, cnt) + hr * uv[t];
       dl[0] += wv[t] * uv[t];
     }
   }
@@ -331,10 +357,9 @@ k_cg_step(DevPlan P, Ctl* C, double* x, double* r, double* u, double* p, double*
     double delta = 0.0;
 #pragma unroll
     for (int k = 0; k < kCgCluster; ++k) delta += parts[k];
-    const double g = __ldcg(&gam[s]);
-    const double b = first ? 0.0 : g / __ldcg(&gprev[s]);
-    const double den = first ? delta : delta - b * g / __ldcg(&aprev[s]);
-    ab[0] = (den > 0.0 && isfinite(den) && isfinite(b)) ? g / den : 0.0;
+    const double b = first ? 0.0 : g_s / gp_s;
+    const double den = first ? delta : delta - b * g_s / ap_s;
+    ab[0] = (den > 0.0 && isfinite(den) && isfinite(b)) ? g_s / den : 0.0;
     ab[1] = b;
   }
   __syncthreads();
@@ -345,13 +370,13 @@ k_cg_step(DevPlan P, Ctl* C, double* x, double* r, double* u, double* p, double*
     const int j = ((t * kCgSub + sub) * kCgCluster + rank) * VT + col;
     if (j < P.n) {
       const size_t o = (size_t)s * P.n + j;
-      const double pj = first ? uv[t] : fma(b, p[o], uv[t]);
-      const double qj = first ? wv[t] : fma(b, q[o], wv[t]);
+      const double pj = first ? uv[t] : fma(b, t == 0 ? p0 : p[o], uv[t]);
+      const double qj = first ? wv[t] : fma(b, t == 0 ? q0 : q[o], wv[t]);
       p[o] = pj;
       q[o] = qj;
       x[o] = fma(a, pj, x[o]);
-      const double rj = fma(-a, qj, r[o]);
-      const double uj = dinv[o] * rj;
+      const double rj = fma(-a, qj, t == 0 ? r0 : r[o]);
+      const double uj = (t == 0 ? d0 : dinv[o]) * rj;
       r[o] = rj;
       u[o] = uj;
       v32[(size_t)s * P.n_pad + j] = (float)uj;
@@ -378,12 +403,12 @@ k_cg_step(DevPlan P, Ctl* C, double* x, double* r, double* u, double* p, double*
       g += pg[k];
       rr += pr[k];
     }
-    gprev[s] = __ldcg(&gam[s]);
+    gprev[s] = g_s;
     aprev[s] = a;
     gam[s] = g;
     cgi[s] += 1;
     cgcnt[s] += 1;
-    act_next[s] = (a > 0.0 && g > 0.0 && sqrt(rr) > __ldcg(&tol[s])) ? 1 : 0;
+    act_next[s] = (a > 0.0 && g > 0.0 && sqrt(rr) > tol_s) ? 1 : 0;
   }
   cl.sync();   // every CTA's shared memory stays until rank 0 has read it
   if (rank != 0) return;
@@ -393,10 +418,10 @@ k_cg_step(DevPlan P, Ctl* C, double* x, double* r, double* u, double* p, double*
   // step each and take their next activity
   int was = 0, na = 0;
   for (int k = threadIdx.x; k < P.N; k += 32) {
-    if (__ldcg(&act[k])) {
+    const int ak = __ldcg(&act[k]), nx = __ldcg(&act_next[k]);   // both loads in flight
+    if (ak) {
       ++was;
       atomicAdd(reinterpret_cast<unsigned long long*>(&C->g[k / P.Ns].cg), 1ull);
-      const int nx = __ldcg(&act_next[k]);
       act[k] = nx;
       na += nx;
     }
