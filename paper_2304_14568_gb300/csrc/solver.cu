@@ -862,8 +862,8 @@ __global__ void k_chol_rhs(DevPlan P, const Ctl* __restrict__ C, const double* _
 // product).  grid (nb = ceil(n / kSymRows), N), kSymWarps warps.  CTA (rb, s)
 // takes rows i in [i0, i0 + kSymRows) and the columns j <= i of those rows, in
 // stripes of 128 columns (warp w takes stripes w, w + kSymWarps, ...; lane l
-// columns 4l .. 4l + 3 of a stripe; the loads of 16 rows are in flight at
-// once, and two CTAs fit an SM).  Each b = B_ij with j < i adds b c_j to
+// columns 4l .. 4l + 3 of a stripe; the 32 rows' loads of a stripe are all in
+// flight at once, so one CTA per SM keeps enough bytes in flight).  Each b = B_ij with j < i adds b c_j to
 // row i's sum and b c_i to column j's sum; the diagonal adds to its row only.
 // Row sums (float per lane, then float64 across lanes and warps in a fixed
 // order) go to x; the CTA's column sums go to colpart[s][rb][j], which
@@ -887,7 +887,7 @@ __device__ __forceinline__ void load4(const float* p, int jb, int jend, float (&
 }
 
 template <bool VEC>
-__global__ void __launch_bounds__(kSymWarps * 32, 2)
+__global__ void __launch_bounds__(kSymWarps * 32)
 k_chol_x_sym(DevPlan P, const Ctl* __restrict__ C, const float* __restrict__ binv, const float* __restrict__ c,
              double* x, float* __restrict__ colpart) {
   __shared__ float crow[kSymRows];
@@ -911,40 +911,37 @@ k_chol_x_sym(DevPlan P, const Ctl* __restrict__ C, const float* __restrict__ bin
     float cj[4], ca[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
     for (int q = 0; q < 4; ++q) cj[q] = jb + q < jend ? cs[jb + q] : 0.f;
-    const bool full = st * 128 + 128 <= i0;   // the whole stripe lies left of the block's diagonal
-    // rows in two halves: the half's loads are all issued before its products
+    if (st * 128 + 128 <= i0) {   // the whole stripe lies left of the block's diagonal
 #pragma unroll
-    for (int h = 0; h < kSymRows; h += kSymRows / 2) {
-      float b[kSymRows / 2][4];
+      for (int r = 0; r < kSymRows; ++r) {
+        if (r < rows) {
+          float b[4];
+          load4<VEC>(Bs + (size_t)(i0 + r) * n, jb, jend, b);
+          const float ci = crow[r];
+          float t = b[0] * cj[0];
 #pragma unroll
-      for (int r = 0; r < kSymRows / 2; ++r) {
-        if (h + r < rows) {
-          load4<VEC>(Bs + (size_t)(i0 + h + r) * n, jb, jend, b[r]);
-        } else {
+          for (int q = 1; q < 4; ++q) t = fmaf(b[q], cj[q], t);
+          racc[r] += t;
 #pragma unroll
-          for (int q = 0; q < 4; ++q) b[r][q] = 0.f;
+          for (int q = 0; q < 4; ++q) ca[q] = fmaf(b[q], ci, ca[q]);
         }
       }
+    } else {
 #pragma unroll
-      for (int r = 0; r < kSymRows / 2; ++r) {
-        const int i = i0 + h + r;
-        const float ci = crow[h + r];   // 0 beyond the last row
-        if (full) {
-          float t = b[r][0] * cj[0];
-#pragma unroll
-          for (int q = 1; q < 4; ++q) t = fmaf(b[r][q], cj[q], t);
-          racc[h + r] += t;
-#pragma unroll
-          for (int q = 0; q < 4; ++q) ca[q] = fmaf(b[r][q], ci, ca[q]);
-        } else {
+      for (int r = 0; r < kSymRows; ++r) {
+        if (r < rows) {
+          const int i = i0 + r;
+          float b[4];
+          load4<VEC>(Bs + (size_t)i * n, jb, jend, b);
+          const float ci = crow[r];
           float t = 0.f;
 #pragma unroll
           for (int q = 0; q < 4; ++q) {
             const int j = jb + q;
-            if (j <= i) t = fmaf(b[r][q], cj[q], t);
-            if (j < i) ca[q] = fmaf(b[r][q], ci, ca[q]);
+            if (j <= i) t = fmaf(b[q], cj[q], t);
+            if (j < i) ca[q] = fmaf(b[q], ci, ca[q]);
           }
-          racc[h + r] += t;
+          racc[r] += t;
         }
       }
     }
