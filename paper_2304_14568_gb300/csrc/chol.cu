@@ -297,11 +297,6 @@ int chol_prepare(Plan* P, const std::vector<double>& rho, CholExtra* extra) {
     if ((e = cudaMalloc(&P->binv, sizeof(float) * nn * N))) return cuda_fail(e, "allocate the factor");
     P->allocs.push_back(P->binv);
   }
-  if (!P->colpart) {   // column sums of the lower-triangle x-update: one n_pad row per row block
-    const size_t cp = sizeof(float) * (size_t)((n + kSymRows - 1) / kSymRows) * dp.n_pad * N;
-    if ((e = cudaMalloc(&P->colpart, cp))) return cuda_fail(e, "allocate the x-update's column sums");
-    P->allocs.push_back(P->colpart);
-  }
   if (!P->bchol) {
     if ((e = cudaMalloc(&P->bchol, sizeof(double) * (size_t)n * N))) return cuda_fail(e, "allocate A~'p~");
     P->allocs.push_back(P->bchol);

@@ -69,9 +69,6 @@ struct Ctl {
   Grp g[kMaxGroups];      // per group (one per problem of a batched plan)
 };
 
-// rows of one block of the cached-factor x-update (solver.cu, k_chol_x_sym)
-constexpr int kSymRows = 32;
-
 // trace entry: iteration, seconds since the solve started, r_prim, r_dual,
 // eps_prim, eps_dual, dual step, CG steps so far (summed over scenarios)
 constexpr int kTraceFields = 8;
@@ -115,7 +112,6 @@ struct Plan {
   // cached-factor subproblem (chol.cu): B_s^{-1} [N][n][n] FP32, A~_s^T p~ [N][n],
   // record index of kept row k in scenario s's list [N][m_act] (-1: empty there)
   float *binv = nullptr;
-  float *colpart = nullptr;        // [N][ceil(n / kSymRows)][n_pad] column sums of the x-update's row blocks
   double *bchol = nullptr;
   int *rec_of = nullptr;
   double *trace = nullptr;         // [kTraceCap][kTraceFields] (allocated on first traced solve)

@@ -857,131 +857,54 @@ __global__ void k_chol_rhs(DevPlan P, const Ctl* __restrict__ C, const double* _
   c[(size_t)s * P.n_pad + j] = (float)(bchol[o] + 0.5 * C->g[gi].rho * z[(size_t)gi * P.n + j] - 0.5 * y[o]);
 }
 
-// Cached-factor x-update, part 2 (App. A): x_s = B_s^{-1} c_s, reading only
-// the lower triangle of the symmetric B_s^{-1} (half the bytes of the dense
-// product).  grid (nb = ceil(n / kSymRows), N), kSymWarps warps.  CTA (rb, s)
-// takes rows i in [i0, i0 + kSymRows) and the columns j <= i of those rows, in
-// stripes of 128 columns (warp w takes stripes w, w + kSymWarps, ...; lane l
-// columns 4l .. 4l + 3 of a stripe; the 32 rows' loads of a stripe are all in
-// flight at once, so one CTA per SM keeps enough bytes in flight).  Each b = B_ij with j < i adds b c_j to
-// row i's sum and b c_i to column j's sum; the diagonal adds to its row only.
-// Row sums (float per lane, then float64 across lanes and warps in a fixed
-// order) go to x; the CTA's column sums go to colpart[s][rb][j], which
-// k_chol_colsum adds to x in increasing rb.  The matrix is streamed once
-// (evict-first); the upper triangle is never read.
-constexpr int kSymWarps = 8;
-
-template <bool VEC>
-__device__ __forceinline__ void load4(const float* p, int jb, int jend, float (&b)[4]) {
-  if (VEC) {   // jb % 4 == 0 and n % 4 == 0: jb < jend <= n keeps the 16 bytes inside the row
-    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (jb < jend) v = __ldcs(reinterpret_cast<const float4*>(p + jb));
-    b[0] = v.x;
-    b[1] = v.y;
-    b[2] = v.z;
-    b[3] = v.w;
-  } else {
-#pragma unroll
-    for (int q = 0; q < 4; ++q) b[q] = jb + q < jend ? __ldcs(p + jb + q) : 0.f;
-  }
-}
-
-template <bool VEC>
-__global__ void __launch_bounds__(kSymWarps * 32)
-k_chol_x_sym(DevPlan P, const Ctl* __restrict__ C, const float* __restrict__ binv, const float* __restrict__ c,
-             double* x, float* __restrict__ colpart) {
-  __shared__ float crow[kSymRows];
-  __shared__ double rsum[kSymWarps][kSymRows];
-  // the longest row blocks (the last rows) are dispatched first
-  const int rb = gridDim.x - 1 - blockIdx.x;
-  const int s = blockIdx.y, n = P.n, i0 = rb * kSymRows;
+// Cached-factor x-update, part 2 (App. A): x_s = B_s^{-1} c_s.  grid (ceil(n /
+// kCholRows), N), 256 threads: c_s staged in shared memory, each warp takes rows
+// of B_s^{-1} (streamed once, evict-first) with four 16-byte loads in flight per
+// lane, FP64 accumulation of FP32 products.
+constexpr int kCholRows = 64;
+__global__ void __launch_bounds__(256)
+k_chol_x(DevPlan P, const Ctl* __restrict__ C, const float* __restrict__ binv, const float* __restrict__ c,
+         double* x) {
+  extern __shared__ float cbuf[];
+  const int s = blockIdx.y, n = P.n;
   if (C->g[s / P.Ns].done) return;   // a stopped group keeps its x
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int rows = min(kSymRows, n - i0), jend = i0 + rows;
-  const float* cs = c + (size_t)s * P.n_pad;
-  if (threadIdx.x < kSymRows) crow[threadIdx.x] = (int)threadIdx.x < rows ? cs[i0 + threadIdx.x] : 0.f;
+  for (int j = threadIdx.x; j < n; j += blockDim.x) cbuf[j] = c[(size_t)s * P.n_pad + j];
   __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const float* Bs = binv + (size_t)s * n * n;
-  float* cpo = colpart + ((size_t)s * gridDim.x + rb) * P.n_pad;
-  float racc[kSymRows];
-#pragma unroll
-  for (int r = 0; r < kSymRows; ++r) racc[r] = 0.f;
-  for (int st = w; st * 128 < jend; st += kSymWarps) {
-    const int jb = st * 128 + 4 * lane;
-    float cj[4], ca[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-    for (int q = 0; q < 4; ++q) cj[q] = jb + q < jend ? cs[jb + q] : 0.f;
-    if (st * 128 + 128 <= i0) {   // the whole stripe lies left of the block's diagonal
-#pragma unroll
-      for (int r = 0; r < kSymRows; ++r) {
-        if (r < rows) {
-          float b[4];
-          load4<VEC>(Bs + (size_t)(i0 + r) * n, jb, jend, b);
-          const float ci = crow[r];
-          float t = b[0] * cj[0];
-#pragma unroll
-          for (int q = 1; q < 4; ++q) t = fmaf(b[q], cj[q], t);
-          racc[r] += t;
-#pragma unroll
-          for (int q = 0; q < 4; ++q) ca[q] = fmaf(b[q], ci, ca[q]);
-        }
+  const bool vec = (n & 3) == 0;
+  for (int r = w; r < kCholRows; r += 8) {
+    const int j = blockIdx.x * kCholRows + r;
+    if (j >= n) break;
+    const float* row = Bs + (size_t)j * n;
+    double acc = 0.0;
+    if (vec) {
+      const float4* row4 = reinterpret_cast<const float4*>(row);
+      const float4* c4 = reinterpret_cast<const float4*>(cbuf);
+      const int nq = n >> 2;
+      int k = lane;
+      for (; k + 96 < nq; k += 128) {
+        const float4 b0 = __ldcs(row4 + k), b1 = __ldcs(row4 + k + 32), b2 = __ldcs(row4 + k + 64),
+                     b3 = __ldcs(row4 + k + 96);
+        const float4 v0 = c4[k], v1 = c4[k + 32], v2 = c4[k + 64], v3 = c4[k + 96];
+        float t = b0.x * v0.x + b0.y * v0.y + b0.z * v0.z + b0.w * v0.w;
+        t += b1.x * v1.x + b1.y * v1.y + b1.z * v1.z + b1.w * v1.w;
+        acc += (double)t;
+        t = b2.x * v2.x + b2.y * v2.y + b2.z * v2.z + b2.w * v2.w;
+        t += b3.x * v3.x + b3.y * v3.y + b3.z * v3.z + b3.w * v3.w;
+        acc += (double)t;
+      }
+      for (; k < nq; k += 32) {
+        const float4 b = __ldcs(row4 + k);
+        const float4 v = c4[k];
+        acc += (double)(b.x * v.x + b.y * v.y + b.z * v.z + b.w * v.w);
       }
     } else {
-#pragma unroll
-      for (int r = 0; r < kSymRows; ++r) {
-        if (r < rows) {
-          const int i = i0 + r;
-          float b[4];
-          load4<VEC>(Bs + (size_t)i * n, jb, jend, b);
-          const float ci = crow[r];
-          float t = 0.f;
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const int j = jb + q;
-            if (j <= i) t = fmaf(b[q], cj[q], t);
-            if (j < i) ca[q] = fmaf(b[q], ci, ca[q]);
-          }
-          racc[r] += t;
-        }
-      }
+      for (int k = lane; k < n; k += 32) acc += (double)(__ldcs(row + k) * cbuf[k]);
     }
-#pragma unroll
-    for (int q = 0; q < 4; ++q)
-      if (jb + q < jend) cpo[jb + q] = ca[q];
+    acc = warp_sum_d(acc);
+    if (lane == 0) x[(size_t)s * n + j] = acc;
   }
-#pragma unroll
-  for (int r = 0; r < kSymRows; ++r) {
-    const double v = warp_sum_d((double)racc[r]);
-    if (lane == 0) rsum[w][r] = v;
-  }
-  __syncthreads();
-  if ((int)threadIdx.x < rows) {
-    double t = 0.0;
-#pragma unroll
-    for (int k = 0; k < kSymWarps; ++k) t += rsum[k][threadIdx.x];
-    x[(size_t)s * n + i0 + threadIdx.x] = t;
-  }
-}
-
-// Cached-factor x-update, part 3: x_j += the column sums of the row blocks
-// rb >= j / kSymRows (the blocks holding rows i >= j), added in increasing rb
-// (sixteen loads in flight at a time).  grid (nchunk, N).
-__global__ void k_chol_colsum(DevPlan P, const Ctl* __restrict__ C, const float* __restrict__ colpart, int nb,
-                              double* x) {
-  const int s = blockIdx.y, j = blockIdx.x * VT + threadIdx.x;
-  if (j >= P.n || C->g[s / P.Ns].done) return;
-  const float* cp = colpart + (size_t)s * nb * P.n_pad + j;
-  double t = 0.0;
-  int rb = j / kSymRows;
-  for (; rb + 16 <= nb; rb += 16) {
-    float v[16];
-#pragma unroll
-    for (int u = 0; u < 16; ++u) v[u] = __ldcg(cp + (size_t)(rb + u) * P.n_pad);
-#pragma unroll
-    for (int u = 0; u < 16; ++u) t += (double)v[u];
-  }
-  for (; rb < nb; ++rb) t += (double)__ldcg(cp + (size_t)rb * P.n_pad);
-  x[(size_t)s * P.n + j] += t;
 }
 
 // grid (nchunk): out = scale * sum over all blocks.
@@ -1111,25 +1034,12 @@ void admm_tail_final(Exec& e, Plan* P) {
   launch(e, k_final_obj, dim3(1), dim3(32), 0, P->dp, P->ctl);
 }
 
-// x_s = B_s^{-1} c_s from the lower triangle (c_s staged in v32)
-void chol_x(Exec& e, Plan* P) {
-  const DevPlan& dp = P->dp;
-  const int nb = (dp.n + kSymRows - 1) / kSymRows;
-  if ((dp.n & 3) == 0)
-    launch(e, k_chol_x_sym<true>, dim3(nb, dp.N), dim3(kSymWarps * 32), 0, dp, (const Ctl*)P->ctl,
-           (const float*)P->binv, (const float*)P->v32, P->x, P->colpart);
-  else
-    launch(e, k_chol_x_sym<false>, dim3(nb, dp.N), dim3(kSymWarps * 32), 0, dp, (const Ctl*)P->ctl,
-           (const float*)P->binv, (const float*)P->v32, P->x, P->colpart);
-  launch(e, k_chol_colsum, dim3(P->nchunk, dp.N), dim3(VT), 0, dp, (const Ctl*)P->ctl, (const float*)P->colpart,
-         nb, P->x);
-}
-
 void chol_iteration_head(Exec& e, Plan* P) {
   const DevPlan& dp = P->dp;
   launch(e, k_chol_rhs, dim3(P->nchunk, dp.N), dim3(VT), 0, dp, (const Ctl*)P->ctl, (const double*)P->bchol,
          (const double*)P->z, (const double*)P->y, P->v32);
-  chol_x(e, P);
+  launch(e, k_chol_x, dim3((dp.n + kCholRows - 1) / kCholRows, dp.N), dim3(256), sizeof(float) * (size_t)dp.n_pad,
+         dp, (const Ctl*)P->ctl, (const float*)P->binv, (const float*)P->v32, P->x);
 }
 
 cudaError_t build_admm_chol_graph(Plan* P, int use_obj) {
@@ -1348,6 +1258,9 @@ int admm_solve_impl(Plan* P, const rpt_admm_params* prm, const double* z0, const
   cudaError_t e;
   double setup_s = 0.0;
   if (chol) {
+    if ((e = cudaFuncSetAttribute(k_chol_x, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)(sizeof(float) * (size_t)dp.n_pad))))
+      return cuda_fail(e, "kernel attribute");
     const bool cached = !con && P->chol_ready && !P->chol_con && P->chol_rho == rho;
     const auto t0 = std::chrono::steady_clock::now();
     if (int rc = chol_prepare(P, rho, con)) return rc;
@@ -1436,7 +1349,9 @@ int admm_solve_impl(Plan* P, const rpt_admm_params* prm, const double* z0, const
       ex.st = st;
       if (con) {
         if ((e = con->rhs(P))) return cuda_fail(e, "dose-constraint right-hand side");
-        chol_x(ex, P);
+        launch(ex, k_chol_x, dim3((dp.n + kCholRows - 1) / kCholRows, dp.N), dim3(256),
+               sizeof(float) * (size_t)dp.n_pad, dp, (const Ctl*)P->ctl, (const float*)P->binv,
+               (const float*)P->v32, P->x);
       } else {
         chol_iteration_head(ex, P);
       }
@@ -1499,7 +1414,7 @@ int admm_solve_impl(Plan* P, const rpt_admm_params* prm, const double* z0, const
   }
   // init + per iteration (residual pass, CG init, 2 per CG step, z/d/y, 2 for the
   // optional objective test) + final objective pass and its reduction (+ staging)
-  const long long kernels = (chol ? 3 + 6LL * h.k : 3 + 5LL * h.k + 2LL * h.cg_steps) +
+  const long long kernels = (chol ? 3 + 5LL * h.k : 3 + 5LL * h.k + 2LL * h.cg_steps) +
                             (use_obj ? 2LL * h.k : 0LL) + (G > 1 ? 1 : 0);
   auto fill = [&](rpt_solve_info* o, const Grp& q, int st_q) {
     std::memset(o, 0, sizeof(*o));
