@@ -435,6 +435,10 @@ int create_plan(const rpt_problem* pr, const rpt_device_opts* opts, rpt_plan** o
   RowLists R;                        // per scenario: rows (CSR) or bundles, with entry offsets
   std::vector<int32_t> col_h;        // [NE] spot index per stored entry (block column)
   std::vector<float> val_h;          // [NE * vpe]
+  // bundled layout: each scenario's block columns stay in their own arrays and
+  // are uploaded to their offsets (no host-side concatenation)
+  std::vector<std::vector<int32_t>> bcol;
+  std::vector<std::vector<float>> bval;
   std::vector<int4> rec_h;           // records uploaded to the device
   std::vector<int> recbase_h(N + 1, 0);
   std::vector<int64_t> ebase(N, 0), ecount(N, 0);   // first stored entry and count per scenario
@@ -547,17 +551,15 @@ int create_plan(const rpt_problem* pr, const rpt_device_opts* opts, rpt_plan** o
         bundled = true;
         vpe = kBunRows;
         NE = nbc;
-        col_h.resize((size_t)nbc);
-        val_h.resize((size_t)nbc * kBunRows);
         rec_h.resize((size_t)recs);
+        bcol.resize(N);
+        bval.resize(N);
         for (int s = 0; s < N; ++s) {
-          std::copy(B[s].col.begin(), B[s].col.end(), col_h.begin() + ebase[s]);
-          std::copy(B[s].val.begin(), B[s].val.end(), val_h.begin() + ebase[s] * kBunRows);
           std::copy(B[s].rec.begin(), B[s].rec.end(), rec_h.begin() + recbase_h[s]);
           for (int q = 0; q < B[s].nb; ++q) rec_of_h[(size_t)s * m_act + q] = B[s].pos_of[q];
           std::vector<int4>().swap(B[s].rec);
-          std::vector<int32_t>().swap(B[s].col);
-          std::vector<float>().swap(B[s].val);
+          bcol[s] = std::move(B[s].col);
+          bval[s] = std::move(B[s].val);
         }
         R = std::move(RB);
         ctas = 1;
@@ -848,8 +850,15 @@ int create_plan(const rpt_problem* pr, const rpt_device_opts* opts, rpt_plan** o
     }                                                                                      \
   } while (0)
   RPT_CP(d_base, ebase.data(), N * sizeof(int64_t));
-  RPT_CP(d_col32, col_h.data(), (size_t)NE * sizeof(int32_t));
-  RPT_CP(d_val32, val_h.data(), (size_t)NE * vpe * sizeof(float));
+  if (bundled) {
+    for (int s = 0; s < N; ++s) {
+      RPT_CP(d_col32 + ebase[s], bcol[s].data(), bcol[s].size() * sizeof(int32_t));
+      RPT_CP(d_val32 + ebase[s] * vpe, bval[s].data(), bval[s].size() * sizeof(float));
+    }
+  } else {
+    RPT_CP(d_col32, col_h.data(), (size_t)NE * sizeof(int32_t));
+    RPT_CP(d_val32, val_h.data(), (size_t)NE * vpe * sizeof(float));
+  }
   RPT_CP(d_rec, rec_h.data(), rec_h.size() * sizeof(int4));
   RPT_CP(d_recbase, recbase_h.data(), (N + 1) * sizeof(int));
   RPT_CP(P->rec_of, rec_of_h.data(), rec_of_h.size() * sizeof(int));
