@@ -45,7 +45,7 @@ struct Ctl {
   int pgd_max_iter, max_trials, trial, accepted, failed, pk, pouter, pad2;
   long long trials_total;
   // last-block-done counters (every finisher resets its own counter)
-  unsigned int cnt_init, cnt_dots_g, cnt_upd, cnt_d, cnt_y, cnt_z, cnt_red, cnt_pg, cnt_pt;
+  unsigned int cnt_init, cnt_upd, cnt_d, cnt_y, cnt_z, cnt_red, cnt_pg, cnt_pt;
   unsigned int pad3;
   // optional per-iteration trace (rpt_admm_params.trace): kTraceFields doubles per
   // iteration, at most trace_cap iterations, written by the dual update's last block
