@@ -114,27 +114,40 @@ inline void bank_order(const int32_t* col, int len, int G, BankScratch& S) {
   S.order.clear();
   if (len <= 0) return;
   S.idx.resize(len);
+  S.order.resize(len);
   for (int b = 0; b < 32; ++b) cur[b] = start[b];
   for (int i = 0; i < len; ++i) S.idx[cur[col[i] & 31]++] = i;   // entries by bank, stable
   for (int b = 0; b < 32; ++b) cur[b] = start[b];
-  int banks[32];
-  while ((int)S.order.size() < len) {
-    // banks by entries left, largest first
-    int nb = 0;
-    for (int b = 0; b < 32; ++b)
-      if (cur[b] < start[b + 1]) banks[nb++] = b;
-    std::sort(banks, banks + nb, [&](int x, int y) {
-      const int rx = start[x + 1] - cur[x], ry = start[y + 1] - cur[y];
-      return rx != ry ? rx > ry : x < y;
-    });
-    const int want = std::min(G, len - (int)S.order.size());
+  // non-empty banks by entries left, largest first (ties: lower bank first); the
+  // order carries over from group to group, where it changes little, and is
+  // restored by insertion sort after the emptied banks are dropped
+  auto before = [&](int x, int y) {
+    const int rx = start[x + 1] - cur[x], ry = start[y + 1] - cur[y];
+    return rx != ry ? rx > ry : x < y;
+  };
+  int banks[32], nb = 0;
+  for (int b = 0; b < 32; ++b)
+    if (cnt[b] > 0) banks[nb++] = b;
+  int o = 0;
+  while (o < len) {
+    int kept = 0;
+    for (int k = 0; k < nb; ++k)
+      if (cur[banks[k]] < start[banks[k] + 1]) banks[kept++] = banks[k];
+    nb = kept;
+    for (int k = 1; k < nb; ++k) {
+      const int b = banks[k];
+      int m = k;
+      for (; m > 0 && before(b, banks[m - 1]); --m) banks[m] = banks[m - 1];
+      banks[m] = b;
+    }
+    const int want = std::min(G, len - o);
     int taken = 0;
-    for (int k = 0; k < nb && taken < want; ++k, ++taken) S.order.push_back(S.idx[cur[banks[k]]++]);
+    for (int k = 0; k < nb && taken < want; ++k, ++taken) S.order[o++] = S.idx[cur[banks[k]]++];
     // fewer non-empty banks than lanes: fill the group from the largest banks again
     for (int k = 0; taken < want; k = (k + 1) % nb) {
       const int b = banks[k];
       if (cur[b] < start[b + 1]) {
-        S.order.push_back(S.idx[cur[b]++]);
+        S.order[o++] = S.idx[cur[b]++];
         ++taken;
       }
     }
@@ -223,54 +236,69 @@ inline int32_t f2i_bits(float f) {
   return i;
 }
 
+// Block columns of the bundle of rows r0 .. r0 + rn - 1: the union of the rows'
+// columns by a kBunRows-way merge (each row's next column held as its head,
+// INT32_MAX once the row is exhausted; columns are below INT32_MAX).  With C
+// and V, the union's columns and their kBunRows values (zero where a row lacks
+// the column) are written there; returns the union's size.
+inline int merge_bundle(const std::vector<BundleInRow>& rows, int r0, int rn, int32_t* C, float* V) {
+  const int32_t* col[kBunRows];
+  const float* val[kBunRows];
+  int len[kBunRows], pos[kBunRows];
+  int32_t head[kBunRows];
+  for (int r = 0; r < kBunRows; ++r) {
+    const bool has = r < rn;
+    col[r] = has ? rows[r0 + r].col : nullptr;
+    val[r] = has ? rows[r0 + r].val : nullptr;
+    len[r] = has ? rows[r0 + r].len : 0;
+    pos[r] = 0;
+    head[r] = len[r] > 0 ? col[r][0] : INT32_MAX;
+  }
+  int n = 0;
+  for (;;) {
+    int32_t cmin = head[0];
+    for (int r = 1; r < kBunRows; ++r) cmin = std::min(cmin, head[r]);
+    if (cmin == INT32_MAX) break;
+    if (C) C[n] = cmin;
+    for (int r = 0; r < kBunRows; ++r) {
+      const bool hit = head[r] == cmin;
+      if (C) V[(size_t)n * kBunRows + r] = hit ? val[r][pos[r]] : 0.f;
+      if (hit) {
+        ++pos[r];
+        head[r] = pos[r] < len[r] ? col[r][pos[r]] : INT32_MAX;
+      }
+    }
+    ++n;
+  }
+  return n;
+}
+
+// Two passes over the bundles: their widths first (the sorted order and every
+// bundle's offset follow from them), then each bundle merged into scratch,
+// bank-ordered and written once, at its offset in the sorted layout.
 inline void build_bundles(const std::vector<BundleInRow>& rows, BundleScen* out, BankScratch& S) {
   const int nr = (int)rows.size();
   const int nb = (nr + kBunRows - 1) / kBunRows;
-  // per bundle: union of columns by a kBunRows-way merge, values in place
-  std::vector<std::vector<int32_t>> bc(nb);
-  std::vector<std::vector<float>> bv(nb);
+  std::vector<int32_t> width(nb);
+  int wmax = 0;
   for (int q = 0; q < nb; ++q) {
     const int r0 = q * kBunRows, rn = std::min(kBunRows, nr - r0);
-    int pos[kBunRows] = {0};
-    std::vector<int32_t>& C = bc[q];
-    std::vector<float>& V = bv[q];
-    for (;;) {
-      int32_t cmin = INT32_MAX;
-      for (int r = 0; r < rn; ++r)
-        if (pos[r] < rows[r0 + r].len) cmin = std::min(cmin, rows[r0 + r].col[pos[r]]);
-      if (cmin == INT32_MAX) break;
-      C.push_back(cmin);
-      for (int r = 0; r < kBunRows; ++r) {
-        float v = 0.f;
-        if (r < rn && pos[r] < rows[r0 + r].len && rows[r0 + r].col[pos[r]] == cmin) v = rows[r0 + r].val[pos[r]++];
-        V.push_back(v);
-      }
-    }
-    // bank-balanced block-column order for the bundle's lanes
-    const int len = (int)C.size();
-    if (len > 1) {
-      bank_order(C.data(), len, bundle_lanes(len), S);
-      std::vector<int32_t> c2(len);
-      std::vector<float> v2((size_t)len * kBunRows);
-      for (int i = 0; i < len; ++i) {
-        c2[i] = C[S.order[i]];
-        for (int r = 0; r < kBunRows; ++r) v2[(size_t)i * kBunRows + r] = V[(size_t)S.order[i] * kBunRows + r];
-      }
-      C.swap(c2);
-      V.swap(v2);
-    }
+    width[q] = merge_bundle(rows, r0, rn, nullptr, nullptr);
+    wmax = std::max(wmax, width[q]);
   }
   std::vector<int> ord(nb);
   for (int q = 0; q < nb; ++q) ord[q] = q;
-  std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return bc[a].size() > bc[b].size(); });
+  std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return width[a] > width[b]; });
   out->nb = nb;
   out->pos_of.assign(nb, 0);
   out->rec.assign((size_t)4 * (nb + 1), int4{0, 0, 0, 0});
   int64_t total = 0;
-  for (int q = 0; q < nb; ++q) total += (int64_t)bc[q].size();
+  for (int q = 0; q < nb; ++q) total += (int64_t)width[q];
   out->nbc = total;
   out->col.resize((size_t)total);
   out->val.resize((size_t)total * kBunRows);
+  S.c.resize((size_t)wmax);
+  S.v.resize((size_t)wmax * kBunRows);
   int64_t off = 0;
   for (int k = 0; k < nb; ++k) {
     const int q = ord[k];
@@ -287,9 +315,22 @@ inline void build_bundles(const std::vector<BundleInRow>& rows, BundleScen* out,
     R4[1] = int4{wc[0], wc[1], wc[2], wc[3]};
     R4[2] = int4{pp[0], pp[1], pp[2], pp[3]};
     R4[3] = int4{kp[0], kp[1], kp[2], kp[3]};
-    std::copy(bc[q].begin(), bc[q].end(), out->col.begin() + off);
-    std::copy(bv[q].begin(), bv[q].end(), out->val.begin() + off * kBunRows);
-    off += (int64_t)bc[q].size();
+    const int len = merge_bundle(rows, r0, rn, S.c.data(), S.v.data());
+    int32_t* oc = out->col.data() + off;
+    float* ov = out->val.data() + off * kBunRows;
+    if (len > 1) {
+      // bank-balanced block-column order for the bundle's lanes
+      bank_order(S.c.data(), len, bundle_lanes(len), S);
+      for (int i = 0; i < len; ++i) {
+        const int src = S.order[i];
+        oc[i] = S.c[src];
+        for (int r = 0; r < kBunRows; ++r) ov[(size_t)i * kBunRows + r] = S.v[(size_t)src * kBunRows + r];
+      }
+    } else if (len == 1) {
+      oc[0] = S.c[0];
+      for (int r = 0; r < kBunRows; ++r) ov[r] = S.v[r];
+    }
+    off += len;
   }
   out->rec[(size_t)4 * nb] = int4{(int)off, 0, 0, 0};
 }
