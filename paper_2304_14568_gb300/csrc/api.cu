@@ -529,22 +529,22 @@ int create_plan(const rpt_problem* pr, const rpt_device_opts* opts, rpt_plan** o
         if (want_thr) thr_list = {want_thr};
         else if (autotune) thr_list = {1024, 768, 640};
         else thr_list = {1024};
-        auto keep_for = [](int) { return kBunKeep; };
-        bool found = false;
+        // (the chunks of a shape are the same for every CTA size: cut them once)
         for (const int3& c : fit) {
+          std::vector<ChunkDesc> ch;
+          std::vector<int> sc;
+          if (!build_chunks(RB, ebase, N, c.x, c.y, false, kBunMinLanes, &ch, &sc, kBunKeep)) continue;
           for (int t : thr_list) {
             RingCfg rc;
             rc.cmax = c.x;
             rc.rmax = c.y;
             rc.stages = c.z;
             rc.thr = t;
-            if (!build_chunks(RB, ebase, N, rc.cmax, rc.rmax, false, kBunMinLanes, &rc.chunks, &rc.scen_chunk,
-                              keep_for(t)))
-              continue;
+            rc.chunks = ch;
+            rc.scen_chunk = sc;
             ring_cfgs.push_back(std::move(rc));
-            found = true;
           }
-          if (found && !autotune) break;
+          if (!autotune) break;
         }
       }
       if (!ring_cfgs.empty()) {
