@@ -118,36 +118,38 @@ inline void bank_order(const int32_t* col, int len, int G, BankScratch& S) {
   for (int b = 0; b < 32; ++b) cur[b] = start[b];
   for (int i = 0; i < len; ++i) S.idx[cur[col[i] & 31]++] = i;   // entries by bank, stable
   for (int b = 0; b < 32; ++b) cur[b] = start[b];
-  // non-empty banks by entries left, largest first (ties: lower bank first); the
-  // order carries over from group to group, where it changes little, and is
-  // restored by insertion sort after the emptied banks are dropped
-  auto before = [&](int x, int y) {
-    const int rx = start[x + 1] - cur[x], ry = start[y + 1] - cur[y];
-    return rx != ry ? rx > ry : x < y;
-  };
-  int banks[32], nb = 0;
+  // non-empty banks by entries left, largest first (ties: lower bank first),
+  // kept as keys (left << 5) | (31 - bank) in decreasing order; the order
+  // carries over from group to group, where it changes little, and is restored
+  // by insertion sort after the emptied banks are dropped
+  int key[32], nb = 0;
   for (int b = 0; b < 32; ++b)
-    if (cnt[b] > 0) banks[nb++] = b;
+    if (cnt[b] > 0) key[nb++] = (cnt[b] << 5) | (31 - b);
   int o = 0;
   while (o < len) {
     int kept = 0;
     for (int k = 0; k < nb; ++k)
-      if (cur[banks[k]] < start[banks[k] + 1]) banks[kept++] = banks[k];
+      if (key[k] >= 32) key[kept++] = key[k];
     nb = kept;
     for (int k = 1; k < nb; ++k) {
-      const int b = banks[k];
+      const int x = key[k];
       int m = k;
-      for (; m > 0 && before(b, banks[m - 1]); --m) banks[m] = banks[m - 1];
-      banks[m] = b;
+      for (; m > 0 && x > key[m - 1]; --m) key[m] = key[m - 1];
+      key[m] = x;
     }
     const int want = std::min(G, len - o);
     int taken = 0;
-    for (int k = 0; k < nb && taken < want; ++k, ++taken) S.order[o++] = S.idx[cur[banks[k]]++];
+    for (int k = 0; k < nb && taken < want; ++k, ++taken) {
+      const int b = 31 - (key[k] & 31);
+      S.order[o++] = S.idx[cur[b]++];
+      key[k] -= 32;
+    }
     // fewer non-empty banks than lanes: fill the group from the largest banks again
     for (int k = 0; taken < want; k = (k + 1) % nb) {
-      const int b = banks[k];
-      if (cur[b] < start[b + 1]) {
+      if (key[k] >= 32) {
+        const int b = 31 - (key[k] & 31);
         S.order[o++] = S.idx[cur[b]++];
+        key[k] -= 32;
         ++taken;
       }
     }
