@@ -71,6 +71,51 @@ def test_bank_balance_is_a_permutation_that_spreads_banks(shim, seed):
             assert np.unique(grp).size >= min(grp.size, left)
 
 
+def _bank_order_rule(col, G):
+    """The bank order's rule written out: entries grouped by bank (spot column
+    mod 32) in their original order; every group of G output slots takes one
+    entry from each non-empty bank, banks with the most entries left first (ties:
+    the lower bank), then, if there are fewer such banks than slots, further
+    entries from those banks again in the same order."""
+    left = {b: [i for i in range(len(col)) if col[i] % 32 == b] for b in range(32)}
+    order = []
+    while len(order) < len(col):
+        banks = sorted((b for b in range(32) if left[b]), key=lambda b: (-len(left[b]), b))
+        want = min(G, len(col) - len(order))
+        taken = 0
+        for b in banks[:want]:
+            order.append(left[b].pop(0))
+            taken += 1
+        k = 0
+        while taken < want:
+            b = banks[k % len(banks)]
+            if left[b]:
+                order.append(left[b].pop(0))
+                taken += 1
+            k += 1
+    return order
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_bank_balance_order_follows_its_rule(shim, seed):
+    rng = np.random.default_rng(100 + seed)
+    for _ in range(60):
+        ln = int(rng.integers(1, 200))
+        G = int(rng.choice([1, 2, 8, 16, 32]))
+        kind = int(rng.integers(0, 3))
+        if kind == 0:     # clustered: a few banks only, so groups are filled from them again
+            col = np.sort(rng.choice(np.arange(0, 32 * ln, 32), size=ln, replace=False) + rng.integers(0, 3))
+        else:
+            span = ln + 5 if kind == 1 else 5000
+            col = np.sort(rng.choice(span, size=ln, replace=False))
+        col = col.astype(np.int32)
+        val = np.arange(ln, dtype=np.float32)
+        c2, v2 = col.copy(), val.copy()
+        shim.shim_bank_balance(c2, v2, ln, G)
+        order = _bank_order_rule(col.tolist(), G)
+        assert c2.tolist() == col[order].tolist() and v2.tolist() == val[order].tolist()
+
+
 @pytest.mark.parametrize("plen,G", [(4, 8), (32, 8), (36, 8), (64, 16), (96, 32), (128, 32), (132, 32), (260, 32)])
 def test_interleave_row_formula(shim, plen, G):
     col = np.arange(plen, dtype=np.int32) * 3
