@@ -769,7 +769,7 @@ def main():
     if not args.no_e2e:
         # end to end through the C ABI with host buffers: upload + solve + result read-back
         h2d = st["matrix_bytes"] + prob.m * 16 + prob.n * 16
-        e2e, e2e_it = [], []
+        e2e, e2e_it, phases = [], [], []
         for _ in range(max(2, args.steps)):
             torch.cuda.synchronize(dev)
             t0 = time.perf_counter()
@@ -779,10 +779,14 @@ def main():
             torch.cuda.synchronize(dev)
             e2e.append(time.perf_counter() - t0)
             e2e_it.append(i2["iterations"])
+            s2 = p2.stats()
+            phases.append((s2["layout_seconds"], s2["device_seconds"], s2["autotune_seconds"], i2["seconds"]))
             p2.close()
         out["e2e"] = {"value": statistics.mean(e2e), "unit": "s", "h2d_bytes_per_step": int(h2d),
                       "d2h_bytes_per_step": int(prob.n * 8), "runs": len(e2e),
                       "iterations": e2e_it,
+                      "phases_s": {k: statistics.mean(p[i] for p in phases) for i, k in
+                                   enumerate(("create_host_layout", "create_device", "create_autotune", "solve"))},
                       "note": "plan_create from host CSR (validate, bundle, upload, autotune the ring) + solve + "
                               "x read-back; mean over runs (the iteration count of a solve varies by a few "
                               "percent with the order of floating-point atomics)"}

@@ -214,6 +214,10 @@ typedef struct {
   int32_t exact_sums;     /* 1: the row passes sum in exact fixed point (path 4 with accumulate 1), so
                              their results do not depend on scheduling; 0: float atomics */
   int32_t ring_threads;   /* path 4: threads of a row-pass CTA (1024, 768 or 640); 0 otherwise */
+  /* wall time of rpt_plan_create by phase (seconds): */
+  double  layout_seconds;   /* host: validation, row compaction and the stored layout */
+  double  device_seconds;   /* device set-up, allocation, upload and device-side preparation */
+  double  autotune_seconds; /* ring autotuning (0 when no configuration was timed) */
 } rpt_plan_stats;
 
 /* ---- defaults ----------------------------------------------------------- */

@@ -8,6 +8,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <chrono>
 #include <thread>
 #include <vector>
 
@@ -205,6 +206,10 @@ int create_plan(const rpt_problem* pr, const rpt_device_opts* opts, rpt_plan** o
     set_error("null argument");
     return RPT_EINVAL;
   }
+  // phase times of the creation (rpt_plan_stats): host layout, device work, autotuning
+  using clock = std::chrono::steady_clock;
+  auto secs = [](clock::time_point a, clock::time_point b) { return std::chrono::duration<double>(b - a).count(); };
+  const clock::time_point t_begin = clock::now();
   const int m = pr->m, n = pr->n, N = pr->N;
   const int G = U ? U->G : 1, Ns = U ? U->Ns : N;
   static_assert(batch::kMaxProblems == kMaxGroups, "batched problems = solver groups");
@@ -353,6 +358,7 @@ int create_plan(const rpt_problem* pr, const rpt_device_opts* opts, rpt_plan** o
     NNZp += pn;
   }
 
+  const clock::time_point t_host0 = clock::now();
   Plan* P = new (std::nothrow) Plan();
   if (!P) {
     set_error("out of host memory");
@@ -374,6 +380,7 @@ int create_plan(const rpt_problem* pr, const rpt_device_opts* opts, rpt_plan** o
     }
     P->own_stream = true;
   }
+  const clock::time_point t_dev0 = clock::now();
   const int n_pad = (n + 31) / 32 * 32;
   DevPlan& dp = P->dp;
   dp.m = m;
@@ -765,6 +772,7 @@ int create_plan(const rpt_problem* pr, const rpt_device_opts* opts, rpt_plan** o
   for (int s = 0; s < N; ++s)
     for (int j = 0; j < n; ++j) diag_h[(size_t)s * n + j] = (float)(cs[s] * chk[s].diag[j]);
 
+  const clock::time_point t_host1 = clock::now();
   // ---- device memory ----
   // entry arrays are padded so that 16-entry aligned bulk copies stay inside them
   constexpr int64_t kPad = 64;
@@ -1040,6 +1048,14 @@ int create_plan(const rpt_problem* pr, const rpt_device_opts* opts, rpt_plan** o
   S.stages = (dp.path == 1 || dp.path == 3) ? dp.stages : 0;
   S.autotuned = 0;
   S.autotune_ms = 0.0;
+  if ((e = cudaStreamSynchronize(st))) {
+    free_plan(P);
+    return cuda_fail(e, "sync");
+  }
+  const clock::time_point t_dev1 = clock::now();
+  S.layout_seconds = secs(t_begin, t_host0) + secs(t_dev0, t_host1);
+  S.device_seconds = secs(t_host0, t_dev0) + secs(t_host1, t_dev1);
+  S.autotune_seconds = 0.0;
   // ---- autotuning: time every fitting ring configuration on this plan, keep the fastest ----
   if ((use_tma || bundled) && ring_cfgs.size() > 1) {
     std::vector<double> ms(ring_cfgs.size(), 1e30);
@@ -1098,6 +1114,7 @@ int create_plan(const rpt_problem* pr, const rpt_device_opts* opts, rpt_plan** o
     S.ring_threads = bundled ? ring_cfgs[best].thr : 0;
     S.autotuned = (int32_t)ring_cfgs.size();
     S.autotune_ms = ms[best];
+    S.autotune_seconds = secs(t_dev1, clock::now());
   }
   *out = reinterpret_cast<rpt_plan*>(P);
   return RPT_OK;

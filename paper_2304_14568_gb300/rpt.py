@@ -109,7 +109,8 @@ class _Stats(C.Structure):
                 ("row_path", C.c_int32), ("min_lanes", C.c_int32), ("chunk_entries", C.c_int32),
                 ("chunk_rows", C.c_int32), ("stages", C.c_int32), ("autotuned", C.c_int32),
                 ("autotune_ms", C.c_double), ("bundles", C.c_int64), ("block_cols", C.c_int64),
-                ("bundle_fill", C.c_double), ("exact_sums", C.c_int32), ("ring_threads", C.c_int32)]
+                ("bundle_fill", C.c_double), ("exact_sums", C.c_int32), ("ring_threads", C.c_int32),
+                ("layout_seconds", C.c_double), ("device_seconds", C.c_double), ("autotune_seconds", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
