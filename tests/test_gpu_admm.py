@@ -126,6 +126,33 @@ def test_iterates_match_oracle(rpt, bb, zm, per_scen):
             assert info["r_prim"] == pytest.approx(ref["r_prim"], rel=1e-3, abs=1e-5 * sz)
 
 
+def test_iterates_match_oracle_wide(rpt):
+    """8,500 spots: the CG step kernel's clusters take the columns past 8,192 in
+    a second round (32 chunks of 256 columns per round).  Iterates after 1 and 2
+    iterations against the oracle's exact-subproblem ADMM-BB with the error
+    budget of test_iterates_match_oracle."""
+    from tests.gpu_util import fp32_op_bound
+    prob = random_problem(35, m=600, n=8500, N=2, mean_row=30.0, long_rows=0, ub=6.0)
+    W = Weighted(prob)
+    rho = 0.3 * default_rho(W)
+    kf = fp32_op_bound(prob)
+    Aa = [abs(M) for M in W.At]
+    with plan_of(rpt, prob) as P:
+        for k in (1, 2):
+            ref = admm_bb(W, rho=rho, max_iter=k, eps_abs=0.0, eps_rel=0.0)
+            x, info = P.admm_bb_solve(rho=rho, max_iter=k, eps_abs=0.0, eps_rel=0.0, **TIGHT_CG)
+            z, X, Y = P.state_get()
+            e2 = 0.0
+            for s in range(prob.N):
+                xs = np.abs(ref["x"][s])
+                mag = Aa[s].T @ (Aa[s] @ xs) + 0.5 * rho * xs + np.abs(W.b(s))
+                e2 += float(np.sum(mag ** 2))
+            bound = 10.0 * k * (2.0 / rho) * kf * math.sqrt(e2)
+            assert np.linalg.norm(X - ref["x"]) <= bound, (k, np.linalg.norm(X - ref["x"]), bound)
+            assert np.linalg.norm(z - ref["z"]) <= bound
+            assert np.linalg.norm(Y - ref["y"]) <= 4.0 * rho * bound + 1e-9 * np.linalg.norm(ref["y"])
+
+
 @pytest.fixture(scope="module")
 def random_interior():
     """A random problem whose optimum is interior in most coordinates (the box is
