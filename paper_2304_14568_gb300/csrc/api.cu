@@ -477,34 +477,28 @@ int create_plan(const rpt_problem* pr, const rpt_device_opts* opts, rpt_plan** o
       if (tma_smem_bytes(n_pad, c.x, c.y, c.z, bv, bi, true, true, exact) + 1024 <= (size_t)smem_optin)
         fit.push_back(c);
     if (!fit.empty()) {
-      std::vector<BundleScen> B(N);
+      std::vector<BundleScen> B;
       {
+        // each scenario's rows in kept order, then the bundles of all scenarios
+        // with their work spread over every host thread
+        std::vector<std::vector<BundleInRow>> rows(N);
+        for (int s = 0; s < N; ++s) {
+          const int32_t* rp = pr->row_ptr[s];
+          rows[s].reserve(order[s].size());
+          for (int32_t k : order[s]) {
+            const int32_t i = kept[k], a0 = rp[i];
+            BundleInRow br;
+            br.kept = k;
+            br.col = pr->col_idx[s] + a0;
+            br.val = pr->val[s] + a0;
+            br.len = rp[i + 1] - a0;
+            br.wc = (float)(cs[s] * pr->voxel_w[i]);
+            br.p = (float)pr->presc[i];
+            rows[s].push_back(br);
+          }
+        }
         const int hw = std::max(1u, std::thread::hardware_concurrency());
-        const int nt = std::min(N, std::min(hw, 32));
-        std::atomic<int> next(0);
-        std::vector<std::thread> th;
-        for (int t = 0; t < nt; ++t)
-          th.emplace_back([&]() {
-            BankScratch bs;
-            std::vector<BundleInRow> rows;
-            for (int s = next++; s < N; s = next++) {
-              const int32_t* rp = pr->row_ptr[s];
-              rows.clear();
-              for (int32_t k : order[s]) {
-                const int32_t i = kept[k], a0 = rp[i];
-                BundleInRow br;
-                br.kept = k;
-                br.col = pr->col_idx[s] + a0;
-                br.val = pr->val[s] + a0;
-                br.len = rp[i + 1] - a0;
-                br.wc = (float)(cs[s] * pr->voxel_w[i]);
-                br.p = (float)pr->presc[i];
-                rows.push_back(br);
-              }
-              build_bundles(rows, &B[s], bs);
-            }
-          });
-        for (auto& t : th) t.join();
+        build_bundles_all(rows, &B, std::min(hw, 32));
       }
       RowLists RB;
       RB.rec_base.assign(N + 1, 0);

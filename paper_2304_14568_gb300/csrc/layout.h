@@ -10,8 +10,10 @@
 #include <vector_types.h>
 
 #include <algorithm>
+#include <atomic>
 #include <climits>
 #include <cstring>
+#include <thread>
 #include <vector>
 
 #include "chunk.h"
@@ -275,35 +277,38 @@ inline int merge_bundle(const std::vector<BundleInRow>& rows, int r0, int rn, in
   return n;
 }
 
-// Two passes over the bundles: their widths first (the sorted order and every
-// bundle's offset follow from them), then each bundle merged into scratch,
-// bank-ordered and written once, at its offset in the sorted layout.
-inline void build_bundles(const std::vector<BundleInRow>& rows, BundleScen* out, BankScratch& S) {
+// The bundling in three steps, so that the work of several scenarios can be
+// spread over threads:
+//   bundle_widths: the widths (block columns) of bundles q0 .. q1 - 1;
+//   bundle_order:  from all widths, the sorted order (widest first, stable),
+//                  pos_of, the records and the storage of out;
+//   bundle_fill:   the block columns of sorted bundles k0 .. k1 - 1, each merged
+//                  into scratch, bank-ordered and written once at its offset.
+inline int bundle_count(const std::vector<BundleInRow>& rows) {
+  return ((int)rows.size() + kBunRows - 1) / kBunRows;
+}
+
+inline void bundle_widths(const std::vector<BundleInRow>& rows, int q0, int q1, int32_t* width) {
   const int nr = (int)rows.size();
-  const int nb = (nr + kBunRows - 1) / kBunRows;
-  std::vector<int32_t> width(nb);
-  int wmax = 0;
-  for (int q = 0; q < nb; ++q) {
+  for (int q = q0; q < q1; ++q) {
     const int r0 = q * kBunRows, rn = std::min(kBunRows, nr - r0);
     width[q] = merge_bundle(rows, r0, rn, nullptr, nullptr);
-    wmax = std::max(wmax, width[q]);
   }
-  std::vector<int> ord(nb);
-  for (int q = 0; q < nb; ++q) ord[q] = q;
-  std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return width[a] > width[b]; });
+}
+
+inline void bundle_order(const std::vector<BundleInRow>& rows, const std::vector<int32_t>& width, BundleScen* out,
+                         std::vector<int>* ord) {
+  const int nr = (int)rows.size();
+  const int nb = (int)width.size();
+  ord->resize(nb);
+  for (int q = 0; q < nb; ++q) (*ord)[q] = q;
+  std::stable_sort(ord->begin(), ord->end(), [&](int a, int b) { return width[a] > width[b]; });
   out->nb = nb;
   out->pos_of.assign(nb, 0);
   out->rec.assign((size_t)4 * (nb + 1), int4{0, 0, 0, 0});
-  int64_t total = 0;
-  for (int q = 0; q < nb; ++q) total += (int64_t)width[q];
-  out->nbc = total;
-  out->col.resize((size_t)total);
-  out->val.resize((size_t)total * kBunRows);
-  S.c.resize((size_t)wmax);
-  S.v.resize((size_t)wmax * kBunRows);
   int64_t off = 0;
   for (int k = 0; k < nb; ++k) {
-    const int q = ord[k];
+    const int q = (*ord)[k];
     out->pos_of[q] = k;
     const int r0 = q * kBunRows, rn = std::min(kBunRows, nr - r0);
     int4* R4 = &out->rec[(size_t)4 * k];
@@ -317,6 +322,25 @@ inline void build_bundles(const std::vector<BundleInRow>& rows, BundleScen* out,
     R4[1] = int4{wc[0], wc[1], wc[2], wc[3]};
     R4[2] = int4{pp[0], pp[1], pp[2], pp[3]};
     R4[3] = int4{kp[0], kp[1], kp[2], kp[3]};
+    off += width[q];
+  }
+  out->rec[(size_t)4 * nb] = int4{(int)off, 0, 0, 0};
+  out->nbc = off;
+  out->col.resize((size_t)off);
+  out->val.resize((size_t)off * kBunRows);
+}
+
+inline void bundle_fill(const std::vector<BundleInRow>& rows, const std::vector<int32_t>& width,
+                        const std::vector<int>& ord, int k0, int k1, BundleScen* out, BankScratch& S) {
+  const int nr = (int)rows.size();
+  int wmax = 0;
+  for (int k = k0; k < k1; ++k) wmax = std::max(wmax, width[ord[k]]);
+  if ((int)S.c.size() < wmax) S.c.resize((size_t)wmax);
+  if (S.v.size() < (size_t)wmax * kBunRows) S.v.resize((size_t)wmax * kBunRows);
+  for (int k = k0; k < k1; ++k) {
+    const int q = ord[k];
+    const int r0 = q * kBunRows, rn = std::min(kBunRows, nr - r0);
+    const int64_t off = out->rec[(size_t)4 * k].x;
     const int len = merge_bundle(rows, r0, rn, S.c.data(), S.v.data());
     int32_t* oc = out->col.data() + off;
     float* ov = out->val.data() + off * kBunRows;
@@ -332,9 +356,56 @@ inline void build_bundles(const std::vector<BundleInRow>& rows, BundleScen* out,
       oc[0] = S.c[0];
       for (int r = 0; r < kBunRows; ++r) ov[r] = S.v[r];
     }
-    off += len;
   }
-  out->rec[(size_t)4 * nb] = int4{(int)off, 0, 0, 0};
+}
+
+// One scenario's bundles on the calling thread.
+inline void build_bundles(const std::vector<BundleInRow>& rows, BundleScen* out, BankScratch& S) {
+  const int nb = bundle_count(rows);
+  std::vector<int32_t> width(nb);
+  bundle_widths(rows, 0, nb, width.data());
+  std::vector<int> ord;
+  bundle_order(rows, width, out, &ord);
+  bundle_fill(rows, width, ord, 0, nb, out, S);
+}
+
+// Every scenario's bundles, the same as build_bundles per scenario, with the
+// widths and the fills of all scenarios cut into ranges of kBunRange bundles
+// that nt threads take one after another (the order step runs per scenario).
+constexpr int kBunRange = 2048;
+
+inline void build_bundles_all(const std::vector<std::vector<BundleInRow>>& rows, std::vector<BundleScen>* out,
+                              int nt) {
+  const int N = (int)rows.size();
+  out->assign(N, BundleScen());
+  std::vector<std::vector<int32_t>> width(N);
+  std::vector<std::vector<int>> ord(N);
+  std::vector<int2> items;   // (scenario, first bundle) of every range
+  for (int s = 0; s < N; ++s) {
+    width[s].resize(bundle_count(rows[s]));
+    for (int q = 0; q < (int)width[s].size(); q += kBunRange) items.push_back(int2{s, q});
+  }
+  auto run = [&](int count, auto&& body) {
+    const int t_n = std::max(1, std::min(nt, count));
+    std::atomic<int> next(0);
+    auto loop = [&]() {
+      BankScratch S;
+      for (int i = next++; i < count; i = next++) body(i, S);
+    };
+    std::vector<std::thread> th;
+    for (int t = 1; t < t_n; ++t) th.emplace_back(loop);
+    loop();
+    for (auto& t : th) t.join();
+  };
+  run((int)items.size(), [&](int i, BankScratch&) {
+    const int s = items[i].x, q0 = items[i].y;
+    bundle_widths(rows[s], q0, std::min(q0 + kBunRange, (int)width[s].size()), width[s].data());
+  });
+  run(N, [&](int s, BankScratch&) { bundle_order(rows[s], width[s], &(*out)[s], &ord[s]); });
+  run((int)items.size(), [&](int i, BankScratch& S) {
+    const int s = items[i].x, k0 = items[i].y;
+    bundle_fill(rows[s], width[s], ord[s], k0, std::min(k0 + kBunRange, (int)width[s].size()), &(*out)[s], S);
+  });
 }
 
 }  // namespace layout

@@ -2,6 +2,7 @@
 // with the host compiler alone (no CUDA runtime, no device), so that the host
 // layout logic of plan creation is tested on the CPU.
 #include <cstdint>
+#include <cstring>
 #include <vector>
 
 #include "layout.h"
@@ -94,5 +95,32 @@ int64_t shim_build_bundles(int nrows, const int32_t* rp, const int32_t* ci, cons
 }
 
 int shim_bundle_lanes(int ncols) { return bundle_lanes(ncols); }
+
+// The bundles of N scenarios (CSR each) by the threaded driver with nt threads,
+// compared with build_bundles scenario by scenario: 1 if every array is equal.
+int shim_bundles_all_equal(int N, const int* nrows, const int32_t* const* rp, const int32_t* const* ci,
+                           const float* const* va, int nt) {
+  std::vector<std::vector<BundleInRow>> rows(N);
+  for (int s = 0; s < N; ++s) {
+    rows[s].resize(nrows[s]);
+    for (int i = 0; i < nrows[s]; ++i)
+      rows[s][i] = BundleInRow{5 * i + s, ci[s] + rp[s][i], va[s] + rp[s][i], rp[s][i + 1] - rp[s][i], 0.25f * i,
+                               1.0f + s};
+  }
+  std::vector<BundleScen> A;
+  build_bundles_all(rows, &A, nt);
+  if ((int)A.size() != N) return 0;
+  BankScratch S;
+  for (int s = 0; s < N; ++s) {
+    BundleScen B;
+    build_bundles(rows[s], &B, S);
+    if (A[s].nb != B.nb || A[s].nbc != B.nbc || A[s].col != B.col || A[s].val != B.val || A[s].pos_of != B.pos_of ||
+        A[s].rec.size() != B.rec.size())
+      return 0;
+    for (size_t k = 0; k < B.rec.size(); ++k)
+      if (std::memcmp(&A[s].rec[k], &B.rec[k], sizeof(int4)) != 0) return 0;
+  }
+  return 1;
+}
 
 }  // extern "C"

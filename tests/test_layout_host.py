@@ -23,7 +23,7 @@ def shim(tmp_path_factory):
     if cxx is None or not os.path.exists(os.path.join(CUDA_INC, "vector_types.h")):
         pytest.skip("needs g++ and the CUDA headers")
     out = str(tmp_path_factory.mktemp("layout") / "liblayout_shim.so")
-    subprocess.run([cxx, "-O2", "-std=c++17", "-shared", "-fPIC", "-I", CSRC, "-I", CUDA_INC,
+    subprocess.run([cxx, "-O2", "-std=c++17", "-shared", "-fPIC", "-pthread", "-I", CSRC, "-I", CUDA_INC,
                     os.path.join(HERE, "layout_shim.cpp"), "-o", out], check=True)
     L = C.CDLL(out)
     i32p, f32p, i64p = (np.ctypeslib.ndpointer(t, flags="C") for t in (np.int32, np.float32, np.int64))
@@ -34,6 +34,8 @@ def shim(tmp_path_factory):
     L.shim_build_bundles.argtypes = [C.c_int, i32p, i32p, f32p, i32p, f32p, f32p, C.c_int64, C.c_int,
                                      i32p, f32p, i32p, i32p, C.POINTER(C.c_int)]
     L.shim_build_bundles.restype = C.c_int64
+    L.shim_bundles_all_equal.argtypes = [C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_void_p),
+                                         C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.c_int]
     return L
 
 
@@ -254,3 +256,27 @@ def test_bundles_store_every_entry_once(shim, seed):
             # the union covers the row
             assert set(row) <= set(cols.tolist())
     assert seen.all()
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_bundles_of_all_scenarios_on_threads_equal_one_by_one(shim, seed):
+    """Plan creation bundles every scenario with the work cut into ranges that
+    several threads take (build_bundles_all): the arrays equal those of
+    build_bundles run scenario by scenario, for empty, small and multi-range
+    scenarios and any thread count."""
+    rng = np.random.default_rng(200 + seed)
+    N = int(rng.integers(1, 6))
+    keep = []
+    for _ in range(N):
+        nr = int(rng.choice([0, 1, 5, 300, 9000]))      # 9000 rows: two ranges of 2048 bundles
+        n = int(rng.choice([7, 100, 3000]))
+        lens = rng.integers(1, min(n, 120) + 1, size=nr)
+        rp = np.concatenate([[0], np.cumsum(lens)]).astype(np.int32)
+        ci = np.concatenate([np.sort(rng.choice(n, size=int(k), replace=False)) for k in lens] +
+                            [np.zeros(0)]).astype(np.int32)
+        va = rng.random(int(rp[-1])).astype(np.float32)
+        keep.append((rp, ci, va))
+    nrows = (C.c_int * N)(*[r.size - 1 for r, _, _ in keep])
+    ptrs = [(C.c_void_p * N)(*[a[k].ctypes.data for a in keep]) for k in range(3)]
+    for nt in (1, 3, 8):
+        assert shim.shim_bundles_all_equal(N, nrows, *ptrs, nt) == 1, nt
