@@ -9,6 +9,7 @@
 #include <new>
 #include <string>
 #include <chrono>
+#include <exception>
 #include <thread>
 #include <vector>
 
@@ -292,17 +293,8 @@ int create_plan(const rpt_problem* pr, const rpt_device_opts* opts, rpt_plan** o
   }
   // ---- CSR validation (one host thread per scenario, bounded) ----
   std::vector<ScenarioCheck> chk(N);
-  {
-    const int hw = std::max(1u, std::thread::hardware_concurrency());
-    const int nt = std::min(N, std::min(hw, 32));
-    std::atomic<int> next(0);
-    std::vector<std::thread> th;
-    for (int t = 0; t < nt; ++t)
-      th.emplace_back([&]() {
-        for (int s = next++; s < N; s = next++) check_scenario(pr, s, &chk[s]);
-      });
-    for (auto& t : th) t.join();
-  }
+  parallel_for(N, std::min<int>(std::max(1u, std::thread::hardware_concurrency()), 32),
+               [&](int s, int) { check_scenario(pr, s, &chk[s]); });
   for (int s = 0; s < N; ++s)
     if (!chk[s].err.empty()) {
       set_error(chk[s].err);
@@ -364,6 +356,14 @@ int create_plan(const rpt_problem* pr, const rpt_device_opts* opts, rpt_plan** o
     set_error("out of host memory");
     return RPT_ENOMEM;
   }
+  // an exception from here on (out of host memory) releases the plan while it
+  // unwinds; every error return releases it itself
+  struct ReleaseOnThrow {
+    Plan* p;
+    ~ReleaseOnThrow() {
+      if (std::uncaught_exceptions() > 0) free_plan(p);
+    }
+  } release_on_throw{P};
   P->device = opts ? opts->device : 0;
   cudaError_t e = cudaSetDevice(P->device);
   if (e != cudaSuccess) {
@@ -631,15 +631,8 @@ int create_plan(const rpt_problem* pr, const rpt_device_opts* opts, rpt_plan** o
       }
       out[R.nrows[s]] = make_int4(pos, 0, 0, 0);
     };
-    const int hw = std::max(1u, std::thread::hardware_concurrency());
-    const int nt = std::min(N, std::min(hw, 32));
-    std::atomic<int> next(0);
-    std::vector<std::thread> th;
-    for (int t = 0; t < nt; ++t)
-      th.emplace_back([&]() {
-        for (int s = next++; s < N; s = next++) fill(s);
-      });
-    for (auto& t : th) t.join();
+    parallel_for(N, std::min<int>(std::max(1u, std::thread::hardware_concurrency()), 32),
+                 [&](int s, int) { fill(s); });
   }
   // ---- work decomposition: register-direct row blocks (default) or bulk-copy ring ----
   const double per_lane = 4.0;   // register path: per-row overhead per lane, in entries

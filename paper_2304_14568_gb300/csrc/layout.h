@@ -13,6 +13,7 @@
 #include <atomic>
 #include <climits>
 #include <cstring>
+#include <exception>
 #include <thread>
 #include <vector>
 
@@ -20,6 +21,32 @@
 
 namespace rpt {
 namespace layout {
+
+// Runs body(i, t) for every i in [0, count) on min(nt, count) threads, t being
+// the thread's index (the calling thread is thread 0); items are taken one after
+// another.  An exception in a thread (out of memory) stops the others from
+// taking new items and is rethrown here once every thread has joined.
+template <typename F>
+inline void parallel_for(int count, int nt, F&& body) {
+  const int t_n = std::max(1, std::min(nt, count));
+  std::atomic<int> next(0);
+  std::atomic<bool> failed(false);
+  std::vector<std::exception_ptr> err(t_n);
+  auto loop = [&](int t) {
+    try {
+      for (int i = next++; i < count && !failed; i = next++) body(i, t);
+    } catch (...) {
+      err[t] = std::current_exception();
+      failed = true;
+    }
+  };
+  std::vector<std::thread> th;
+  for (int t = 1; t < t_n; ++t) th.emplace_back(loop, t);
+  loop(0);
+  for (auto& t : th) t.join();
+  for (auto& e : err)
+    if (e) std::rethrow_exception(e);
+}
 
 // Lanes per row: the smallest power of two G >= min_lanes with G * kKeep >= len
 // (at most 32).  min_lanes > 1 keeps the rows that share one warp instruction few:
@@ -372,6 +399,7 @@ inline void build_bundles(const std::vector<BundleInRow>& rows, BundleScen* out,
 // Every scenario's bundles, the same as build_bundles per scenario, with the
 // widths and the fills of all scenarios cut into ranges of kBunRange bundles
 // that nt threads take one after another (the order step runs per scenario).
+// An exception in a thread is rethrown on the caller's.
 constexpr int kBunRange = 2048;
 
 inline void build_bundles_all(const std::vector<std::vector<BundleInRow>>& rows, std::vector<BundleScen>* out,
@@ -385,26 +413,16 @@ inline void build_bundles_all(const std::vector<std::vector<BundleInRow>>& rows,
     width[s].resize(bundle_count(rows[s]));
     for (int q = 0; q < (int)width[s].size(); q += kBunRange) items.push_back(int2{s, q});
   }
-  auto run = [&](int count, auto&& body) {
-    const int t_n = std::max(1, std::min(nt, count));
-    std::atomic<int> next(0);
-    auto loop = [&]() {
-      BankScratch S;
-      for (int i = next++; i < count; i = next++) body(i, S);
-    };
-    std::vector<std::thread> th;
-    for (int t = 1; t < t_n; ++t) th.emplace_back(loop);
-    loop();
-    for (auto& t : th) t.join();
-  };
-  run((int)items.size(), [&](int i, BankScratch&) {
+  std::vector<BankScratch> scratch(std::max(1, std::min(nt, (int)items.size())));
+  parallel_for((int)items.size(), nt, [&](int i, int) {
     const int s = items[i].x, q0 = items[i].y;
     bundle_widths(rows[s], q0, std::min(q0 + kBunRange, (int)width[s].size()), width[s].data());
   });
-  run(N, [&](int s, BankScratch&) { bundle_order(rows[s], width[s], &(*out)[s], &ord[s]); });
-  run((int)items.size(), [&](int i, BankScratch& S) {
+  parallel_for(N, nt, [&](int s, int) { bundle_order(rows[s], width[s], &(*out)[s], &ord[s]); });
+  parallel_for((int)items.size(), (int)scratch.size(), [&](int i, int t) {
     const int s = items[i].x, k0 = items[i].y;
-    bundle_fill(rows[s], width[s], ord[s], k0, std::min(k0 + kBunRange, (int)width[s].size()), &(*out)[s], S);
+    bundle_fill(rows[s], width[s], ord[s], k0, std::min(k0 + kBunRange, (int)width[s].size()), &(*out)[s],
+                scratch[t]);
   });
 }
 
