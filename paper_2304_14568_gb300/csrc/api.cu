@@ -291,7 +291,7 @@ int create_plan(const rpt_problem* pr, const rpt_device_opts* opts, rpt_plan** o
       return RPT_EINVAL;
     }
   }
-  // ---- CSR validation (one host thread per scenario, bounded) ----
+  // ---- CSR validation (scenarios spread over the host threads) ----
   std::vector<ScenarioCheck> chk(N);
   parallel_for(N, std::min<int>(std::max(1u, std::thread::hardware_concurrency()), 32),
                [&](int s, int) { check_scenario(pr, s, &chk[s]); });
@@ -481,8 +481,9 @@ int create_plan(const rpt_problem* pr, const rpt_device_opts* opts, rpt_plan** o
       {
         // each scenario's rows in kept order, then the bundles of all scenarios
         // with their work spread over every host thread
+        const int nt = std::min<int>(std::max(1u, std::thread::hardware_concurrency()), 32);
         std::vector<std::vector<BundleInRow>> rows(N);
-        for (int s = 0; s < N; ++s) {
+        parallel_for(N, nt, [&](int s, int) {
           const int32_t* rp = pr->row_ptr[s];
           rows[s].reserve(order[s].size());
           for (int32_t k : order[s]) {
@@ -496,9 +497,8 @@ int create_plan(const rpt_problem* pr, const rpt_device_opts* opts, rpt_plan** o
             br.p = (float)pr->presc[i];
             rows[s].push_back(br);
           }
-        }
-        const int hw = std::max(1u, std::thread::hardware_concurrency());
-        build_bundles_all(rows, &B, std::min(hw, 32));
+        });
+        build_bundles_all(rows, &B, nt);
       }
       RowLists RB;
       RB.rec_base.assign(N + 1, 0);
