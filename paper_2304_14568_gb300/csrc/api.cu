@@ -360,8 +360,9 @@ int create_plan(const rpt_problem* pr, const rpt_device_opts* opts, rpt_plan** o
   // unwinds; every error return releases it itself
   struct ReleaseOnThrow {
     Plan* p;
+    int before = std::uncaught_exceptions();
     ~ReleaseOnThrow() {
-      if (std::uncaught_exceptions() > 0) free_plan(p);
+      if (std::uncaught_exceptions() > before) free_plan(p);
     }
   } release_on_throw{P};
   P->device = opts ? opts->device : 0;
